@@ -1,0 +1,317 @@
+#!/usr/bin/env python3
+"""Benchmark of the bulk histogram fill on GB300 (one JSON line on rank 0).
+
+Workload (one step): the 1D weighted configuration, two fills of 1e8 events
+each through the C ABI -- (a) 1000 fixed bins on [-5,5), x ~ N(0,1);
+(b) 500 log-spaced variable bins on [1,1000], x ~ Exp(mean 30); weights
+U[0.5,1.5) -- binary64 columns resident in HBM (1.6 GB per fill, far larger
+than the 129 MB L2, so no flush is needed between steps).
+
+``value`` is events filled per second over the timed steps (max over ranks,
+CUDA events on the launching stream).  ``e2e`` is the same metric through the
+same public calls with the inputs copied each step from pinned host memory
+and the result read back.  ``roofline`` is the dominant fill kernel's
+algorithmic HBM bytes (16 per event: x and w read once) per launch over its
+measured launch time, against the measured HBM copy bandwidth.
+``cpu_baseline`` times the CPU oracle (chunk-parallel, all host cores) on the
+same workload drawn on the host.
+
+--impl reference times the CPU oracle itself as the reference arm (bounded
+samples of the same workload per step).
+Multi-GPU (torchrun): every rank fills its own events (weak scaling, no
+data-path collective); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_EVENTS = 100_000_000
+BYTES_PER_EVENT = 16  # binary64 coordinate + binary64 weight, each read once
+METRIC = "Gevents/s filled"
+WORKLOAD = ("1d_weighted_1e8x2: (a) 1000 fixed bins [-5,5) x~N(0,1); "
+            "(b) 500 log bins [1,1000] x~Exp(30); w~U[0.5,1.5)")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 100):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", f"-lms={period_ms}"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(n_per_fill: int, threads: int):
+    """The CPU oracle on host-drawn inputs of the same workload."""
+    import oracle
+    from paper_2401_13310_gb300 import workloads as W
+    oracle.build()
+    wa = W.cfg2a(n=n_per_fill)
+    wb = W.cfg2b(n=n_per_fill)
+    t0 = time.perf_counter()
+    oracle.fill(wa.axes, wa.values, wa.weights, threads=threads)
+    oracle.fill(wb.axes, wb.values, wb.weights, threads=threads)
+    dt = time.perf_counter() - t0
+    return 2 * n_per_fill / dt / 1e9, dt
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, timed on the host cores."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2401_13310_gb300 import workloads as W
+    oracle.build()
+    threads = len(os.sched_getaffinity(0))
+    n = args.ref_events
+    wa = W.cfg2a(n=n)
+    wb = W.cfg2b(n=n)
+    for _ in range(args.warmup):
+        oracle.fill(wa.axes, wa.values, wa.weights, threads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.fill(wa.axes, wa.values, wa.weights, threads=threads)
+        oracle.fill(wb.axes, wb.values, wb.weights, threads=threads)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = 2 * n * args.steps / total / 1e9
+    sample = f"{n} events of each of (a) and (b) per step, drawn on the host (numpy PCG64)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gevents/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "events_per_step": 2 * n, "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": "Gevents/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "Gevents/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2401_13310_gb300 import _build
+    _build.build()
+    from paper_2401_13310_gb300 import binding as B
+    from paper_2401_13310_gb300 import workloads as W
+
+    world, rank, local = dist_setup()
+    n = args.events
+    # device-resident inputs (torch Philox on the GPU, seeded per rank)
+    wa = W.cfg2a(n=n, device="cuda", seed=1 + 1000 * rank)
+    wb = W.cfg2b(n=n, device="cuda", seed=2 + 1000 * rank)
+    flags = {"fp64": B.HIST_PREC_FP64, "f64atomic": B.HIST_PREC_F64ATOMIC}[args.prec]
+    ha = B.Hist(wa.axes, flags)
+    hb = B.Hist(wb.axes, flags)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ha.fill(wa.values, wa.weights)
+        hb.fill(wb.values, wb.weights)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        ha.fill(wa.values, wa.weights)
+        ev[k][1].record(stream)
+        hb.fill(wb.values, wb.weights)
+        ev[k][2].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms_total = max_over_ranks(t_start.elapsed_time(t_end), world)
+    ms_a = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    ms_b = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    events_total = 2 * n * args.steps * world
+    value = events_total / (ms_total * 1e-3) / 1e9
+
+    hbm, peak_src = peaks()
+    avg_a, avg_b = sum(ms_a) / len(ms_a), sum(ms_b) / len(ms_b)
+    dom_ms, dom = (avg_a, "a_fixed1000") if avg_a >= avg_b else (avg_b, "b_var500")
+    achieved = BYTES_PER_EVENT * n / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "kernel": f"k_fill (1D, fixed-point) on {dom}",
+                "peak_source": peak_src,
+                "per_fill_ms": {"a_fixed1000": avg_a, "b_var500": avg_b},
+                "frac_a": BYTES_PER_EVENT * n / (avg_a * 1e-3) / 1e9 / hbm,
+                "frac_b": BYTES_PER_EVENT * n / (avg_b * 1e-3) / 1e9 / hbm}
+
+    # ---- end to end: host inputs copied every step, result read back
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    host = [t.to("cpu").pin_memory() for t in (wa.values, wa.weights, wb.values, wb.weights)]
+    dev = [torch.empty_like(t) for t in (wa.values, wa.weights, wb.values, wb.weights)]
+    h2d = sum(t.numel() * t.element_size() for t in host)
+    d2h = (ha.nbins_total + hb.nbins_total) * 32 + 2 * 12 * 8
+    ha.reset()
+    hb.reset()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for d, hsrc in zip(dev, host):
+            d.copy_(hsrc, non_blocking=True)
+        ha.fill(dev[0], dev[1])
+        hb.fill(dev[2], dev[3])
+        ha.result()
+        hb.result()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": 2 * n * e2e_steps * world / e2e_s / 1e9, "unit": "Gevents/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+    del host, dev
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = len(os.sched_getaffinity(0))
+        v, dt = cpu_baseline(args.cpu_events, threads)
+        cpu = {"value": v, "unit": "Gevents/s", "cores": threads, "kind": "oracle",
+               "sample": f"{args.cpu_events} events of each of (a) and (b), drawn on the host "
+                         f"(numpy PCG64), chunk-parallel oracle, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gevents/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "events_per_step": 2 * n,
+                       "l2": "inputs larger than L2 (1.6 GB per fill), no flush",
+                       "precision": args.prec, "parallelism": f"dp{world} (independent events per rank)"},
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": 4 * args.steps, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ha.close()
+    hb.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--events", type=int, default=N_EVENTS)
+    ap.add_argument("--prec", choices=["fp64", "f64atomic"], default="fp64")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-events", type=int, default=N_EVENTS)
+    ap.add_argument("--ref-events", type=int, default=20_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,167 @@
+/*
+ * hist.h -- C ABI of the GB300 bulk histogram-filling library (libhist.so).
+ *
+ * The operation (Chen, Dessole, Varbanescu 2024, Sec. 3.1 "Histogramming
+ * Action"): for every event of a bulk, (1) find the bin of its coordinate on
+ * each axis -- fixed-width bins by the formula
+ * 1 + floor(nbins * (x - min) / (max - min)), variable-width bins by a binary
+ * search over the edges, coordinates outside the range in the underflow bin 0
+ * or the overflow bin nbins + 1, higher dimensions repeating the search per
+ * axis -- (2) add one, or the event weight, to that bin, and (3) update the
+ * statistics sums (Sec. 3.2: in 1D sum w, sum w^2, sum w*x, sum w*x^2).
+ * As in the paper's GPU histogram class (Sec. 3.2), the library owns the
+ * device allocations, fills bulk by bulk and copies the result back once.
+ *
+ * Semantics (the same readings as the CPU oracle that the tests compare
+ * against):
+ *   - bins are lower-inclusive [e_j, e_{j+1});
+ *   - the fixed formula is evaluated left to right in binary64 without fused
+ *     multiply-add, and a coordinate x < max is never overflow;
+ *   - NaN coordinates go to the overflow bin; +-inf to overflow / underflow;
+ *   - ND bins are linearised x fastest: g = b0 + (n0+2) * (b1 + (n1+2) * b2);
+ *   - statistics cover events whose every axis bin is in range (all events
+ *     with HIST_STAT_OVERFLOWS); slot 0 counts every event;
+ *   - fills accumulate: a fill adds to the previous fills, never overwrites.
+ *
+ * Conventions: every function returns a status (HIST_OK = 0 or a negative
+ * HIST_ERR_*); nothing is thrown across the ABI; all argument checks happen
+ * on the host before any launch.  Device pointers are CUDA device (or
+ * managed) addresses on the histogram's device; host pointers are ordinary
+ * host memory.  A stream argument is a cudaStream_t (NULL = the legacy
+ * default stream).
+ */
+#ifndef HIST_H
+#define HIST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *hist_stream_t; /* the same type as cudaStream_t */
+
+/* Status codes. */
+enum {
+  HIST_OK = 0,
+  HIST_ERR_ARG = -1,      /* bad argument (null pointer, n < 0, bad flags, ...) */
+  HIST_ERR_AXIS = -2,     /* invalid axis: nbins < 1, min >= max, non-finite or
+                             non-increasing edges */
+  HIST_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+  HIST_ERR_OOM = -4,      /* device or host allocation failed */
+  HIST_ERR_ALIGN = -5,    /* pointer not 8-byte aligned */
+  HIST_ERR_TIMEOUT = -6,  /* a bounded device wait gave up */
+  HIST_ERR_LOCATOR = -7,  /* learned locator not trained / unusable */
+  HIST_ERR_STATE = -8,    /* call not valid in the object's current state */
+  HIST_ERR_UNSUPPORTED = -9
+};
+
+/* Axis kinds. */
+enum { HIST_AXIS_FIXED = 0, HIST_AXIS_VARIABLE = 1 };
+
+/* One axis.  FIXED: nbins bins of equal width on [xmin, xmax), both finite,
+ * xmin < xmax, (xmax - xmin) finite.  VARIABLE: edges[0..nbins] strictly
+ * increasing and finite (host pointer, copied by hist_book; xmin/xmax are
+ * ignored). */
+typedef struct {
+  int32_t kind;
+  int32_t nbins;
+  double xmin, xmax;
+  const double *edges;
+} hist_axis_t;
+
+/* Booking flags (bitwise or). */
+#define HIST_TRACK_COUNTS (1u << 0)   /* keep per-bin entry counts for weighted fills */
+#define HIST_STAT_OVERFLOWS (1u << 1) /* include under/overflow entries in the statistics */
+/* Accumulation of weighted bin contents (bits 4-5):
+ *   HIST_PREC_FP64   (default) exact fixed-point sums of each weight truncated
+ *                    to a multiple of 2^-50 (relative error <= 2^-42 per
+ *                    weight with |w| in [2^-8, 2^8); other weights are added
+ *                    in binary64); per-bin error <= 2.3e-13 * sum |w|;
+ *                    bit-reproducible for in-window weights.
+ *   HIST_PREC_FP32C  FP32 compensated (hi, lo) partials per block, flushed
+ *                    to binary64; per-bin error bound stated in the docs.
+ *   HIST_PREC_F64ATOMIC  binary64 atomic adds (order-dependent rounding). */
+#define HIST_PREC_FP64 (0u << 4)
+#define HIST_PREC_FP32C (1u << 4)
+#define HIST_PREC_F64ATOMIC (2u << 4)
+#define HIST_PREC_MASK (3u << 4)
+/* Variable-axis locator (bits 8-9): binary search (default) or a trained
+ * index model with an exact window correction (needs hist_train_locator). */
+#define HIST_LOCATOR_BSEARCH (0u << 8)
+#define HIST_LOCATOR_LEARNED (1u << 8)
+#define HIST_LOCATOR_MASK (3u << 8)
+
+typedef struct hist hist_t; /* opaque; owns its device bins, statistics and axis tables */
+
+/* Book a 1D-3D histogram on the current CUDA device (Sec. 3.1: the booking
+ * of a histogram model with its axes).  Validates the axes, builds the exact
+ * per-axis threshold tables and allocates the device state; no fill is in
+ * flight afterwards.  *out receives the new object (owned by the caller,
+ * released with hist_free).  Errors: HIST_ERR_ARG, HIST_ERR_AXIS,
+ * HIST_ERR_OOM, HIST_ERR_CUDA. */
+int hist_book(const hist_axis_t *axes, int ndim, uint32_t flags, hist_t **out);
+
+/* Fill one bulk of n events (Sec. 3.1 steps 1-3; Sec. 3.2 fill per bulk).
+ * values: device, column-major [ndim][n] (axis d at values + d*n), binary64.
+ * weights: device [n] binary64, or NULL for unit weights.
+ * Asynchronous and ordered on `stream`: the caller keeps the inputs alive and
+ * unmodified until the stream has passed this call (the paper's Sec. 3.3
+ * lesson: a host bulk must not be overwritten while its copy is in flight).
+ * Fills accumulate.  n == 0 is a no-op.  Errors: HIST_ERR_ARG (null h or
+ * values with n > 0, n < 0), HIST_ERR_ALIGN (pointer not 8-byte aligned),
+ * HIST_ERR_CUDA. */
+int hist_fill_bulk(hist_t *h, const double *values, const double *weights, int64_t n,
+                   hist_stream_t stream);
+
+/* Copy the accumulated result to host memory (the single copy-back of
+ * Sec. 3.2).  Synchronises the stream of the last fill.
+ * bins: host [nbins_total] binary64 bin contents, ROOT-linearised (x fastest,
+ *       flow bins included), or NULL;
+ * stats: host [hist_nstats] = [N, sum w, sum w^2, sum wx, sum wx^2
+ *        (, sum wy, sum wy^2, sum wxy (, sum wz, sum wz^2, sum wxz, sum wyz))],
+ *        or NULL.
+ * Non-destructive: later fills keep accumulating. */
+int hist_result(hist_t *h, double *bins, double *stats);
+
+/* Host [nbins_total] entry counts per bin (exact).  Unit-weight histograms
+ * always have them; weighted ones need HIST_TRACK_COUNTS (else
+ * HIST_ERR_STATE). */
+int hist_counts(hist_t *h, uint64_t *counts);
+
+/* Per-event linear bin index of a bulk (step 1 of Sec. 3.1 alone).
+ * values as in hist_fill_bulk; out: device int64 [n].  Asynchronous on
+ * `stream`.  Does not change the histogram. */
+int hist_locate(hist_t *h, const double *values, int64_t n, int64_t *out, hist_stream_t stream);
+
+/* Zero bins, counts and statistics (synchronous). */
+int hist_reset(hist_t *h);
+
+/* Release all device and host state (synchronises first).  NULL is a no-op. */
+void hist_free(hist_t *h);
+
+/* Sizes. */
+int64_t hist_nbins_total(const hist_t *h);
+int hist_nstats(const hist_t *h);
+int hist_ndim(const hist_t *h);
+
+/* The exact threshold keys of one axis, as the device compares them (host
+ * only; needs no GPU).  out: host int64 [axis->nbins + 3].  key(x) is the
+ * int64 that orders like the binary64 x (-0 and +0 -> 0, NaN -> overflow);
+ * out[0] = INT64_MIN, out[nbins+2] = INT64_MAX and, for k = 1..nbins+1,
+ * out[k] = the least key whose coordinate lands in bin k or above under the
+ * Sec. 3.1 rule of this axis.  The bin of x is the largest k with
+ * out[k] <= key(x).  Errors: HIST_ERR_ARG, HIST_ERR_AXIS. */
+int hist_axis_thresholds(const hist_axis_t *axis, int64_t *out);
+
+/* Static description of a status code. */
+const char *hist_strerror(int code);
+
+/* Library version string. */
+const char *hist_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HIST_H */

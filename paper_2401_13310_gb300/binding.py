@@ -1,0 +1,266 @@
+"""Thin ctypes binding of ``libhist.so`` (the C ABI in ``include/hist.h``).
+
+Argument marshalling only: every step of the fill runs in the library's CUDA
+kernels.  There is no CPU fallback -- if ``libhist.so`` is missing or cannot
+be loaded, every call raises.  PyTorch is used for device memory and the
+current stream (``data_ptr()``, ``torch.cuda.current_stream().cuda_stream``).
+
+The functions keep the C names (``hist_book``, ``hist_fill_bulk``,
+``hist_result`` ...); :class:`Hist` is a small owner object around them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhist.so")
+
+HIST_OK = 0
+HIST_ERR_ARG = -1
+HIST_ERR_AXIS = -2
+HIST_ERR_CUDA = -3
+HIST_ERR_OOM = -4
+HIST_ERR_ALIGN = -5
+HIST_ERR_TIMEOUT = -6
+HIST_ERR_LOCATOR = -7
+HIST_ERR_STATE = -8
+HIST_ERR_UNSUPPORTED = -9
+
+HIST_AXIS_FIXED = 0
+HIST_AXIS_VARIABLE = 1
+
+HIST_TRACK_COUNTS = 1 << 0
+HIST_STAT_OVERFLOWS = 1 << 1
+HIST_PREC_FP64 = 0 << 4
+HIST_PREC_FP32C = 1 << 4
+HIST_PREC_F64ATOMIC = 2 << 4
+HIST_LOCATOR_BSEARCH = 0 << 8
+HIST_LOCATOR_LEARNED = 1 << 8
+
+
+class HistError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+class hist_axis_t(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nbins", ctypes.c_int32),
+                ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
+                ("edges", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+_P = ctypes.c_void_p
+
+
+def load(path: str | None = None):
+    """Load libhist.so (raises if it is not built: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with paper_2401_13310_gb300.build()")
+        lib = ctypes.CDLL(p)
+        sig = {
+            "hist_book": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint32, _P]),
+            "hist_fill_bulk": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P]),
+            "hist_result": (ctypes.c_int, [_P, _P, _P]),
+            "hist_counts": (ctypes.c_int, [_P, _P]),
+            "hist_locate": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+            "hist_reset": (ctypes.c_int, [_P]),
+            "hist_free": (None, [_P]),
+            "hist_nbins_total": (ctypes.c_int64, [_P]),
+            "hist_nstats": (ctypes.c_int, [_P]),
+            "hist_ndim": (ctypes.c_int, [_P]),
+            "hist_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "hist_version": (ctypes.c_char_p, []),
+            "hist_axis_thresholds": (ctypes.c_int, [_P, _P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().hist_strerror(code).decode()
+    except Exception:  # pragma: no cover - only when the library is absent
+        return "status"
+
+
+def _check(code: int, where: str) -> None:
+    if code != HIST_OK:
+        raise HistError(code, where)
+
+
+def make_axes(axes):
+    """Plain axis dicts -> (ctypes array, keepalive)."""
+    arr = (hist_axis_t * len(axes))()
+    keep = []
+    for d, ax in enumerate(axes):
+        if ax["kind"] == "fixed":
+            arr[d].kind = HIST_AXIS_FIXED
+            arr[d].nbins = int(ax["nbins"])
+            arr[d].xmin = float(ax["xmin"])
+            arr[d].xmax = float(ax["xmax"])
+            arr[d].edges = None
+        else:
+            e = np.ascontiguousarray(ax["edges"], dtype=np.float64)
+            keep.append(e)
+            arr[d].kind = HIST_AXIS_VARIABLE
+            arr[d].nbins = int(e.shape[0] - 1)
+            arr[d].edges = e.ctypes.data
+    return arr, keep
+
+
+def _ptr(x) -> int | None:
+    """Device/host address of a torch tensor, numpy array or raw int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------- C names ----
+
+def hist_book(axes, flags: int = 0) -> int:
+    arr, keep = make_axes(axes)
+    out = ctypes.c_void_p()
+    rc = load().hist_book(ctypes.addressof(arr), len(axes), int(flags), ctypes.byref(out))
+    del keep
+    _check(rc, "hist_book")
+    return out.value
+
+
+def hist_fill_bulk(h: int, values, weights, n: int, stream=None) -> None:
+    _check(load().hist_fill_bulk(h, _ptr(values), _ptr(weights), int(n), _stream_ptr(stream)),
+           "hist_fill_bulk")
+
+
+def hist_locate(h: int, values, n: int, out, stream=None) -> None:
+    _check(load().hist_locate(h, _ptr(values), int(n), _ptr(out), _stream_ptr(stream)), "hist_locate")
+
+
+def hist_nbins_total(h: int) -> int:
+    return int(load().hist_nbins_total(h))
+
+
+def hist_nstats(h: int) -> int:
+    return int(load().hist_nstats(h))
+
+
+def hist_result(h: int):
+    nb, ns = hist_nbins_total(h), hist_nstats(h)
+    bins = np.zeros(nb, dtype=np.float64)
+    stats = np.zeros(ns, dtype=np.float64)
+    _check(load().hist_result(h, bins.ctypes.data, stats.ctypes.data), "hist_result")
+    return bins, stats
+
+
+def hist_counts(h: int) -> np.ndarray:
+    c = np.zeros(hist_nbins_total(h), dtype=np.uint64)
+    _check(load().hist_counts(h, c.ctypes.data), "hist_counts")
+    return c
+
+
+def hist_reset(h: int) -> None:
+    _check(load().hist_reset(h), "hist_reset")
+
+
+def hist_free(h: int) -> None:
+    load().hist_free(h)
+
+
+def hist_axis_thresholds(axis) -> np.ndarray:
+    """The exact threshold keys (int64, nbins + 3) the device compares against."""
+    arr, keep = make_axes([axis])
+    nb = int(arr[0].nbins)
+    out = np.zeros(nb + 3, dtype=np.int64)
+    rc = load().hist_axis_thresholds(ctypes.addressof(arr), out.ctypes.data)
+    del keep
+    _check(rc, "hist_axis_thresholds")
+    return out
+
+
+# ---------------------------------------------------------------- owner ------
+
+class Hist:
+    """Owns one booked histogram.  ``values`` is a CUDA float64 tensor of
+    shape (ndim, n) (or (n,) in 1D), ``weights`` a CUDA float64 tensor (n,)
+    or None; fills run on the current torch stream and accumulate."""
+
+    def __init__(self, axes, flags: int = 0):
+        self.axes = axes
+        self.ndim = len(axes)
+        self.flags = flags
+        self.h = hist_book(axes, flags)
+
+    def fill(self, values, weights=None, stream=None) -> None:
+        n = int(values.shape[-1])
+        if values.dim() == 1:
+            assert self.ndim == 1
+        else:
+            assert values.shape[0] == self.ndim and values.is_contiguous()
+        if weights is not None:
+            assert weights.shape == (n,) and weights.is_contiguous()
+        hist_fill_bulk(self.h, values, weights, n, stream)
+
+    def locate(self, values, out=None, stream=None):
+        import torch
+        n = int(values.shape[-1])
+        if out is None:
+            out = torch.empty(n, dtype=torch.int64, device=values.device)
+        hist_locate(self.h, values, n, out, stream)
+        return out
+
+    def result(self):
+        return hist_result(self.h)
+
+    def counts(self):
+        return hist_counts(self.h)
+
+    def reset(self):
+        hist_reset(self.h)
+
+    @property
+    def nbins_total(self) -> int:
+        return hist_nbins_total(self.h)
+
+    def close(self) -> None:
+        if self.h:
+            hist_free(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

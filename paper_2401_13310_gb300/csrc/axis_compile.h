@@ -1,0 +1,27 @@
+// axis_compile.h -- host-side axis validation and exact threshold tables.
+#pragma once
+
+#include <cstdint>
+
+namespace hgb {
+
+// Key that orders like the double (-0 and +0 -> 0; NaN -> just below INT64_MAX).
+int64_t host_key(double x);
+double host_double_of_key(int64_t k);
+
+// Sec. 3.1 fixed-width find-bin, binary64 without contraction, x < max never overflow.
+int32_t host_fixed_bin(int32_t nbins, double xmin, double xmax, double x);
+
+// 0 if the axis is valid (kind 0 fixed, 1 variable), -1 otherwise.
+int validate_axis(int32_t kind, int32_t nbins, double xmin, double xmax, const double* edges);
+
+// T must hold nbins + 3 keys: T[0] = INT64_MIN, T[nbins+2] = INT64_MAX and
+// T[k] = least key whose coordinate's bin is >= k, k = 1..nbins+1.
+void build_fixed_thresholds(int32_t nbins, double xmin, double xmax, int64_t* T);
+void build_variable_thresholds(int32_t nbins, const double* edges, int64_t* T);
+
+// FP32 affine estimate k ~ floor(xf * scale + offset); returns true when its
+// error over in-range coordinates stays well under one bin.
+bool affine_estimate(int32_t nbins, double xmin, double xmax, float* scale, float* offset);
+
+}  // namespace hgb

@@ -1,0 +1,451 @@
+// hist_api.cpp -- the C ABI declared in include/hist.h.
+//
+// A histogram object plays the role of the paper's GPU histogram class
+// (Sec. 3.2): it owns the device allocations (bins, statistics, axis
+// tables, launch scratch), fills bulk by bulk on the caller's stream, and
+// copies the result back once on request.  Fills accumulate (Sec. 3.3: the
+// statistics of the previous bulk are combined with the current ones, never
+// overwritten).  All argument checks run on the host before any launch.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/hist.h"
+#include "axis_compile.h"
+#include "hist_internal.h"
+
+using namespace hgb;
+
+namespace {
+
+constexpr int kDefaultFxElo = 1015;             // |w| in [2^-8, 2^8) summed exactly
+constexpr size_t kSmemTableBudget = 64 * 1024;  // threshold keys staged per block
+constexpr size_t kSmemBinsBudget = 96 * 1024;   // per-block bins (keeps >= 2 blocks per SM)
+
+}  // namespace
+
+struct hist {
+  int device = 0;
+  int sm_count = 0;
+  int ndim = 0;
+  int nstats = 0;
+  uint32_t flags = 0;
+  int acc_mode = ACC_UNIT;
+  int32_t kind[kMaxDim] = {0, 0, 0};
+  int32_t nbins[kMaxDim] = {0, 0, 0};
+  int64_t nbins_total = 0;
+  // axis tables
+  long long* d_T = nullptr;  // concatenated thresholds, nbins + 3 keys per axis
+  int32_t t_off[kMaxDim] = {0, 0, 0};
+  int32_t table_keys = 0;
+  int32_t smem_keys = 0;     // how many keys are staged into shared memory
+  int32_t loc_mode[kMaxDim] = {0, 0, 0};
+  float scale[kMaxDim] = {0, 0, 0}, offset[kMaxDim] = {0, 0, 0};
+  bool smem_unit = true;     // unit-weight fills keep per-block bins in shared memory
+  bool smem_weighted = true; // weighted fills likewise (16 bytes per bin)
+  int fx_elo = kDefaultFxElo;
+  // persistent accumulators
+  unsigned long long* g_lo = nullptr;
+  long long* g_hi = nullptr;
+  unsigned long long* g_count = nullptr;
+  unsigned long long* g_unit = nullptr;
+  double* g_f64 = nullptr;
+  double* g_stats = nullptr;
+  int64_t n_entries = 0;
+  bool counts_complete = true;  // false once a weighted fill ran without HIST_TRACK_COUNTS
+  int64_t fx_global_since_norm = 0;
+  // launch scratch
+  void* part_bins = nullptr;
+  size_t part_bins_bytes = 0;
+  double* part_stats = nullptr;
+  int part_stats_blocks = 0;
+  // ordering of fills issued on different streams
+  cudaEvent_t done = nullptr;
+  bool have_done = false;
+};
+
+namespace {
+
+template <class T>
+int dalloc(T** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return HIST_ERR_OOM;
+  }
+  return e == cudaSuccess ? HIST_OK : HIST_ERR_CUDA;
+}
+
+void free_state(hist* h) {
+  if (h->done) cudaEventDestroy(h->done);
+  cudaFree(h->d_T);
+  cudaFree(h->g_lo);
+  cudaFree(h->g_hi);
+  cudaFree(h->g_count);
+  cudaFree(h->g_unit);
+  cudaFree(h->g_f64);
+  cudaFree(h->g_stats);
+  cudaFree(h->part_bins);
+  cudaFree(h->part_stats);
+}
+
+int acc_mode_of(uint32_t flags, bool unit) {
+  if (unit) return ACC_UNIT;
+  switch (flags & HIST_PREC_MASK) {
+    case HIST_PREC_F64ATOMIC:
+      return ACC_F64;
+    case HIST_PREC_FP32C:
+      return ACC_F32C;
+    default:
+      return ACC_FX;
+  }
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+// Build the launch parameters of one fill (or locate) call.
+FillParams make_params(const hist* h, const double* values, const double* weights, int64_t n, int acc) {
+  FillParams p;
+  std::memset(&p, 0, sizeof(p));
+  for (int d = 0; d < h->ndim; ++d) {
+    AxisDev& a = p.ax[d];
+    a.T = h->d_T + h->t_off[d];
+    a.nbins = h->nbins[d];
+    a.mode = h->loc_mode[d];
+    a.smem_off = (h->t_off[d] + h->nbins[d] + 3 <= h->smem_keys) ? h->t_off[d] : -1;
+    a.scale = h->scale[d];
+    a.offset = h->offset[d];
+    p.col[d] = values + (size_t)d * (size_t)n;
+  }
+  p.w = weights;
+  p.T_concat = h->d_T;
+  p.n = n;
+  p.nbins_total = h->nbins_total;
+  p.ndim = h->ndim;
+  p.nstats = h->nstats;
+  p.stat_overflows = (h->flags & HIST_STAT_OVERFLOWS) ? 1 : 0;
+  p.track_counts = (h->flags & HIST_TRACK_COUNTS) ? 1 : 0;
+  p.fx_elo = h->fx_elo;
+  p.table_keys = h->smem_keys;
+  bool al = weights == nullptr || aligned16(weights);
+  for (int d = 0; d < h->ndim; ++d) al = al && aligned16(p.col[d]);
+  p.aligned = al ? 1 : 0;
+  p.smem_bins = (acc == ACC_UNIT ? h->smem_unit : h->smem_weighted) ? 1 : 0;
+  p.part_bins = h->part_bins;
+  p.part_stats = h->part_stats;
+  p.g_lo = h->g_lo;
+  p.g_hi = h->g_hi;
+  p.g_count = h->g_count;
+  p.g_unit = h->g_unit;
+  p.g_f64 = h->g_f64;
+  return p;
+}
+
+int ensure_scratch(hist* h, int grid, int acc, bool smem_bins) {
+  const size_t need = smem_bins ? (size_t)grid * (size_t)h->nbins_total * part_bin_bytes(acc, 0) : 16;
+  if (need > h->part_bins_bytes) {
+    cudaFree(h->part_bins);
+    h->part_bins = nullptr;
+    h->part_bins_bytes = 0;
+    int rc = dalloc(&h->part_bins, need);
+    if (rc != HIST_OK) return rc;
+    h->part_bins_bytes = need;
+  }
+  if (grid > h->part_stats_blocks) {
+    cudaFree(h->part_stats);
+    h->part_stats = nullptr;
+    h->part_stats_blocks = 0;
+    int rc = dalloc(&h->part_stats, (size_t)grid * kMaxStats * sizeof(double));
+    if (rc != HIST_OK) return rc;
+    h->part_stats_blocks = grid;
+  }
+  return HIST_OK;
+}
+
+// Order this call after the previous fill when it used another stream.
+int order_after_previous(hist* h, cudaStream_t s) {
+  if (h->have_done) {
+    if (cudaStreamWaitEvent(s, h->done, 0) != cudaSuccess) return HIST_ERR_CUDA;
+  }
+  return HIST_OK;
+}
+
+int fill_impl(hist* h, const double* values, const double* weights, int64_t n, cudaStream_t stream) {
+  const int acc = (weights == nullptr) ? ACC_UNIT : acc_mode_of(h->flags, false);
+  if (acc == ACC_F32C) return HIST_ERR_UNSUPPORTED;
+  if (cudaSetDevice(h->device) != cudaSuccess) return HIST_ERR_CUDA;
+  int rc = order_after_previous(h, stream);
+  if (rc != HIST_OK) return rc;
+  FillParams p = make_params(h, values, weights, n, acc);
+  LaunchShape shape;
+  if (plan_fill(p, acc, h->sm_count, &shape) != 0) return HIST_ERR_CUDA;
+  rc = ensure_scratch(h, shape.grid, acc, p.smem_bins != 0);
+  if (rc != HIST_OK) return rc;
+  p.part_bins = h->part_bins;
+  p.part_stats = h->part_stats;
+  if (launch_fill(p, acc, shape, stream) != 0) return HIST_ERR_CUDA;
+  ReduceParams r;
+  std::memset(&r, 0, sizeof(r));
+  r.part_bins = p.smem_bins ? h->part_bins : nullptr;
+  r.part_stats = h->part_stats;
+  r.nblocks = shape.grid;
+  r.nstats = h->nstats;
+  r.nbins_total = h->nbins_total;
+  r.mode = acc;
+  r.track_counts = p.track_counts;
+  r.g_lo = h->g_lo;
+  r.g_hi = h->g_hi;
+  r.g_count = h->g_count;
+  r.g_unit = h->g_unit;
+  r.g_f64 = h->g_f64;
+  r.g_stats = h->g_stats;
+  if (launch_reduce(r, stream) != 0) return HIST_ERR_CUDA;
+  if (acc == ACC_FX && !p.smem_bins) {
+    h->fx_global_since_norm += n;
+    if (h->fx_global_since_norm > (int64_t)1 << 31) {
+      if (launch_normalize_fx(h->g_lo, h->g_hi, h->nbins_total, stream) != 0) return HIST_ERR_CUDA;
+      h->fx_global_since_norm = 0;
+    }
+  }
+  if (cudaEventRecord(h->done, stream) != cudaSuccess) return HIST_ERR_CUDA;
+  h->have_done = true;
+  h->n_entries += n;
+  if (acc != ACC_UNIT && !(h->flags & HIST_TRACK_COUNTS)) h->counts_complete = false;
+  return HIST_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hist_version(void) { return "gb300-hist 0.1 (sm_103a)"; }
+
+const char* hist_strerror(int code) {
+  switch (code) {
+    case HIST_OK:
+      return "ok";
+    case HIST_ERR_ARG:
+      return "invalid argument";
+    case HIST_ERR_AXIS:
+      return "invalid axis";
+    case HIST_ERR_CUDA:
+      return "CUDA runtime error";
+    case HIST_ERR_OOM:
+      return "out of memory";
+    case HIST_ERR_ALIGN:
+      return "misaligned pointer";
+    case HIST_ERR_TIMEOUT:
+      return "device wait timed out";
+    case HIST_ERR_LOCATOR:
+      return "learned locator unavailable";
+    case HIST_ERR_STATE:
+      return "invalid state for this call";
+    case HIST_ERR_UNSUPPORTED:
+      return "unsupported combination";
+    default:
+      return "unknown status";
+  }
+}
+
+int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
+  if (out == nullptr || axes == nullptr || ndim < 1 || ndim > kMaxDim) return HIST_ERR_ARG;
+  *out = nullptr;
+  const uint32_t known = HIST_TRACK_COUNTS | HIST_STAT_OVERFLOWS | HIST_PREC_MASK | HIST_LOCATOR_MASK;
+  if (flags & ~known) return HIST_ERR_ARG;
+  if ((flags & HIST_PREC_MASK) == (3u << 4)) return HIST_ERR_ARG;
+  if ((flags & HIST_LOCATOR_MASK) > HIST_LOCATOR_LEARNED) return HIST_ERR_ARG;
+  int64_t total = 1;
+  for (int d = 0; d < ndim; ++d) {
+    const hist_axis_t& a = axes[d];
+    if (validate_axis(a.kind, a.nbins, a.xmin, a.xmax, a.edges) != 0) return HIST_ERR_AXIS;
+    total *= (int64_t)a.nbins + 2;
+    if (total >= ((int64_t)1 << 31)) return HIST_ERR_AXIS;
+  }
+  hist* h = new (std::nothrow) hist();
+  if (h == nullptr) return HIST_ERR_OOM;
+  int rc = HIST_OK;
+  do {
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+      rc = HIST_ERR_CUDA;
+      break;
+    }
+    if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+      rc = HIST_ERR_CUDA;
+      break;
+    }
+    h->ndim = ndim;
+    h->nstats = ndim == 1 ? 5 : (ndim == 2 ? 8 : 12);
+    h->flags = flags;
+    h->nbins_total = total;
+    std::vector<int64_t> T;
+    for (int d = 0; d < ndim; ++d) {
+      const hist_axis_t& a = axes[d];
+      h->kind[d] = a.kind;
+      h->nbins[d] = a.nbins;
+      h->t_off[d] = (int32_t)T.size();
+      T.resize(T.size() + (size_t)a.nbins + 3);
+      int64_t* Td = T.data() + h->t_off[d];
+      if (a.kind == HIST_AXIS_FIXED) {
+        build_fixed_thresholds(a.nbins, a.xmin, a.xmax, Td);
+        h->loc_mode[d] =
+            affine_estimate(a.nbins, a.xmin, a.xmax, &h->scale[d], &h->offset[d]) ? LOC_AFFINE : LOC_BSEARCH;
+      } else {
+        build_variable_thresholds(a.nbins, a.edges, Td);
+        h->loc_mode[d] = LOC_BSEARCH;
+      }
+    }
+    h->table_keys = (int32_t)T.size();
+    // stage a prefix of the axes' tables into shared memory
+    h->smem_keys = 0;
+    for (int d = 0; d < ndim; ++d) {
+      const int32_t end = h->t_off[d] + h->nbins[d] + 3;
+      if ((size_t)end * 8 <= kSmemTableBudget) h->smem_keys = end;
+    }
+    rc = dalloc(&h->d_T, T.size() * sizeof(int64_t));
+    if (rc != HIST_OK) break;
+    if (cudaMemcpy(h->d_T, T.data(), T.size() * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+      rc = HIST_ERR_CUDA;
+      break;
+    }
+    // weighted fills use the precision mode; unit fills always count
+    h->acc_mode = acc_mode_of(flags, false);
+    h->smem_unit = (size_t)total * 4 <= kSmemBinsBudget;
+    h->smem_weighted = (size_t)total * 16 <= kSmemBinsBudget;
+    const size_t nb = (size_t)total;
+    if ((rc = dalloc(&h->g_lo, nb * 8)) != HIST_OK) break;
+    if ((rc = dalloc(&h->g_hi, nb * 8)) != HIST_OK) break;
+    if ((rc = dalloc(&h->g_count, nb * 8)) != HIST_OK) break;
+    if ((rc = dalloc(&h->g_unit, nb * 8)) != HIST_OK) break;
+    if ((rc = dalloc(&h->g_f64, nb * 8)) != HIST_OK) break;
+    if ((rc = dalloc(&h->g_stats, kMaxStats * sizeof(double))) != HIST_OK) break;
+    if (cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess) {
+      rc = HIST_ERR_CUDA;
+      break;
+    }
+  } while (false);
+  if (rc == HIST_OK) rc = hist_reset(h);
+  if (rc != HIST_OK) {
+    free_state(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return HIST_OK;
+}
+
+int hist_reset(hist_t* h) {
+  if (h == nullptr) return HIST_ERR_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return HIST_ERR_CUDA;
+  if (h->have_done && cudaEventSynchronize(h->done) != cudaSuccess) return HIST_ERR_CUDA;
+  const size_t nb = (size_t)h->nbins_total;
+  if (cudaMemset(h->g_lo, 0, nb * 8) != cudaSuccess || cudaMemset(h->g_hi, 0, nb * 8) != cudaSuccess ||
+      cudaMemset(h->g_count, 0, nb * 8) != cudaSuccess || cudaMemset(h->g_unit, 0, nb * 8) != cudaSuccess ||
+      cudaMemset(h->g_f64, 0, nb * 8) != cudaSuccess ||
+      cudaMemset(h->g_stats, 0, kMaxStats * sizeof(double)) != cudaSuccess)
+    return HIST_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return HIST_ERR_CUDA;
+  h->n_entries = 0;
+  h->fx_global_since_norm = 0;
+  h->counts_complete = true;
+  return HIST_OK;
+}
+
+void hist_free(hist_t* h) {
+  if (h == nullptr) return;
+  cudaSetDevice(h->device);
+  if (h->have_done) cudaEventSynchronize(h->done);
+  free_state(h);
+  delete h;
+}
+
+int hist_axis_thresholds(const hist_axis_t* axis, int64_t* out) {
+  if (axis == nullptr || out == nullptr) return HIST_ERR_ARG;
+  if (validate_axis(axis->kind, axis->nbins, axis->xmin, axis->xmax, axis->edges) != 0) return HIST_ERR_AXIS;
+  if (axis->kind == HIST_AXIS_FIXED)
+    build_fixed_thresholds(axis->nbins, axis->xmin, axis->xmax, out);
+  else
+    build_variable_thresholds(axis->nbins, axis->edges, out);
+  return HIST_OK;
+}
+
+int64_t hist_nbins_total(const hist_t* h) { return h ? h->nbins_total : -1; }
+int hist_nstats(const hist_t* h) { return h ? h->nstats : -1; }
+int hist_ndim(const hist_t* h) { return h ? h->ndim : -1; }
+
+int hist_fill_bulk(hist_t* h, const double* values, const double* weights, int64_t n, hist_stream_t stream) {
+  if (h == nullptr || n < 0) return HIST_ERR_ARG;
+  if (n == 0) return HIST_OK;
+  if (values == nullptr) return HIST_ERR_ARG;
+  if (!aligned8(values) || (weights != nullptr && !aligned8(weights))) return HIST_ERR_ALIGN;
+  return fill_impl(h, values, weights, n, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int hist_locate(hist_t* h, const double* values, int64_t n, int64_t* out, hist_stream_t stream) {
+  if (h == nullptr || n < 0) return HIST_ERR_ARG;
+  if (n == 0) return HIST_OK;
+  if (values == nullptr || out == nullptr) return HIST_ERR_ARG;
+  if (!aligned8(values) || !aligned8(out)) return HIST_ERR_ALIGN;
+  if (cudaSetDevice(h->device) != cudaSuccess) return HIST_ERR_CUDA;
+  FillParams p = make_params(h, values, nullptr, n, ACC_UNIT);
+  if (launch_locate(p, reinterpret_cast<long long*>(out), reinterpret_cast<void*>(stream)) != 0)
+    return HIST_ERR_CUDA;
+  return HIST_OK;
+}
+
+int hist_result(hist_t* h, double* bins, double* stats) {
+  if (h == nullptr) return HIST_ERR_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return HIST_ERR_CUDA;
+  if (h->have_done && cudaEventSynchronize(h->done) != cudaSuccess) return HIST_ERR_CUDA;
+  const size_t nb = (size_t)h->nbins_total;
+  if (bins != nullptr) {
+    std::vector<unsigned long long> lo(nb), unit(nb);
+    std::vector<long long> hi(nb);
+    std::vector<double> f64(nb);
+    if (cudaMemcpy(lo.data(), h->g_lo, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(hi.data(), h->g_hi, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(unit.data(), h->g_unit, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(f64.data(), h->g_f64, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return HIST_ERR_CUDA;
+    // Content = (fixed-point words + unit entries, as one exact integer in
+    // units of 2^(fx_elo - 1065)) rounded once to binary64, plus the binary64
+    // words (slow-path weights, binary64 mode).
+    const int shift = 1065 - h->fx_elo;
+    const double lsb = std::ldexp(1.0, -shift);
+    for (size_t g = 0; g < nb; ++g) {
+      const __int128 fx = ((__int128)hi[g] << 32) + (__int128)lo[g] + ((__int128)unit[g] << shift);
+      bins[g] = (double)fx * lsb + f64[g];
+    }
+  }
+  if (stats != nullptr) {
+    double s[kMaxStats];
+    if (cudaMemcpy(s, h->g_stats, sizeof(s), cudaMemcpyDeviceToHost) != cudaSuccess) return HIST_ERR_CUDA;
+    s[0] = (double)h->n_entries;
+    for (int k = 0; k < h->nstats; ++k) stats[k] = s[k];
+  }
+  return HIST_OK;
+}
+
+int hist_counts(hist_t* h, uint64_t* counts) {
+  if (h == nullptr || counts == nullptr) return HIST_ERR_ARG;
+  if (!h->counts_complete) return HIST_ERR_STATE;
+  if (cudaSetDevice(h->device) != cudaSuccess) return HIST_ERR_CUDA;
+  if (h->have_done && cudaEventSynchronize(h->done) != cudaSuccess) return HIST_ERR_CUDA;
+  const size_t nb = (size_t)h->nbins_total;
+  std::vector<unsigned long long> unit(nb);
+  if (cudaMemcpy(counts, h->g_count, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(unit.data(), h->g_unit, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HIST_ERR_CUDA;
+  for (size_t g = 0; g < nb; ++g) counts[g] += unit[g];
+  return HIST_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// hist_internal.h -- types shared by the library's host and device code.
+//
+// Every axis, fixed or variable, is reduced at booking time to a table of
+// threshold keys T[0..nbins+2]: T[0] = INT64_MIN, T[nbins+2] = INT64_MAX and,
+// for k = 1..nbins+1, T[k] is the smallest key whose coordinate falls in bin
+// k or above.  The bin of x is then the largest k with T[k] <= key(x), where
+// key() maps a binary64 to an int64 that orders like the double (-0 and +0
+// share key 0; NaN maps just below INT64_MAX, i.e. to the overflow bin).
+// For a variable axis T[k] = key(edge[k-1]) (Sec. 3.1 binary search over
+// the edges, lower-inclusive bins).  For a fixed axis the host finds T[k] by
+// bisection over keys with the binary64 formula of Sec. 3.1, which is
+// monotone in x, so the device reproduces the formula exactly with integer
+// comparisons and never needs binary64 arithmetic.
+#pragma once
+
+#include <cstdint>
+
+namespace hgb {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxStats = 12;
+constexpr long long kNanKey = 0x7FFFFFFFFFFFFFFELL;
+
+// How the device finds the bin on one axis.
+enum LocMode : int32_t {
+  LOC_AFFINE = 0,   // FP32 affine estimate from the coordinate, then <= 1 step correction
+  LOC_BSEARCH = 1,  // branchless binary search over the thresholds
+  LOC_LEARNED = 2,  // trained piecewise-linear index model + windowed search
+};
+
+// How weights reach the bins.
+enum AccMode : int32_t {
+  ACC_UNIT = 0,  // unit weights: u32 counters
+  ACC_FX = 1,    // exact fixed-point sums (u32 limb atomics with carries)
+  ACC_F64 = 2,   // binary64 atomics
+  ACC_F32C = 3,  // FP32 compensated (hi, lo) partials
+};
+
+struct LearnedDev {
+  const int32_t* base;   // [nseg + 1] exact bin index at each segment start
+  const uint16_t* th0;   // [nseg] bf16 offset residual
+  const uint16_t* th1;   // [nseg] bf16 slope
+  float u0, u_scale;     // u = (xf - u0) * u_scale in [0, nseg)
+  int32_t nseg;
+  int32_t window;        // certified half-width of the search window
+};
+
+struct AxisDev {
+  const long long* T;  // device thresholds (nbins + 3 keys)
+  int32_t nbins;
+  int32_t mode;        // LocMode
+  int32_t smem_off;    // offset of this axis' keys in the shared copy, -1 = read T from global
+  float scale, offset; // LOC_AFFINE: k ~ floor(xf * scale + offset)
+  LearnedDev lm;
+};
+
+struct FillParams {
+  AxisDev ax[kMaxDim];
+  const double* col[kMaxDim];
+  const double* w;              // nullptr = unit weights
+  const long long* T_concat;    // all axes' keys back to back (shared-memory staging source)
+  long long n;
+  long long nbins_total;
+  int32_t ndim;
+  int32_t nstats;
+  int32_t stat_overflows;
+  int32_t track_counts;
+  int32_t fx_elo;               // biased binary64 exponent of the fixed-point window's low end
+  int32_t table_keys;           // keys staged into shared memory (sum over staged axes)
+  int32_t aligned;              // columns and weights all 16-byte aligned
+  int32_t smem_bins;            // 1 = per-block shared-memory bins, 0 = global atomics
+  // per-launch partial results (scratch)
+  void* part_bins;              // [grid][nbins_total] words per bin depend on the mode
+  double* part_stats;           // [grid][kMaxStats]
+  // persistent accumulators owned by the histogram
+  unsigned long long* g_lo;     // fixed point: sum of the low 32 bits of every addend
+  long long* g_hi;              // fixed point: sum of (addend >> 32)
+  unsigned long long* g_count;  // entries of weighted fills (HIST_TRACK_COUNTS)
+  unsigned long long* g_unit;   // entries of unit-weight fills (each adds weight 1)
+  double* g_f64;                // binary64 bins (F64 mode, F32C mode, FX slow path)
+};
+
+struct ReduceParams {
+  const void* part_bins;
+  const double* part_stats;
+  int32_t nblocks;
+  int32_t nstats;
+  long long nbins_total;
+  int32_t mode;          // AccMode
+  int32_t track_counts;
+  unsigned long long* g_lo;
+  long long* g_hi;
+  unsigned long long* g_count;
+  unsigned long long* g_unit;
+  double* g_f64;
+  double* g_stats;
+};
+
+// Launchers (fill_kernels.cu).
+struct LaunchShape {
+  int grid;
+  int block;
+  size_t smem;
+};
+
+int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shape);
+int launch_fill(const FillParams& p, int acc_mode, const LaunchShape& shape, void* stream);
+int launch_reduce(const ReduceParams& r, void* stream);
+int launch_locate(const FillParams& p, long long* out, void* stream);
+int launch_normalize_fx(unsigned long long* g_lo, long long* g_hi, long long nbins, void* stream);
+size_t part_bin_bytes(int acc_mode, int track_counts);
+
+}  // namespace hgb

@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.  Bin indices and counts must match bit for bit; weighted
+bin contents and statistics must agree with the oracle's compensated sums to
+1e-12 of the sum of |terms| (HIST_PREC_FP64 and HIST_PREC_F64ATOMIC)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_13310_gb300 import workloads as W
+from tests.helpers import check_against_oracle, edge_probe_values, gpu_fill, to_device
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2401_13310_gb300 import _build
+    _build.build()
+    from paper_2401_13310_gb300 import binding
+    binding.load()
+    return binding
+
+
+LOCATE_AXES = [
+    W.fixed(100, 0.0, 1.0), W.fixed(1000, -5.0, 5.0), W.fixed(222, -1.0, 1.5),
+    W.fixed(7, -0.3, 0.4), W.fixed(1, 2.0, 3.0), W.fixed(100000, 0.0, 300.0),
+    W.fixed(64, -1e-300, 1e-300), W.fixed(50, 1e15, 1e15 + 1.0), W.fixed(3, -1e300, 1e300),
+    W.variable(W.log_edges(500, 0.0, 3.0)), W.variable([-3.0, -1.0, -0.0, 0.5, 10.0]),
+    W.variable(np.sort(np.random.default_rng(3).normal(0, 1, 20001))),
+]
+
+
+@pytest.mark.parametrize("axis", LOCATE_AXES, ids=lambda a: f"{a['kind']}{a.get('nbins', len(a.get('edges', [])) - 1)}")
+def test_locate_edges_bit_exact(B, axis):
+    """Every threshold, its neighbours, signed zeros, infinities, NaNs,
+    subnormals, huge values: GPU find-bin equals the oracle's."""
+    import torch
+    rng = np.random.default_rng(5)
+    T = B.hist_axis_thresholds(axis)
+    x = edge_probe_values(axis, T, rng)
+    ref = oracle.locate([axis], x.reshape(1, -1))
+    h = B.Hist([axis])
+    try:
+        got = h.locate(to_device(x.reshape(1, -1))).cpu().numpy()
+        torch.cuda.synchronize()
+    finally:
+        h.close()
+    bad = np.flatnonzero(got != ref)
+    assert bad.size == 0, f"{bad.size} mismatches, e.g. x={x[bad[:5]]!r} got {got[bad[:5]]} ref {ref[bad[:5]]}"
+
+
+def test_locate_nd_bit_exact(B):
+    rng = np.random.default_rng(8)
+    axes = [W.fixed(30, -2.0, 2.0), W.variable(np.sort(rng.uniform(-3, 3, 41))), W.fixed(5, 0.0, 1.0)]
+    n = 100_003
+    v = np.empty((3, n))
+    v[0] = rng.normal(0, 1.3, n)
+    v[1] = rng.normal(0, 2, n)
+    v[2] = rng.uniform(-0.2, 1.2, n)
+    v[:, :7] = [[math.nan, -0.0, math.inf, -2.0, 2.0, 1.9999999999999998, -math.inf]] * 3
+    ref = oracle.locate(axes, v)
+    h = B.Hist(axes)
+    try:
+        got = h.locate(to_device(v)).cpu().numpy()
+    finally:
+        h.close()
+    assert np.array_equal(got, ref)
+
+
+def test_cfg1_unit_weights_full_size(B):
+    """1D, 100 fixed bins on [0,1), 2^20 values on [-0.1, 1.1): counts and
+    unit-weight bins bit-exact, statistics within tolerance."""
+    wl = W.cfg1()
+    ref = oracle.fill(wl.axes, wl.values)
+    bins, stats, counts = gpu_fill(wl.axes, wl.values)
+    check_against_oracle(wl.axes, wl.values, None, bins, stats, counts, ref, what="cfg1")
+    assert counts.sum() == wl.n and counts[0] > 0 and counts[-1] > 0
+
+
+SMALL = [("2a", 1_000_003), ("2b", 1_000_003), ("3a", 300_001), ("3b", 300_001)]
+
+
+@pytest.mark.parametrize("name,n", SMALL)
+@pytest.mark.parametrize("prec", ["fp64", "f64atomic"])
+def test_weighted_configs_small(B, name, n, prec):
+    wl = W.CONFIGS[name](n=n)
+    flags = B.HIST_TRACK_COUNTS | (B.HIST_PREC_F64ATOMIC if prec == "f64atomic" else B.HIST_PREC_FP64)
+    ref = oracle.fill(wl.axes, wl.values, wl.weights, threads=4)
+    bins, stats, counts = gpu_fill(wl.axes, wl.values, wl.weights, flags=flags)
+    check_against_oracle(wl.axes, wl.values, wl.weights, bins, stats, counts, ref, RTOL, RTOL,
+                         what=f"cfg{name} {prec}")
+
+
+@pytest.mark.parametrize("name", ["1", "2a", "2b", "3b"])
+def test_fills_accumulate(B, name):
+    """Several fills of slices equal one fill of the whole (Sec. 3.3: running
+    sums combine with the previous bulk); the fixed-point bins are exact
+    integers, so they are bit-identical however the events are split."""
+    wl = W.CONFIGS[name](n=200_001)
+    flags = B.HIST_TRACK_COUNTS
+    one = gpu_fill(wl.axes, wl.values, wl.weights, flags=flags, chunks=1)
+    many = gpu_fill(wl.axes, wl.values, wl.weights, flags=flags, chunks=7)
+    assert np.array_equal(one[0], many[0])
+    assert np.array_equal(one[2], many[2])
+    ref = oracle.fill(wl.axes, wl.values, wl.weights)
+    check_against_oracle(wl.axes, wl.values, wl.weights, *many, ref, RTOL, RTOL, what=f"cfg{name} chunks")
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 33, 1025, 4099])
+def test_ragged_sizes(B, n):
+    rng = np.random.default_rng(n)
+    axes = [W.fixed(1000, -5.0, 5.0)]
+    x = rng.normal(0, 2, n).reshape(1, n)
+    w = rng.uniform(0.5, 1.5, n)
+    ref = oracle.fill(axes, x, w)
+    bins, stats, counts = gpu_fill(axes, x, w, flags=B.HIST_TRACK_COUNTS)
+    check_against_oracle(axes, x, w, bins, stats, counts, ref, RTOL, RTOL, what=f"n={n}")
+
+
+def test_unaligned_columns(B):
+    """Columns that are 8- but not 16-byte aligned take the scalar-load path."""
+    import torch
+    rng = np.random.default_rng(2)
+    n = 10_001
+    axes = [W.fixed(50, -3.0, 3.0), W.variable(np.linspace(-2, 2, 17))]
+    v = rng.normal(0, 1.5, (2, n))
+    w = rng.uniform(0.5, 1.5, n)
+    buf = torch.zeros(2 * n + 1, dtype=torch.float64, device="cuda")
+    buf[1:] = torch.from_numpy(v.reshape(-1)).cuda()
+    wbuf = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    wbuf[1:] = torch.from_numpy(w).cuda()
+    h = B.Hist(axes, B.HIST_TRACK_COUNTS)
+    try:
+        B.hist_fill_bulk(h.h, buf.data_ptr() + 8, wbuf.data_ptr() + 8, n)
+        bins, stats = h.result()
+        counts = h.counts()
+    finally:
+        h.close()
+    ref = oracle.fill(axes, v, w)
+    check_against_oracle(axes, v, w, bins, stats, counts, ref, RTOL, RTOL, what="unaligned")
+
+
+def test_misaligned_pointer_rejected(B):
+    import torch
+    buf = torch.zeros(64, dtype=torch.float64, device="cuda")
+    h = B.Hist([W.fixed(10, 0.0, 1.0)])
+    try:
+        with pytest.raises(B.HistError) as e:
+            B.hist_fill_bulk(h.h, buf.data_ptr() + 4, None, 8)
+        assert e.value.code == B.HIST_ERR_ALIGN
+        with pytest.raises(B.HistError) as e:
+            B.hist_fill_bulk(h.h, 0, None, 8)
+        assert e.value.code == B.HIST_ERR_ARG
+        with pytest.raises(B.HistError) as e:
+            B.hist_fill_bulk(h.h, buf.data_ptr(), None, -1)
+        assert e.value.code == B.HIST_ERR_ARG
+    finally:
+        h.close()
+
+
+def test_specials_and_stat_overflows(B):
+    """NaN / inf coordinates, NaN / inf / zero / out-of-window weights, with
+    and without HIST_STAT_OVERFLOWS."""
+    rng = np.random.default_rng(4)
+    n = 5000
+    x = rng.normal(0, 2, n)
+    w = rng.uniform(0.5, 1.5, n)
+    x[:12] = [math.nan, -math.nan, math.inf, -math.inf, 0.0, -0.0, 5e-324, 1e300, -1e300, 4.999999999999999, -5.0, 5.0]
+    w[20:30] = [0.0, -0.0, 1e-30, 1e30, 300.0, -7.5, 2.0 ** -9, 2.0 ** 8, 2.0 ** -8, -(2.0 ** 8) + 1]
+    axes = [W.fixed(100, -5.0, 5.0)]
+    for so in (False, True):
+        flags = B.HIST_TRACK_COUNTS | (B.HIST_STAT_OVERFLOWS if so else 0)
+        ref = oracle.fill(axes, x.reshape(1, -1), w, stat_overflows=so)
+        bins, stats, counts = gpu_fill(axes, x, w, flags=flags)
+        if not so:
+            check_against_oracle(axes, x, w, bins, stats, counts, ref, RTOL, RTOL, what="specials")
+        else:
+            # the NaN / inf coordinates make the statistics non-finite
+            assert np.array_equal(counts, ref.counts)
+            assert np.isnan(stats[3]) and np.isnan(ref.stats_acc[3])
+    # NaN weight poisons its bin only
+    w2 = w.copy()
+    w2[100] = math.nan
+    ref = oracle.fill(axes, x.reshape(1, -1), w2)
+    bins, stats, counts = gpu_fill(axes, x, w2, flags=B.HIST_TRACK_COUNTS)
+    g = ref.counts.nonzero()[0]
+    assert np.isnan(bins[oracle.locate(axes, x[100:101].reshape(1, 1))[0]])
+    assert np.array_equal(np.isnan(bins), np.isnan(ref.bins_acc))
+
+
+def test_unit_and_weighted_fills_mix(B):
+    """A unit-weight fill followed by a weighted fill of the same histogram."""
+    import torch
+    rng = np.random.default_rng(9)
+    axes = [W.fixed(40, -2.0, 2.0)]
+    x1 = rng.normal(0, 1, 3001).reshape(1, -1)
+    x2 = rng.normal(0, 1, 2001).reshape(1, -1)
+    w2 = rng.uniform(0.5, 1.5, 2001)
+    acc = oracle.Accumulator(axes)
+    acc.fill(x1)
+    acc.fill(x2, w2)
+    ref = acc.result()
+    h = B.Hist(axes, B.HIST_TRACK_COUNTS)
+    try:
+        h.fill(to_device(x1))
+        h.fill(to_device(x2), to_device(w2))
+        bins, stats = h.result()
+        counts = h.counts()
+    finally:
+        h.close()
+    assert np.array_equal(counts, ref.counts)
+    check_against_oracle(axes, None, w2, bins, stats, counts, ref, RTOL, RTOL, what="mixed")
+
+
+def test_result_idempotent_and_reset(B):
+    wl = W.cfg2a(n=50_000)
+    h = B.Hist(wl.axes, B.HIST_TRACK_COUNTS)
+    try:
+        h.fill(to_device(wl.values), to_device(wl.weights))
+        a = h.result()
+        b = h.result()
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        h.reset()
+        z = h.result()
+        assert not z[0].any() and not z[1].any()
+        assert not h.counts().any()
+    finally:
+        h.close()
+
+
+@pytest.mark.parametrize("name", ["2a", "2b", "3a", "3b"])
+def test_weighted_configs_full_size(B, name):
+    """The full 1e8-event configurations in the default launch configuration,
+    against the chunk-parallel oracle on all host cores."""
+    import os
+    wl = W.CONFIGS[name]()
+    ref = oracle.fill(wl.axes, wl.values, wl.weights, threads=os.cpu_count() or 4)
+    bins, stats, counts = gpu_fill(wl.axes, wl.values, wl.weights, flags=B.HIST_TRACK_COUNTS)
+    check_against_oracle(wl.axes, wl.values, wl.weights, bins, stats, counts, ref, RTOL, RTOL,
+                         what=f"cfg{name} full")
