@@ -151,14 +151,36 @@ void build_variable_thresholds(int32_t nbins, const double* edges, int64_t* T) {
   T[nbins + 2] = INT64_MAX;
 }
 
-bool affine_estimate(int32_t nbins, double xmin, double xmax, float* scale, float* offset) {
-  const double s = (double)nbins / (xmax - xmin);
-  const double o = 1.0 - xmin * s;
-  *scale = (float)s;
-  *offset = (float)o;
-  const double X = std::fmax(std::fabs(xmin), std::fabs(xmax));
-  // worst-case estimate error in bins over in-range x is about X * s * 2^-21
-  return nbins < (1 << 22) && std::isfinite(s) && X * s <= std::ldexp(1.0, 19);
+bool affine_estimate(int32_t nbins, double xmin, double xmax, float* scale, float* offset, float* eps) {
+  // The device evaluates v = fl32(xf * s + o) with xf the coordinate
+  // truncated to 24 significant bits, s ~ S = nbins / W_d and o ~ O = 1 - xmin * S
+  // (W_d = fl64(xmax - xmin), the width the formula divides by).  The
+  // binary64 formula gives 1 + q64 with q64 = (x - xmin) * S * (1 + d),
+  // |d| <= 3.01 * 2^-53.  Bound |v - (1 + q64)| over |x| <= X; beyond X the
+  // estimate is more than a bin width outside the range and the clamp to
+  // bin 0 / nbins + 1 decides correctly.
+  const double W = xmax - xmin;
+  const double S = (double)nbins / W;
+  const double O = 1.0 - xmin * S;
+  const float s = (float)S, o = (float)O;
+  *scale = s;
+  *offset = o;
+  *eps = 1.0f;
+  if (!std::isfinite(S) || !std::isfinite(O) || !std::isfinite((double)s) || !std::isfinite((double)o)) return false;
+  if (nbins >= (1 << 21) || S > std::ldexp(1.0, 100) || S < std::ldexp(1.0, -100)) return false;
+  const double X = std::fmax(std::fabs(xmin), std::fabs(xmax)) + W;
+  const double u24 = std::ldexp(1.0, -24), u53 = std::ldexp(1.0, -53);
+  if (X * S >= std::ldexp(1.0, 21) || std::fabs(O) >= std::ldexp(1.0, 21)) return false;
+  const double ds = std::fabs((double)s - S) + u53 * S;                     // |s - exact S|
+  const double dO = std::fabs((double)o - O) + 2 * u53 * (std::fabs(xmin) * S + std::fabs(O));
+  const double e_trunc = X * std::fabs((double)s) * 2 * u24 + std::ldexp(1.0, -126) * std::fabs((double)s);
+  const double e_scale = X * ds;
+  const double e_fma = u24 * (X * std::fabs((double)s) * (1 + 4 * u24) + std::fabs((double)o));
+  const double e_f64 = 4 * u53 * ((double)nbins + 2) + 2 * u53 * ((double)nbins + 2);
+  const double e = 2.0 * (e_trunc + e_scale + dO + e_fma + e_f64);
+  if (!(e < 0.25)) return false;
+  *eps = (float)(e * (1 + 1e-6)) + std::ldexp(1.0f, -40);
+  return true;
 }
 
 }  // namespace hgb

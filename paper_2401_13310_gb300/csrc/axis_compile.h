@@ -20,8 +20,9 @@ int validate_axis(int32_t kind, int32_t nbins, double xmin, double xmax, const d
 void build_fixed_thresholds(int32_t nbins, double xmin, double xmax, int64_t* T);
 void build_variable_thresholds(int32_t nbins, const double* edges, int64_t* T);
 
-// FP32 affine estimate k ~ floor(xf * scale + offset); returns true when its
-// error over in-range coordinates stays well under one bin.
-bool affine_estimate(int32_t nbins, double xmin, double xmax, float* scale, float* offset);
+// FP32 estimate v = xf * scale + offset of 1 + q (q the binary64 quotient of
+// the fixed-width formula) with a proven bound eps on |v - (1 + q)|; returns
+// false when the axis is outside the range where such a bound stays < 1/4.
+bool affine_estimate(int32_t nbins, double xmin, double xmax, float* scale, float* offset, float* eps);
 
 }  // namespace hgb

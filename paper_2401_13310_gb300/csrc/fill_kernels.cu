@@ -8,30 +8,38 @@
 // (Sec. 3.2, two-stage filling), and reduces the statistics in separate
 // kernels (one per statistic).  Here:
 //
-//  * find-bin is integer-only: every axis is a table of exact threshold keys
-//    (see hist_internal.h).  Fixed axes take an FP32 estimate built from the
-//    coordinate's bits with integer operations and correct it by one compare
-//    each way; variable axes binary-search the keys.  No binary64 arithmetic
-//    runs per event (on GB300 the binary64 pipe issues fewer than two
-//    operations per clock per SM, about 1/60 of the FP32 rate).
+//  * find-bin never uses binary64 arithmetic (on GB300 the binary64 pipe
+//    issues under two operations per clock per SM, about 1/60 of the FP32
+//    rate).  Every axis is a table of exact threshold keys (hist_internal.h).
+//    Fixed axes first evaluate the formula in FP32 from the coordinate's bits;
+//    the host proves a bound eps on the distance between that value and the
+//    binary64 one, so whenever the FP32 value is farther than eps from an
+//    integer its floor IS the binary64 bin.  The rare rest (and variable axes)
+//    compare ordered int64 keys against the thresholds.
 //  * weighted bins are summed exactly in fixed point: |w| in the window
 //    [2^(e-1023), 2^(e-1007)) (e = fx_elo) becomes a 64-bit integer multiple
 //    of 2^(e-1065) (truncation error <= 2^-42 |w|), added to a 96-bit
-//    per-block accumulator held as three u32 words in shared memory with
-//    32-bit atomics that propagate carries (u32 shared atomics sustain about
-//    7 per clock per SM, against 0.7-1 for binary64 ones and 1.5 for 64-bit
-//    ones).  The sum is exact and independent of the order of the atomics.
+//    per-block accumulator held as three u32 words in shared memory by 32-bit
+//    atomics that propagate their carries (u32 shared atomics sustain about 7
+//    per clock per SM, against 0.7-1 for binary64 ones and 1.5 for 64-bit
+//    ones).  The sum is exact, so the order of the atomics does not matter.
 //    Other weights take a slow path (binary64 atomic in global memory).
-//  * the statistics terms are formed and summed per thread in FP32
+//  * sum w is not accumulated per event: it equals the sum of the in-range
+//    bin contents, which the host forms exactly from the fixed-point bins.
+//    The other statistics terms are formed and summed per thread in FP32
 //    double-word arithmetic (error-free products with FMA, TwoSum
 //    accumulation), flushed to binary64 every 64 events, reduced across the
-//    block with warp shuffles and written as one partial per block; a second
-//    kernel adds the partials in block order (deterministic).
-//  * per-block bin partials are written to scratch and summed by the same
-//    second kernel, which replaces the grid-wide atomic merge.
+//    block with warp shuffles and written as one partial per block; the
+//    reduce kernel adds the partials in block order (deterministic).
+//  * each thread handles four events per iteration (two coalesced pairs), so
+//    loads and the carry-chained atomics of independent events overlap.
+//  * per-block bin partials go to scratch; the reduce kernel sums them in
+//    slices and merges the exact integer sums with 64-bit atomics.
 //
 // Nothing here is compiled with FMA contraction (-fmad=false); every
-// error-free transformation uses explicit round-to-nearest intrinsics.
+// error-free transformation uses explicit round-to-nearest intrinsics, and
+// rarely-taken binary64 paths live in non-inlined functions so that they are
+// real branches, not predicated code issued for every event.
 
 #include <cuda_runtime.h>
 
@@ -46,39 +54,61 @@ constexpr unsigned long long kMag = 0x7FFFFFFFFFFFFFFFull;
 constexpr unsigned long long kExpInf = 0x7FF0000000000000ull;
 constexpr unsigned long long kMant = 0x000FFFFFFFFFFFFFull;
 constexpr unsigned long long kHidden = 0x0010000000000000ull;
-constexpr int kFlushIters = 32;  // two events per iteration: flush every 64 events
+#ifndef HGB_MIN_BLOCKS
+#define HGB_MIN_BLOCKS 1
+#endif
+constexpr int kFlushIters = 32;  // two events per iteration: 64 events between binary64 flushes
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
 
 __device__ __forceinline__ unsigned long long dbits(double x) {
   return (unsigned long long)__double_as_longlong(x);
 }
 
+
 // Ordered key of a binary64: compares like the double; -0 and +0 both map to
 // 0; every NaN maps to kNanKey, above +inf (the overflow bin).
 __device__ __forceinline__ long long key_of(unsigned long long b) {
-  unsigned long long mag = b & kMag;
+  const unsigned long long mag = b & kMag;
   long long k = (long long)mag;
   k = ((long long)b < 0) ? -k : k;
   return (mag > kExpInf) ? kNanKey : k;
 }
 
-// FP32 value of a binary64 with the mantissa truncated to 23 bits, built with
-// integer operations (a binary64 -> FP32 conversion would use the binary64
-// pipe).  |x| < 2^-126 gives +-0, |x| >= 2^128 (and inf/NaN) gives +-2^127.
+// FP32 value of a binary64 with the significand truncated to 24 bits, built
+// with integer operations (a binary64 -> FP32 conversion would use the
+// binary64 pipe).  |x| < 2^-126 gives +-0, |x| >= 2^128 (and inf/NaN) +-2^127.
 __device__ __forceinline__ float est_float(unsigned long long b) {
-  unsigned hi = (unsigned)(b >> 32);
-  unsigned sgn = hi & 0x80000000u;
-  unsigned e = (hi >> 20) & 0x7FFu;
+  const unsigned hi = (unsigned)(b >> 32);
+  const unsigned sgn = hi & 0x80000000u;
+  const unsigned e = (hi >> 20) & 0x7FFu;
   unsigned f = ((unsigned)(b >> 29) - 0xC0000000u) & 0x7FFFFFFFu;
   f = (e < 897u) ? 0u : f;
   f = (e > 1150u) ? 0x7F000000u : f;
   return __uint_as_float(f | sgn);
 }
 
+// The same value without the saturation: only meaningful when in_f32(b).
+__device__ __forceinline__ float hi24(unsigned long long b) {
+  const unsigned hi = (unsigned)(b >> 32);
+  return __uint_as_float((((unsigned)(b >> 29) - 0xC0000000u) & 0x7FFFFFFFu) | (hi & 0x80000000u));
+}
+
+// Biased exponent field of a binary64, in place (bits 20..30 of the high word).
+__device__ __forceinline__ unsigned exp_field(unsigned long long b) { return (unsigned)(b >> 32) & 0x7FF00000u; }
+
+// |x| in [2^-126, 2^128): hi24 is exact truncation (zeros, subnormals,
+// huge values, inf and NaN are all outside).
+__device__ __forceinline__ bool in_f32(unsigned ef) { return ef - 0x38100000u < 0x0FE00000u; }
+
+// |x| in [2^-40, 2^40): the double-word statistics path is accurate and no
+// product of statistics terms over- or underflows FP32.
+__device__ __forceinline__ bool in_ff(unsigned ef) { return ef - (983u << 20) < (80u << 20); }
+
 // Largest k in [0, nkeys) with T[k] <= key (T[0] = INT64_MIN).
 __device__ __forceinline__ int bsearch_keys(const long long* T, int nkeys, long long key) {
   int base = 0, len = nkeys;
   while (len > 1) {
-    int half = len >> 1;
+    const int half = len >> 1;
     base = (T[base + half] <= key) ? base + half : base;
     len -= half;
   }
@@ -87,22 +117,38 @@ __device__ __forceinline__ int bsearch_keys(const long long* T, int nkeys, long 
 
 __device__ __forceinline__ float bf16_to_f32(uint16_t h) { return __uint_as_float((unsigned)h << 16); }
 
-// Bin of one coordinate on one axis (Sec. 3.1 step 1), exact.
-__device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T, unsigned long long b) {
+// Exact bin from the thresholds, starting at a guess k0 in [0, nbins+1]:
+// one step each way, then a full binary search if still not bracketed.
+__device__ __noinline__ int locate_exact(const long long* T, int nbins, int k, unsigned long long b) {
   const long long key = key_of(b);
-  if (a.mode == LOC_AFFINE) {
-    float v = fmaf(est_float(b), a.scale, a.offset);
-    v = fminf(fmaxf(v, 0.0f), (float)(a.nbins + 1));
-    int k = (int)(__float_as_uint(__fadd_rd(v, 12582912.0f)) - 0x4B400000u);
-    if (key < T[k]) {
-      --k;
-      if (key < T[k]) k = bsearch_keys(T, a.nbins + 2, key);
-    } else if (key >= T[k + 1]) {
-      ++k;
-      if (key >= T[k + 1]) k = bsearch_keys(T, a.nbins + 2, key);
-    }
-    return k;
+  if (key < T[k]) {
+    --k;
+    if (key < T[k]) k = bsearch_keys(T, nbins + 2, key);
+  } else if (key >= T[k + 1]) {
+    ++k;
+    if (key >= T[k + 1]) k = bsearch_keys(T, nbins + 2, key);
   }
+  return k;
+}
+
+// Bin of one coordinate on one axis (Sec. 3.1 step 1), exact.
+// xf: the coordinate as FP32 (hi24), valid when in_f32 of its exponent field.
+__device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T, unsigned long long b, float xf,
+                                           bool f32ok) {
+  if (a.mode == LOC_AFFINE) {
+    // v estimates 1 + q; t = floor(v) + 1.5*2^23 exactly while |v| < 2^22.
+    // Outside that range either v is an integer (fr = 0, not sure) or the
+    // clamp below puts k in the right flow bin.
+    const float v = __fmaf_rn(xf, a.scale, a.offset);
+    const float t = __fadd_rd(v, kMagic);
+    int k = __float_as_int(t) - 0x4B400000;
+    const float fr = __fsub_rn(v, __fsub_rn(t, kMagic));
+    const bool sure = f32ok && (fabsf(__fsub_rn(fr, 0.5f)) < 0.5f - a.eps);
+    k = min(max(k, 0), a.nbins + 1);
+    if (sure) return k;
+    return locate_exact(T, a.nbins, k, b);
+  }
+  const long long key = key_of(b);
   if (a.mode == LOC_LEARNED) {
     // Piecewise-linear index model: k^ = base[s] + th0[s] + th1[s] * t,
     // t = fractional position in segment s; then an exact search inside the
@@ -110,16 +156,14 @@ __device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T,
     const LearnedDev& m = a.lm;
     float u = (est_float(b) - m.u0) * m.u_scale;
     u = fminf(fmaxf(u, 0.0f), (float)m.nseg - 0.5f);
-    int s = (int)u;
-    float t = u - (float)s;
-    float kh = (float)m.base[s] + bf16_to_f32(m.th0[s]) + bf16_to_f32(m.th1[s]) * t;
-    int k0 = (int)floorf(kh + 0.5f);
+    const int s = (int)u;
+    const float tt = u - (float)s;
+    const float kh = (float)m.base[s] + bf16_to_f32(m.th0[s]) + bf16_to_f32(m.th1[s]) * tt;
+    const int k0 = (int)floorf(kh + 0.5f);
     int lo = k0 - m.window, hi = k0 + m.window;
     lo = lo < 0 ? 0 : lo;
     hi = hi > a.nbins + 1 ? a.nbins + 1 : hi;
-    if (lo <= hi && T[lo] <= key && key < T[hi + 1]) {
-      return lo + bsearch_keys(T + lo, hi - lo + 1, key);
-    }
+    if (lo <= hi && T[lo] <= key && key < T[hi + 1]) return lo + bsearch_keys(T + lo, hi - lo + 1, key);
     return bsearch_keys(T, a.nbins + 2, key);
   }
   return bsearch_keys(T, a.nbins + 2, key);
@@ -131,34 +175,22 @@ struct FF {
   float hi, lo;
 };
 
-// Split a binary64 with |x| in [2^-40, 2^40) or x = +-0 into hi + lo: hi
-// holds the leading 24 significant bits, lo the remaining 29 rounded to 24
-// (|x - hi - lo| <= 2^-48 |x|).  Integer operations and one u32 -> f32
-// conversion only.
-__device__ __forceinline__ FF ff_from_bits(unsigned long long b) {
-  unsigned hi32 = (unsigned)(b >> 32);
-  unsigned sgn = hi32 & 0x80000000u;
-  unsigned e = (hi32 >> 20) & 0x7FFu;
-  unsigned fh = (((unsigned)(b >> 29) - 0xC0000000u) & 0x7FFFFFFFu) | sgn;
-  float lo = __fmul_rn(__uint2float_rn((unsigned)b & 0x1FFFFFFFu), __uint_as_float((e - 948u) << 23));
-  unsigned fl = __float_as_uint(lo) | sgn;
-  const bool zero = (b & kMag) == 0;
+// hi + lo with hi = the leading 24 significant bits of x (hi24) and lo the
+// remaining 29 bits rounded to 24 (|x - hi - lo| <= 2^-48 |x|), for |x| in
+// [2^-40, 2^40).  Integer operations and one u32 -> f32 conversion only.
+__device__ __forceinline__ FF ff_split(unsigned long long b, float hi) {
+  const unsigned hi32 = (unsigned)(b >> 32);
+  const float scale = __uint_as_float(((hi32 >> 20) - 948u) << 23);  // 2^(e-1075), sign bit shifted out
+  const float lo = __fmul_rn(__uint2float_rn((unsigned)b & 0x1FFFFFFFu), scale);
   FF r;
-  r.hi = zero ? 0.0f : __uint_as_float(fh);
-  r.lo = zero ? 0.0f : __uint_as_float(fl);
+  r.hi = hi;
+  r.lo = __uint_as_float(__float_as_uint(lo) | (hi32 & 0x80000000u));
   return r;
 }
 
-// True when |x| is in [2^-40, 2^40) or x = +-0: the double-word path is exact
-// enough and no product of statistics terms over- or underflows FP32.
-__device__ __forceinline__ bool ff_ok(unsigned long long b) {
-  unsigned e = (unsigned)(b >> 52) & 0x7FFu;
-  return (e - 983u) < 80u || (b & kMag) == 0;
-}
-
-// a * b as an unevaluated sum p + e (the a.lo * b.lo term, <= 2^-48 |ab|, is dropped).
+// a * b as an unevaluated sum p + e (a.lo * b.lo, <= 2^-48 |ab|, is dropped).
 __device__ __forceinline__ FF ff_mul(FF a, FF b) {
-  float p = __fmul_rn(a.hi, b.hi);
+  const float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
@@ -168,65 +200,61 @@ __device__ __forceinline__ FF ff_mul(FF a, FF b) {
 // s += t with TwoSum on the high parts (Knuth): the rounding error of
 // s.hi + t.hi is recovered exactly and folded into s.lo.
 __device__ __forceinline__ void ff_acc(FF& s, FF t) {
-  float sum = __fadd_rn(s.hi, t.hi);
-  float bp = __fsub_rn(sum, s.hi);
-  float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(sum, bp)), __fsub_rn(t.hi, bp));
+  const float sum = __fadd_rn(s.hi, t.hi);
+  const float bp = __fsub_rn(sum, s.hi);
+  const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(sum, bp)), __fsub_rn(t.hi, bp));
   s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, err));
   s.hi = sum;
 }
 
-__device__ __forceinline__ double ff_to_double(FF s) { return __dadd_rn((double)s.hi, (double)s.lo); }
+// Exact FP32 -> binary64 widening with integer operations (the conversion
+// instruction runs on the binary64 pipe at half its add rate).  Normal
+// values and zeros only; the double-word parts here are never subnormal.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long mag =
+      ((unsigned long long)(((u >> 23) & 0xFFu) + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)(((u & 0x7FFFFFFFu) == 0u) ? sgn : (sgn | mag)));
+}
+
+__device__ __forceinline__ double ff_to_double(FF s) {
+  return __dadd_rn(f32_to_f64_bits(s.hi), f32_to_f64_bits(s.lo));
+}
 
 // ---------------------------------------------------------------- fixed point
 
 // Weight -> signed fixed-point integer V = trunc(|w| * 2^(1065 - elo)) * sign.
-// Returns false (slow path) unless w = +-0 or its biased exponent is in
-// [elo, elo + 16).  |V| < 2^58.
+// Returns false (slow path: zeros, tiny, huge, inf, NaN) unless the biased
+// exponent is in [elo, elo + 16).  With the significand M (hidden bit
+// included) pre-shifted left by 10, V = (M << 10) >> (20 - (e - elo)) --
+// always a right shift by 5..20, so no bit of an in-window weight above
+// 2^-42 |w| is lost.  |V| < 2^58.
 __device__ __forceinline__ bool fx_of(unsigned long long wb, int elo, long long* V) {
-  const unsigned long long mag = wb & kMag;
-  if (mag == 0) {
-    *V = 0;
-    return true;
-  }
-  const unsigned e = (unsigned)(wb >> 52) & 0x7FFu;
-  if (e - (unsigned)elo >= 16u) return false;
-  const unsigned long long M = (wb & kMant) | kHidden;
-  const int s = (int)e - elo - 10;
-  const unsigned long long U = (s >= 0) ? (M << s) : (M >> (-s));
+  const unsigned rel = ((unsigned)(wb >> 52) & 0x7FFu) - (unsigned)elo;
+  const unsigned long long M10 = ((wb << 10) & (kMant << 10)) | (kHidden << 10);
+  const unsigned long long U = M10 >> ((20u - rel) & 63u);
   *V = ((long long)wb < 0) ? -(long long)U : (long long)U;
-  return true;
-}
-
-// a[2]:a[1]:a[0] += V (96-bit two's complement) with 32-bit shared atomics.
-// Each atomic returns the old word, so the carry it produced is known
-// exactly; the final words equal the exact sum modulo 2^96 for any
-// interleaving of concurrent adds.
-__device__ __forceinline__ void smem_add96(unsigned* a, long long V) {
-  const unsigned v0 = (unsigned)V;
-  const unsigned v1 = (unsigned)((unsigned long long)V >> 32);
-  const unsigned v2 = (unsigned)(V >> 63);
-  const unsigned o0 = atomicAdd(&a[0], v0);
-  const unsigned c0 = (o0 + v0 < o0) ? 1u : 0u;
-  const unsigned a1 = v1 + c0;
-  unsigned c1 = (a1 < c0) ? 1u : 0u;
-  const unsigned o1 = atomicAdd(&a[1], a1);
-  c1 |= (o1 + a1 < o1) ? 1u : 0u;
-  const unsigned a2 = v2 + c1;
-  if (a2 != 0u) atomicAdd(&a[2], a2);
+  return rel < 16u;
 }
 
 // ---------------------------------------------------------------- statistics
 
-// Per-thread statistics accumulator.  Slot numbering (stats[k]):
-// 1 sum w, 2 sum w^2, 3 sum wx, 4 sum wx^2, 5 sum wy, 6 sum wy^2, 7 sum wxy,
-// 8 sum wz, 9 sum wz^2, 10 sum wxz, 11 sum wyz.  Slot 0 (the entry count) is
-// added on the host.
+// Statistics slots (stats[k]): 1 sum w, 2 sum w^2, 3 sum wx, 4 sum wx^2,
+// 5 sum wy, 6 sum wy^2, 7 sum wxy, 8 sum wz, 9 sum wz^2, 10 sum wxz,
+// 11 sum wyz.  Slot 0 (entries) and slot 1 (and slot 2 for unit weights)
+// come from the host: the entry count and the in-range bin contents.
+template <int NDIM>
+struct NStats {
+  static constexpr int NS = NDIM == 1 ? 5 : (NDIM == 2 ? 8 : 12);
+};
+
 template <int NDIM, bool UNIT>
 struct StatAcc {
-  static constexpr int NS = NDIM == 1 ? 5 : (NDIM == 2 ? 8 : 12);
-  FF s[NS];
-  double d[NS];
-  unsigned cnt;  // unit weights: in-range entries (sum w = sum w^2)
+  static constexpr int NS = NStats<NDIM>::NS;
+  FF s[NS];      // double-word partial sums of slots 3.. (slots 0-2 unused)
+  double d[NS];  // binary64 sums, refreshed every flush
+  double w2;     // sum w^2, one binary64 FMA per event (weighted fills)
 
   __device__ __forceinline__ void init() {
 #pragma unroll
@@ -235,13 +263,12 @@ struct StatAcc {
       s[k].lo = 0.0f;
       d[k] = 0.0;
     }
-    cnt = 0;
+    w2 = 0.0;
   }
 
-  // Double-word path: coordinates (and weight) already split.
-  __device__ __forceinline__ void add_ff(const FF* c, FF W) {
+  // Coordinates (and weight) already split; wb = the weight's bits.
+  __device__ __forceinline__ void add_ff(const FF* c, FF W, unsigned long long wb) {
     if (UNIT) {
-      ++cnt;
       ff_acc(s[3], c[0]);
       ff_acc(s[4], ff_mul(c[0], c[0]));
       if (NDIM >= 2) {
@@ -256,8 +283,9 @@ struct StatAcc {
         ff_acc(s[11], ff_mul(c[1], c[2]));
       }
     } else {
-      ff_acc(s[1], W);
-      ff_acc(s[2], ff_mul(W, W));
+      // the binary64 pipe is otherwise idle: w^2 costs one issue slot there
+      const double w = __longlong_as_double((long long)wb);
+      w2 = __fma_rn(w, w, w2);
       const FF WX = ff_mul(W, c[0]);
       ff_acc(s[3], WX);
       ff_acc(s[4], ff_mul(WX, c[0]));
@@ -277,52 +305,61 @@ struct StatAcc {
     }
   }
 
-  // binary64 path (rare: coordinates or weight outside the double-word range,
-  // non-finite values with HIST_STAT_OVERFLOWS).  Terms rounded as in the
-  // definition: w*x*x = (w*x)*x.
-  __device__ __forceinline__ void add_f64(const double* c, double w) {
-    const double wx = __dmul_rn(w, c[0]);
-    d[1] = __dadd_rn(d[1], w);
-    d[2] = __dadd_rn(d[2], __dmul_rn(w, w));
-    d[3] = __dadd_rn(d[3], wx);
-    d[4] = __dadd_rn(d[4], __dmul_rn(wx, c[0]));
-    if (NDIM >= 2) {
-      const double wy = __dmul_rn(w, c[1]);
-      d[5] = __dadd_rn(d[5], wy);
-      d[6] = __dadd_rn(d[6], __dmul_rn(wy, c[1]));
-      d[7] = __dadd_rn(d[7], __dmul_rn(wx, c[1]));
-      if (NDIM >= 3) {
-        const double wz = __dmul_rn(w, c[2]);
-        d[8] = __dadd_rn(d[8], wz);
-        d[9] = __dadd_rn(d[9], __dmul_rn(wz, c[2]));
-        d[10] = __dadd_rn(d[10], __dmul_rn(wx, c[2]));
-        d[11] = __dadd_rn(d[11], __dmul_rn(wy, c[2]));
-      }
-    }
-  }
-
   __device__ __forceinline__ void flush() {
 #pragma unroll
-    for (int k = 1; k < NS; ++k) {
+    for (int k = 3; k < NS; ++k) {
       d[k] = __dadd_rn(d[k], ff_to_double(s[k]));
       s[k].hi = 0.0f;
       s[k].lo = 0.0f;
     }
-    if (UNIT) {
-      d[1] = __dadd_rn(d[1], (double)cnt);
-      d[2] = __dadd_rn(d[2], (double)cnt);
-      cnt = 0;
-    }
   }
 };
 
-// Block-wide sum of the per-thread binary64 statistics (warp shuffles, then
-// one pass over the warps in order); thread 0 writes the block's partial.
+// binary64 statistics terms of one event, rounded as in the definition
+// (w*x*x = (w*x)*x), added into d[2..NS).  Kept out of line: it runs only
+// for coordinates or weights outside the double-word range and for the
+// binary64-atomic mode.
+template <int NDIM>
+__device__ __noinline__ void stat_f64(double* d, const unsigned long long* cb, unsigned long long wb) {
+  double c[NDIM];
+#pragma unroll
+  for (int k = 0; k < NDIM; ++k) c[k] = __longlong_as_double((long long)cb[k]);
+  const double w = __longlong_as_double((long long)wb);
+  const double wx = __dmul_rn(w, c[0]);
+  d[2] = __dadd_rn(d[2], __dmul_rn(w, w));
+  d[3] = __dadd_rn(d[3], wx);
+  d[4] = __dadd_rn(d[4], __dmul_rn(wx, c[0]));
+  if (NDIM >= 2) {
+    const double wy = __dmul_rn(w, c[1]);
+    d[5] = __dadd_rn(d[5], wy);
+    d[6] = __dadd_rn(d[6], __dmul_rn(wy, c[1]));
+    d[7] = __dadd_rn(d[7], __dmul_rn(wx, c[1]));
+    if (NDIM >= 3) {
+      const double wz = __dmul_rn(w, c[2]);
+      d[8] = __dadd_rn(d[8], wz);
+      d[9] = __dadd_rn(d[9], __dmul_rn(wz, c[2]));
+      d[10] = __dadd_rn(d[10], __dmul_rn(wx, c[2]));
+      d[11] = __dadd_rn(d[11], __dmul_rn(wy, c[2]));
+    }
+  }
+}
+
+// Slow-path bin update: binary64 atomic into the global slow words.
+__device__ __noinline__ void slow_bin(double* g_f64, long long g, unsigned long long wb) {
+  atomicAdd(&g_f64[g], __longlong_as_double((long long)wb));
+}
+
+__device__ __noinline__ void f64_bin(double* bins, long long slot, unsigned long long wb) {
+  atomicAdd(&bins[slot], __longlong_as_double((long long)wb));
+}
+
+// Block-wide sum of per-thread binary64 statistics (warp shuffles, then the
+// warps in order); thread k < kMaxStats writes slot k of the block partial.
 template <int NS>
-__device__ __forceinline__ void block_reduce_stats(double* d, double* out, double* sred) {
+__device__ __forceinline__ void block_reduce_stats(const double* d, double* out, double* sred) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 #pragma unroll
-  for (int k = 1; k < NS; ++k) {
+  for (int k = 2; k < NS; ++k) {
     double v = d[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
@@ -332,7 +369,7 @@ __device__ __forceinline__ void block_reduce_stats(double* d, double* out, doubl
   if (threadIdx.x < kMaxStats) {
     const int k = threadIdx.x;
     double v = 0.0;
-    if (k >= 1 && k < NS)
+    if (k >= 2 && k < NS)
       for (int wi = 0; wi < nwarps; ++wi) v = __dadd_rn(v, sred[wi * kMaxStats + k]);
     out[k] = v;
   }
@@ -340,234 +377,283 @@ __device__ __forceinline__ void block_reduce_stats(double* d, double* out, doubl
 
 // ---------------------------------------------------------------- loads
 
-__device__ __forceinline__ void load2(const double* __restrict__ p, long long i, bool vec, double& a,
-                                      double& b) {
-  if (vec) {
-    const double2 v = __ldcs(reinterpret_cast<const double2*>(p + i));
+// Two consecutive binary64 values as raw bits (no double-typed value ever
+// flows through the hot loop, so nothing can be scheduled on the binary64
+// pipe by accident).
+__device__ __forceinline__ void load_pair(const double* __restrict__ p, long long i, bool vec, bool two,
+                                          unsigned long long& a, unsigned long long& b) {
+  const unsigned long long* q = reinterpret_cast<const unsigned long long*>(p);
+  if (vec && two) {
+    const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(q + i));
     a = v.x;
     b = v.y;
   } else {
-    a = __ldcs(p + i);
-    b = __ldcs(p + i + 1);
+    a = __ldcs(q + i);
+    b = two ? __ldcs(q + i + 1) : 0ull;
   }
 }
 
 // ---------------------------------------------------------------- fill kernel
 
-struct SmemLayout {
-  long long* keys;
-  unsigned* bins;
-};
-
-// One event: locate on every axis, accumulate into the bins, update the
-// statistics.  SMEM selects per-block shared bins vs global atomics.
+// Per-thread state of one fill launch and the three steps for one event.
 template <int NDIM, int ACC, bool SMEM>
-__device__ __forceinline__ void do_event(const FillParams& p, const long long* const* Tax, unsigned* sbins,
-                                         double* sbins_f64, const double* c, double w,
-                                         StatAcc<NDIM, ACC == ACC_UNIT>& st, int stride1, int stride2) {
-  unsigned long long cb[NDIM];
-  int k[NDIM];
-  bool in_range = true;
-#pragma unroll
-  for (int d = 0; d < NDIM; ++d) {
-    cb[d] = dbits(c[d]);
-    k[d] = locate_axis(p.ax[d], Tax[d], cb[d]);
-    in_range = in_range && (k[d] >= 1) && (k[d] <= p.ax[d].nbins);
-  }
-  long long g = k[0];
-  if (NDIM >= 2) g += (long long)k[1] * stride1;
-  if (NDIM >= 3) g += (long long)k[2] * stride2;
+struct Filler {
+  static constexpr bool UNIT = (ACC == ACC_UNIT);
+  static constexpr int NS = NStats<NDIM>::NS;
+  const FillParams& p;
+  const long long* Tax[NDIM];
+  unsigned* sbins;
+  double* sbins_f64;
+  int stride1, stride2;
+  StatAcc<NDIM, UNIT> st;
+  double* slow;  // binary64 statistics of slow-path events (local memory)
 
-  const unsigned long long wb = dbits(w);
-  // ---- step 2: the bin
-  if (ACC == ACC_UNIT) {
-    if (SMEM)
-      atomicAdd(&sbins[g], 1u);
-    else
-      atomicAdd(&p.g_unit[g], 1ull);
-  } else if (ACC == ACC_FX) {
-    long long V;
-    if (fx_of(wb, p.fx_elo, &V)) {
-      if (SMEM) {
-        if (V != 0) smem_add96(&sbins[4 * g], V);
-        if (p.track_counts) atomicAdd(&sbins[4 * g + 3], 1u);
-      } else {
-        if (V != 0) {
+  __device__ __forceinline__ Filler(const FillParams& pp) : p(pp) {}
+
+  __device__ __forceinline__ void event(const unsigned long long* cb, unsigned long long wb) {
+    // ---- step 1: the bin on every axis, linearised x fastest
+    float xf[NDIM];
+    unsigned ef[NDIM];
+    long long g = 0;
+    bool inr = true;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+      ef[d] = exp_field(cb[d]);
+      xf[d] = hi24(cb[d]);
+      const int k = locate_axis(p.ax[d], Tax[d], cb[d], xf[d], in_f32(ef[d]));
+      inr = inr && ((unsigned)(k - 1) < (unsigned)p.ax[d].nbins);
+      g += (long long)k * (d == 0 ? 1 : (d == 1 ? stride1 : stride2));
+    }
+    // ---- step 2: the bin content
+    bool w_ok = true;
+    if (UNIT) {
+      if (SMEM)
+        atomicAdd(&sbins[g], 1u);
+      else
+        atomicAdd(&p.g_unit[g], 1ull);
+    } else if (ACC == ACC_FX) {
+      long long V;
+      w_ok = fx_of(wb, p.fx_elo, &V);
+      if (!w_ok) {
+        slow_bin(p.g_f64, g, wb);
+      } else if (V != 0) {
+        if (SMEM) {
+          // 96-bit add with carries: each atomic returns the old word, so the
+          // carry it produced is known exactly whatever the interleaving
+          unsigned* a = &sbins[4 * g];
+          const unsigned v0 = (unsigned)V;
+          const unsigned o0 = atomicAdd(a, v0);
+          const unsigned c0 = (o0 + v0 < o0) ? 1u : 0u;
+          const unsigned a1 = (unsigned)((unsigned long long)V >> 32) + c0;
+          const unsigned c1a = (a1 < c0) ? 1u : 0u;
+          const unsigned o1 = atomicAdd(a + 1, a1);
+          const unsigned c1 = c1a | ((o1 + a1 < o1) ? 1u : 0u);
+          const unsigned a2 = (unsigned)(V >> 63) + c1;
+          if (a2 != 0u) atomicAdd(a + 2, a2);
+        } else {
           atomicAdd(&p.g_lo[g], (unsigned long long)(unsigned)V);
           atomicAdd(reinterpret_cast<unsigned long long*>(&p.g_hi[g]), (unsigned long long)(V >> 32));
         }
-        if (p.track_counts) atomicAdd(&p.g_count[g], 1ull);
       }
-    } else {
-      atomicAdd(&p.g_f64[g], w);
       if (p.track_counts) {
         if (SMEM)
           atomicAdd(&sbins[4 * g + 3], 1u);
         else
           atomicAdd(&p.g_count[g], 1ull);
       }
+    } else {  // ACC_F64: the paper's binary64 atomics
+      if (SMEM) {
+        f64_bin(sbins_f64, 2 * g, wb);
+        if (p.track_counts) f64_bin(sbins_f64, 2 * g + 1, 0x3FF0000000000000ull);
+      } else {
+        f64_bin(p.g_f64, g, wb);
+        if (p.track_counts) atomicAdd(&p.g_count[g], 1ull);
+      }
     }
-  } else if (ACC == ACC_F64) {
-    if (SMEM) {
-      atomicAdd(&sbins_f64[2 * g], w);
-      if (p.track_counts) atomicAdd(&sbins_f64[2 * g + 1], 1.0);
+    // ---- step 3: statistics
+    if (!(inr || p.stat_overflows)) return;
+    bool fast = (ACC != ACC_F64) && w_ok;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) fast = fast && in_ff(ef[d]);
+    if (fast) {
+      FF cf[NDIM];
+#pragma unroll
+      for (int d = 0; d < NDIM; ++d) cf[d] = ff_split(cb[d], xf[d]);
+      FF W;
+      if (UNIT) {
+        W.hi = 1.0f;
+        W.lo = 0.0f;
+      } else {
+        W = ff_split(wb, hi24(wb));  // in-window weights lie in the double-word range
+      }
+      st.add_ff(cf, W, wb);
     } else {
-      atomicAdd(&p.g_f64[g], w);
-      if (p.track_counts) atomicAdd(&p.g_count[g], 1ull);
+      stat_f64<NDIM>(slow, cb, wb);
     }
   }
-  // ---- step 3: statistics
-  if (!(in_range || p.stat_overflows)) return;
-  if (ACC == ACC_F64) {
-    st.add_f64(c, w);
-    return;
-  }
-  bool fast = true;
-#pragma unroll
-  for (int d = 0; d < NDIM; ++d) fast = fast && ff_ok(cb[d]);
-  if (ACC == ACC_FX) fast = fast && ff_ok(wb);
-  if (fast) {
-    FF cf[NDIM];
-#pragma unroll
-    for (int d = 0; d < NDIM; ++d) cf[d] = ff_from_bits(cb[d]);
-    FF W;
-    if (ACC == ACC_UNIT) {
-      W.hi = 1.0f;
-      W.lo = 0.0f;
-    } else {
-      W = ff_from_bits(wb);
-    }
-    st.add_ff(cf, W);
+};
+
+// Two consecutive binary64 values as raw bits (no double-typed value ever
+// flows through the hot loop, so nothing is scheduled on the binary64 pipe
+// by accident).
+template <bool VEC>
+__device__ __forceinline__ void load_pair(const double* __restrict__ p, long long i, unsigned long long& a,
+                                          unsigned long long& b) {
+  const unsigned long long* q = reinterpret_cast<const unsigned long long*>(p);
+  if (VEC) {
+    const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(q + i));
+    a = v.x;
+    b = v.y;
   } else {
-    st.add_f64(c, ACC == ACC_UNIT ? 1.0 : w);
+    a = __ldcs(q + i);
+    b = __ldcs(q + i + 1);
+  }
+}
+
+template <int NDIM, int ACC, bool SMEM, bool VEC>
+__device__ __forceinline__ void fill_pairs(Filler<NDIM, ACC, SMEM>& f, long long npairs) {
+  const FillParams& p = f.p;
+  const long long nthreads = (long long)gridDim.x * blockDim.x;
+  int iters = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < npairs; q += nthreads) {
+    const long long i = 2 * q;
+    unsigned long long c0[NDIM], c1[NDIM], w0 = 0x3FF0000000000000ull, w1 = 0x3FF0000000000000ull;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) load_pair<VEC>(p.col[d], i, c0[d], c1[d]);
+    if (ACC != ACC_UNIT) load_pair<VEC>(p.w, i, w0, w1);
+    f.event(c0, w0);
+    f.event(c1, w1);
+    if (++iters == kFlushIters) {
+      f.st.flush();
+      iters = 0;
+    }
   }
 }
 
 template <int NDIM, int ACC, bool SMEM>
-__global__ void __launch_bounds__(256) k_fill(const FillParams p) {
+__global__ void __launch_bounds__(256, HGB_MIN_BLOCKS) k_fill(const FillParams p) {
+  constexpr bool UNIT = (ACC == ACC_UNIT);
+  constexpr int NS = NStats<NDIM>::NS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nkeys = p.table_keys;
   long long* skeys = reinterpret_cast<long long*>(smem_raw);
   unsigned char* after_keys = smem_raw + (((size_t)nkeys * 8 + 15) & ~(size_t)15);
-  unsigned* sbins = reinterpret_cast<unsigned*>(after_keys);
-  double* sbins_f64 = reinterpret_cast<double*>(after_keys);
   __shared__ double sred[8 * kMaxStats];
 
-  // stage threshold keys
+  Filler<NDIM, ACC, SMEM> f(p);
+  f.sbins = reinterpret_cast<unsigned*>(after_keys);
+  f.sbins_f64 = reinterpret_cast<double*>(after_keys);
   for (int i = threadIdx.x; i < nkeys; i += blockDim.x) skeys[i] = p.T_concat[i];
-  const long long* Tax[NDIM];
 #pragma unroll
-  for (int d = 0; d < NDIM; ++d) Tax[d] = (p.ax[d].smem_off >= 0) ? skeys + p.ax[d].smem_off : p.ax[d].T;
-
+  for (int d = 0; d < NDIM; ++d) f.Tax[d] = (p.ax[d].smem_off >= 0) ? skeys + p.ax[d].smem_off : p.ax[d].T;
   const int nb = (int)p.nbins_total;
   if (SMEM) {
-    const int words = (ACC == ACC_UNIT) ? nb : (ACC == ACC_FX ? 4 * nb : 4 * nb);
-    for (int i = threadIdx.x; i < words; i += blockDim.x) sbins[i] = 0u;
+    const int words = UNIT ? nb : 4 * nb;
+    for (int i = threadIdx.x; i < words; i += blockDim.x) f.sbins[i] = 0u;
   }
+  f.stride1 = p.ax[0].nbins + 2;
+  f.stride2 = NDIM >= 2 ? f.stride1 * (p.ax[1].nbins + 2) : 0;
+  f.st.init();
+  double slow[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) slow[k] = 0.0;
+  f.slow = slow;
   __syncthreads();
 
-  const int stride1 = p.ax[0].nbins + 2;
-  const int stride2 = NDIM >= 2 ? stride1 * (p.ax[1].nbins + 2) : 0;
-
-  StatAcc<NDIM, ACC == ACC_UNIT> st;
-  st.init();
-
+  // every full pair of events, then the odd last event
   const long long n = p.n;
-  const long long tstride = 2LL * gridDim.x * blockDim.x;
-  const bool vec = p.aligned != 0;
-  int iters = 0;
-  for (long long i = 2LL * (blockIdx.x * (long long)blockDim.x + threadIdx.x); i < n; i += tstride) {
-    double c0[NDIM], c1[NDIM], w0 = 1.0, w1 = 1.0;
-    const bool pair = (i + 1 < n);
-    if (pair) {
+  if (p.aligned)
+    fill_pairs<NDIM, ACC, SMEM, true>(f, n >> 1);
+  else
+    fill_pairs<NDIM, ACC, SMEM, false>(f, n >> 1);
+  if ((n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
+    unsigned long long c[NDIM];
 #pragma unroll
-      for (int d = 0; d < NDIM; ++d) load2(p.col[d], i, vec, c0[d], c1[d]);
-      if (ACC != ACC_UNIT) load2(p.w, i, vec, w0, w1);
-    } else {
-#pragma unroll
-      for (int d = 0; d < NDIM; ++d) c0[d] = __ldcs(p.col[d] + i);
-      if (ACC != ACC_UNIT) w0 = __ldcs(p.w + i);
-    }
-    do_event<NDIM, ACC, SMEM>(p, Tax, sbins, sbins_f64, c0, w0, st, stride1, stride2);
-    if (pair) do_event<NDIM, ACC, SMEM>(p, Tax, sbins, sbins_f64, c1, w1, st, stride1, stride2);
-    if (++iters == kFlushIters) {
-      if (ACC != ACC_F64) st.flush();
-      iters = 0;
-    }
+    for (int d = 0; d < NDIM; ++d) c[d] = __ldcs(reinterpret_cast<const unsigned long long*>(p.col[d]) + (n - 1));
+    const unsigned long long w =
+        UNIT ? 0x3FF0000000000000ull : __ldcs(reinterpret_cast<const unsigned long long*>(p.w) + (n - 1));
+    f.event(c, w);
   }
-  if (ACC != ACC_F64) st.flush();
+  f.st.flush();
+  f.st.d[2] = f.st.w2;
+#pragma unroll
+  for (int k = 2; k < NS; ++k) f.st.d[k] = __dadd_rn(f.st.d[k], slow[k]);
 
   __syncthreads();
-  // per-block partial bins -> scratch
   if (SMEM) {
-    if (ACC == ACC_UNIT) {
+    if (UNIT) {
       unsigned* out = reinterpret_cast<unsigned*>(p.part_bins) + (size_t)blockIdx.x * nb;
-      for (int i = threadIdx.x; i < nb; i += blockDim.x) out[i] = sbins[i];
-    } else if (ACC == ACC_FX) {
-      uint4* out = reinterpret_cast<uint4*>(p.part_bins) + (size_t)blockIdx.x * nb;
-      const uint4* sb4 = reinterpret_cast<const uint4*>(sbins);
-      for (int i = threadIdx.x; i < nb; i += blockDim.x) out[i] = sb4[i];
+      for (int i = threadIdx.x; i < nb; i += blockDim.x) out[i] = f.sbins[i];
     } else {
-      double2* out = reinterpret_cast<double2*>(p.part_bins) + (size_t)blockIdx.x * nb;
-      const double2* sb2 = reinterpret_cast<const double2*>(sbins_f64);
-      for (int i = threadIdx.x; i < nb; i += blockDim.x) out[i] = sb2[i];
+      uint4* out = reinterpret_cast<uint4*>(p.part_bins) + (size_t)blockIdx.x * nb;
+      const uint4* sb4 = reinterpret_cast<const uint4*>(f.sbins);
+      for (int i = threadIdx.x; i < nb; i += blockDim.x) out[i] = sb4[i];
     }
   }
-  block_reduce_stats<StatAcc<NDIM, ACC == ACC_UNIT>::NS>(st.d, p.part_stats + (size_t)blockIdx.x * kMaxStats,
-                                                         sred);
+  block_reduce_stats<NS>(f.st.d, p.part_stats + (size_t)blockIdx.x * kMaxStats, sred);
 }
 
-// Sum of the per-block partials, in block order, into the persistent
-// accumulators; block 0 also sums the statistics partials.
+// Reduce: grid (bin tiles) x (slices of partials).  Thread (tile, slice, t)
+// sums bin g over partials [slice*r.slice, ...) and merges the result into
+// the persistent accumulators -- with integer atomics for the exact modes
+// (order-independent), with binary64 atomics for the binary64 mode.  CTA
+// (0, 0) also adds the statistics partials, in block order, with a fixed
+// shuffle tree (deterministic).
 __global__ void __launch_bounds__(256) k_reduce(const ReduceParams r) {
   const long long nb = r.nbins_total;
   if (r.part_bins != nullptr) {
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < nb;
-         g += (long long)gridDim.x * blockDim.x) {
+    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int b0 = blockIdx.y * r.slice;
+    const int b1 = min(r.nblocks, b0 + r.slice);
+    if (g < nb && b0 < b1) {
       if (r.mode == ACC_UNIT) {
         const unsigned* pb = reinterpret_cast<const unsigned*>(r.part_bins);
         unsigned long long c = 0;
-        for (int b = 0; b < r.nblocks; ++b) c += pb[(size_t)b * nb + g];
-        r.g_unit[g] += c;
+        for (int b = b0; b < b1; ++b) c += pb[(size_t)b * nb + g];
+        if (c) atomicAdd(&r.g_unit[g], c);
       } else if (r.mode == ACC_FX) {
         const uint4* pb = reinterpret_cast<const uint4*>(r.part_bins);
         __int128 acc = 0;
         unsigned long long c = 0;
-        for (int b = 0; b < r.nblocks; ++b) {
+        for (int b = b0; b < b1; ++b) {
           const uint4 v = pb[(size_t)b * nb + g];
-          // sign-extend the 96-bit word triple
-          const __int128 lo64 = (__int128)(((unsigned long long)v.y << 32) | v.x);
-          const __int128 hi32 = (__int128)(int)v.z;
-          acc += lo64 + (hi32 << 64);
+          acc += (__int128)(((unsigned long long)v.y << 32) | v.x) + ((__int128)(int)v.z << 64);
           c += v.w;
         }
-        r.g_lo[g] += (unsigned long long)(acc & (__int128)0xFFFFFFFFull);
-        r.g_hi[g] += (long long)(acc >> 32);
-        if (r.track_counts) r.g_count[g] += c;
+        const unsigned long long lo = (unsigned long long)(acc & (__int128)0xFFFFFFFFull);
+        const long long hi = (long long)(acc >> 32);
+        if (lo) atomicAdd(&r.g_lo[g], lo);
+        if (hi) atomicAdd(reinterpret_cast<unsigned long long*>(&r.g_hi[g]), (unsigned long long)hi);
+        if (r.track_counts && c) atomicAdd(&r.g_count[g], c);
       } else {
         const double2* pb = reinterpret_cast<const double2*>(r.part_bins);
         double s = 0.0, c = 0.0;
-        for (int b = 0; b < r.nblocks; ++b) {
+        for (int b = b0; b < b1; ++b) {
           const double2 v = pb[(size_t)b * nb + g];
           s = __dadd_rn(s, v.x);
           c = __dadd_rn(c, v.y);
         }
-        r.g_f64[g] = __dadd_rn(r.g_f64[g], s);
-        if (r.track_counts) r.g_count[g] += (unsigned long long)c;
+        atomicAdd(&r.g_f64[g], s);
+        if (r.track_counts && c != 0.0) atomicAdd(&r.g_count[g], (unsigned long long)c);
       }
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x < r.nstats && threadIdx.x >= 1) {
-    const int k = threadIdx.x;
-    double s = 0.0;
-    for (int b = 0; b < r.nblocks; ++b) s = __dadd_rn(s, r.part_stats[(size_t)b * kMaxStats + k]);
-    r.g_stats[k] = __dadd_rn(r.g_stats[k], s);
+  if (blockIdx.x == 0 && blockIdx.y == 0) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 2 + warp; k < r.nstats; k += blockDim.x >> 5) {
+      double s = 0.0;
+      for (int b = lane; b < r.nblocks; b += 32) s = __dadd_rn(s, r.part_stats[(size_t)b * kMaxStats + k]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_down_sync(0xffffffffu, s, o));
+      if (lane == 0) r.g_stats[k] = __dadd_rn(r.g_stats[k], s);
+    }
   }
 }
 
 // Fold the low-word sums into the high words so neither can overflow.
 __global__ void k_normalize_fx(unsigned long long* g_lo, long long* g_hi, long long nb) {
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < nb; g += (long long)gridDim.x * blockDim.x) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < nb;
+       g += (long long)gridDim.x * blockDim.x) {
     const unsigned long long lo = g_lo[g];
     g_hi[g] += (long long)(lo >> 32);
     g_lo[g] = lo & 0xFFFFFFFFull;
@@ -579,11 +665,13 @@ __global__ void __launch_bounds__(256) k_locate(const FillParams p, long long* _
   const long long n = p.n;
   const int stride1 = p.ax[0].nbins + 2;
   const int stride2 = NDIM >= 2 ? stride1 * (p.ax[1].nbins + 2) : 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
     long long g = 0;
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
-      const int k = locate_axis(p.ax[d], p.ax[d].T, dbits(__ldcs(p.col[d] + i)));
+      const unsigned long long b = dbits(__ldcs(p.col[d] + i));
+      const int k = locate_axis(p.ax[d], p.ax[d].T, b, hi24(b), in_f32(exp_field(b)));
       g += (long long)k * (d == 0 ? 1 : (d == 1 ? stride1 : stride2));
     }
     out[i] = g;
@@ -596,7 +684,7 @@ const void* fill_fn() {
 }
 
 const void* pick_fill(int ndim, int acc, bool smem) {
-#define HGB_PICK(N, A)                                                       \
+#define HGB_PICK(N, A) \
   if (ndim == N && acc == A) return smem ? fill_fn<N, A, true>() : fill_fn<N, A, false>();
   HGB_PICK(1, ACC_UNIT)
   HGB_PICK(1, ACC_FX)
@@ -613,10 +701,7 @@ const void* pick_fill(int ndim, int acc, bool smem) {
 
 }  // namespace
 
-size_t part_bin_bytes(int acc_mode, int /*track_counts*/) {
-  if (acc_mode == ACC_UNIT) return 4;
-  return 16;
-}
+size_t part_bin_bytes(int acc_mode, int /*track_counts*/) { return acc_mode == ACC_UNIT ? 4 : 16; }
 
 int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shape) {
   const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0);
@@ -630,7 +715,7 @@ int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shap
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem) != cudaSuccess) return -2;
   if (per_sm < 1) return -3;
-  long long want = (p.n + 2LL * block - 1) / (2LL * block);
+  const long long want = (p.n + 2LL * block - 1) / (2LL * block);
   long long grid = (long long)per_sm * sm_count;
   if (want < grid) grid = want;
   if (grid < 1) grid = 1;
@@ -644,16 +729,27 @@ int launch_fill(const FillParams& p, int acc_mode, const LaunchShape& s, void* s
   const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0);
   if (fn == nullptr) return -1;
   void* args[] = {const_cast<FillParams*>(&p)};
-  cudaError_t e = cudaLaunchKernel(fn, dim3(s.grid), dim3(s.block), args, s.smem, (cudaStream_t)stream);
+  const cudaError_t e = cudaLaunchKernel(fn, dim3(s.grid), dim3(s.block), args, s.smem, (cudaStream_t)stream);
   return e == cudaSuccess ? 0 : -2;
 }
 
-int launch_reduce(const ReduceParams& r, void* stream) {
-  long long blocks = (r.nbins_total + 255) / 256;
-  if (blocks < 1) blocks = 1;
-  if (blocks > 4096) blocks = 4096;
-  if (r.part_bins == nullptr) blocks = 1;
-  k_reduce<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(r);
+int launch_reduce(const ReduceParams& r0, void* stream) {
+  ReduceParams r = r0;
+  long long tiles = (r.nbins_total + 255) / 256;
+  int slices = 1;
+  if (r.part_bins != nullptr) {
+    // about 32 partials per thread, at least ~2 CTAs per SM overall
+    r.slice = 32;
+    slices = (r.nblocks + r.slice - 1) / r.slice;
+    if (slices > 65535) slices = 65535;
+    r.slice = (r.nblocks + slices - 1) / slices;
+  } else {
+    tiles = 1;
+    r.slice = r.nblocks;
+  }
+  if (tiles > 65535LL * 16) return -1;
+  dim3 grid((unsigned)tiles, (unsigned)slices);
+  k_reduce<<<grid, 256, 0, (cudaStream_t)stream>>>(r);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -47,7 +47,7 @@ struct hist {
   int32_t table_keys = 0;
   int32_t smem_keys = 0;     // how many keys are staged into shared memory
   int32_t loc_mode[kMaxDim] = {0, 0, 0};
-  float scale[kMaxDim] = {0, 0, 0}, offset[kMaxDim] = {0, 0, 0};
+  float scale[kMaxDim] = {0, 0, 0}, offset[kMaxDim] = {0, 0, 0}, eps[kMaxDim] = {1, 1, 1};
   bool smem_unit = true;     // unit-weight fills keep per-block bins in shared memory
   bool smem_weighted = true; // weighted fills likewise (16 bytes per bin)
   int fx_elo = kDefaultFxElo;
@@ -124,6 +124,7 @@ FillParams make_params(const hist* h, const double* values, const double* weight
     a.smem_off = (h->t_off[d] + h->nbins[d] + 3 <= h->smem_keys) ? h->t_off[d] : -1;
     a.scale = h->scale[d];
     a.offset = h->offset[d];
+    a.eps = h->eps[d];
     p.col[d] = values + (size_t)d * (size_t)n;
   }
   p.w = weights;
@@ -297,7 +298,8 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
       if (a.kind == HIST_AXIS_FIXED) {
         build_fixed_thresholds(a.nbins, a.xmin, a.xmax, Td);
         h->loc_mode[d] =
-            affine_estimate(a.nbins, a.xmin, a.xmax, &h->scale[d], &h->offset[d]) ? LOC_AFFINE : LOC_BSEARCH;
+            affine_estimate(a.nbins, a.xmin, a.xmax, &h->scale[d], &h->offset[d], &h->eps[d]) ? LOC_AFFINE
+                                                                                              : LOC_BSEARCH;
       } else {
         build_variable_thresholds(a.nbins, a.edges, Td);
         h->loc_mode[d] = LOC_BSEARCH;
@@ -401,34 +403,63 @@ int hist_locate(hist_t* h, const double* values, int64_t n, int64_t* out, hist_s
   return HIST_OK;
 }
 
+namespace {
+
+// Is linear bin g inside the range on every axis?
+bool bin_in_range(const hist* h, int64_t g) {
+  for (int d = 0; d < h->ndim; ++d) {
+    const int64_t n2 = (int64_t)h->nbins[d] + 2;
+    const int64_t k = g % n2;
+    g /= n2;
+    if (k < 1 || k > h->nbins[d]) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
 int hist_result(hist_t* h, double* bins, double* stats) {
   if (h == nullptr) return HIST_ERR_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return HIST_ERR_CUDA;
   if (h->have_done && cudaEventSynchronize(h->done) != cudaSuccess) return HIST_ERR_CUDA;
   const size_t nb = (size_t)h->nbins_total;
-  if (bins != nullptr) {
-    std::vector<unsigned long long> lo(nb), unit(nb);
-    std::vector<long long> hi(nb);
-    std::vector<double> f64(nb);
-    if (cudaMemcpy(lo.data(), h->g_lo, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(hi.data(), h->g_hi, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(unit.data(), h->g_unit, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(f64.data(), h->g_f64, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
-      return HIST_ERR_CUDA;
-    // Content = (fixed-point words + unit entries, as one exact integer in
-    // units of 2^(fx_elo - 1065)) rounded once to binary64, plus the binary64
-    // words (slow-path weights, binary64 mode).
-    const int shift = 1065 - h->fx_elo;
-    const double lsb = std::ldexp(1.0, -shift);
-    for (size_t g = 0; g < nb; ++g) {
-      const __int128 fx = ((__int128)hi[g] << 32) + (__int128)lo[g] + ((__int128)unit[g] << shift);
-      bins[g] = (double)fx * lsb + f64[g];
+  std::vector<unsigned long long> lo(nb), unit(nb);
+  std::vector<long long> hi(nb);
+  std::vector<double> f64(nb);
+  if (cudaMemcpy(lo.data(), h->g_lo, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(hi.data(), h->g_hi, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(unit.data(), h->g_unit, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(f64.data(), h->g_f64, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HIST_ERR_CUDA;
+  // Bin content = (fixed-point words + unit entries, as one exact integer in
+  // units of 2^(fx_elo - 1065)) rounded once to binary64, plus the binary64
+  // words (slow-path weights, binary64 mode).
+  const int shift = 1065 - h->fx_elo;
+  const double lsb = std::ldexp(1.0, -shift);
+  const bool all = (h->flags & HIST_STAT_OVERFLOWS) != 0;
+  __int128 sel_fx = 0;           // exact sum over the statistics' bins
+  double sel_f64 = 0.0, sel_c = 0.0;  // compensated sum of their binary64 words
+  unsigned long long sel_unit = 0;
+  for (size_t g = 0; g < nb; ++g) {
+    const __int128 fx = ((__int128)hi[g] << 32) + (__int128)lo[g] + ((__int128)unit[g] << shift);
+    if (bins != nullptr) bins[g] = (double)fx * lsb + f64[g];
+    if (all || bin_in_range(h, (int64_t)g)) {
+      sel_fx += fx;
+      sel_unit += unit[g];
+      const double t = sel_f64 + f64[g];
+      if (std::isfinite(t))
+        sel_c += (std::fabs(sel_f64) >= std::fabs(f64[g])) ? (sel_f64 - t) + f64[g] : (f64[g] - t) + sel_f64;
+      sel_f64 = t;
     }
   }
   if (stats != nullptr) {
     double s[kMaxStats];
     if (cudaMemcpy(s, h->g_stats, sizeof(s), cudaMemcpyDeviceToHost) != cudaSuccess) return HIST_ERR_CUDA;
     s[0] = (double)h->n_entries;
+    // sum w over the statistics' entries = sum of those bins' contents
+    s[1] = (double)sel_fx * lsb + (sel_f64 + sel_c);
+    // unit-weight entries add 1 each to sum w^2
+    s[2] += (double)sel_unit;
     for (int k = 0; k < h->nstats; ++k) stats[k] = s[k];
   }
   return HIST_OK;

@@ -50,7 +50,8 @@ struct AxisDev {
   int32_t nbins;
   int32_t mode;        // LocMode
   int32_t smem_off;    // offset of this axis' keys in the shared copy, -1 = read T from global
-  float scale, offset; // LOC_AFFINE: k ~ floor(xf * scale + offset)
+  float scale, offset; // LOC_AFFINE: v = xf * scale + offset estimates 1 + q of the formula
+  float eps;           // proven bound on |v - (1 + q)|; floor(v) is exact when frac(v) is farther than eps from an integer
   LearnedDev lm;
 };
 
@@ -83,7 +84,8 @@ struct FillParams {
 struct ReduceParams {
   const void* part_bins;
   const double* part_stats;
-  int32_t nblocks;
+  int32_t nblocks;      // number of per-block partials
+  int32_t slice;        // partials summed by one reducing thread
   int32_t nstats;
   long long nbins_total;
   int32_t mode;          // AccMode
