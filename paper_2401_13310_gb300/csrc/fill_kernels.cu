@@ -316,17 +316,18 @@ struct StatAcc {
 };
 
 // binary64 statistics terms of one event, rounded as in the definition
-// (w*x*x = (w*x)*x), added into d[2..NS).  Kept out of line: it runs only
+// (w*x*x = (w*x)*x), added into d[2..NS) (d[2] only for weighted fills: the
+// host adds sum w^2 of unit-weight entries).  Kept out of line: it runs only
 // for coordinates or weights outside the double-word range and for the
 // binary64-atomic mode.
-template <int NDIM>
+template <int NDIM, bool UNIT>
 __device__ __noinline__ void stat_f64(double* d, const unsigned long long* cb, unsigned long long wb) {
   double c[NDIM];
 #pragma unroll
   for (int k = 0; k < NDIM; ++k) c[k] = __longlong_as_double((long long)cb[k]);
   const double w = __longlong_as_double((long long)wb);
   const double wx = __dmul_rn(w, c[0]);
-  d[2] = __dadd_rn(d[2], __dmul_rn(w, w));
+  if (!UNIT) d[2] = __dadd_rn(d[2], __dmul_rn(w, w));  // unit weights: the host adds sum w^2
   d[3] = __dadd_rn(d[3], wx);
   d[4] = __dadd_rn(d[4], __dmul_rn(wx, c[0]));
   if (NDIM >= 2) {
@@ -488,7 +489,7 @@ struct Filler {
       }
       st.add_ff(cf, W, wb);
     } else {
-      stat_f64<NDIM>(slow, cb, wb);
+      stat_f64<NDIM, UNIT>(slow, cb, wb);
     }
   }
 };
@@ -510,22 +511,52 @@ __device__ __forceinline__ void load_pair(const double* __restrict__ p, long lon
   }
 }
 
+#ifndef HGB_PREFETCH
+#define HGB_PREFETCH 1
+#endif
+
+// All full pairs of events, grid-strided.  The next pair's loads are issued
+// before the current pair is processed, so each thread keeps two pairs of
+// loads in flight across the long per-event work.
 template <int NDIM, int ACC, bool SMEM, bool VEC>
 __device__ __forceinline__ void fill_pairs(Filler<NDIM, ACC, SMEM>& f, long long npairs) {
   const FillParams& p = f.p;
   const long long nthreads = (long long)gridDim.x * blockDim.x;
   int iters = 0;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < npairs; q += nthreads) {
-    const long long i = 2 * q;
-    unsigned long long c0[NDIM], c1[NDIM], w0 = 0x3FF0000000000000ull, w1 = 0x3FF0000000000000ull;
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  unsigned long long c0[NDIM], c1[NDIM], w0 = 0x3FF0000000000000ull, w1 = 0x3FF0000000000000ull;
+  if (HGB_PREFETCH && q < npairs) {
 #pragma unroll
-    for (int d = 0; d < NDIM; ++d) load_pair<VEC>(p.col[d], i, c0[d], c1[d]);
-    if (ACC != ACC_UNIT) load_pair<VEC>(p.w, i, w0, w1);
+    for (int d = 0; d < NDIM; ++d) load_pair<VEC>(p.col[d], 2 * q, c0[d], c1[d]);
+    if (ACC != ACC_UNIT) load_pair<VEC>(p.w, 2 * q, w0, w1);
+  }
+  for (; q < npairs; q += nthreads) {
+    if (!HGB_PREFETCH) {
+#pragma unroll
+      for (int d = 0; d < NDIM; ++d) load_pair<VEC>(p.col[d], 2 * q, c0[d], c1[d]);
+      if (ACC != ACC_UNIT) load_pair<VEC>(p.w, 2 * q, w0, w1);
+    }
+    unsigned long long n0[NDIM], n1[NDIM], nw0 = 0x3FF0000000000000ull, nw1 = 0x3FF0000000000000ull;
+    const long long qn = q + nthreads;
+    if (HGB_PREFETCH && qn < npairs) {
+#pragma unroll
+      for (int d = 0; d < NDIM; ++d) load_pair<VEC>(p.col[d], 2 * qn, n0[d], n1[d]);
+      if (ACC != ACC_UNIT) load_pair<VEC>(p.w, 2 * qn, nw0, nw1);
+    }
     f.event(c0, w0);
     f.event(c1, w1);
     if (++iters == kFlushIters) {
       f.st.flush();
       iters = 0;
+    }
+    if (HGB_PREFETCH) {
+#pragma unroll
+      for (int d = 0; d < NDIM; ++d) {
+        c0[d] = n0[d];
+        c1[d] = n1[d];
+      }
+      w0 = nw0;
+      w1 = nw1;
     }
   }
 }

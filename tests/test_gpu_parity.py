@@ -242,3 +242,23 @@ def test_weighted_configs_full_size(B, name):
     bins, stats, counts = gpu_fill(wl.axes, wl.values, wl.weights, flags=B.HIST_TRACK_COUNTS)
     check_against_oracle(wl.axes, wl.values, wl.weights, bins, stats, counts, ref, RTOL, RTOL,
                          what=f"cfg{name} full")
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_zero_and_tiny_coordinates(B, weighted):
+    """In-range coordinates outside the double-word range (exact zeros,
+    subnormals, tiny values) take the binary64 statistics path; with unit
+    weights sum w^2 must still equal the in-range entry count."""
+    rng = np.random.default_rng(12)
+    n = 20_001
+    x = rng.normal(0, 0.5, n)
+    x[::3] = 0.0
+    x[1::7] = -0.0
+    x[2::11] = 1e-300
+    x[3::13] = -5e-324
+    x[4::17] = 3e-13
+    axes = [W.fixed(10, -1.0, 1.0)]
+    w = rng.uniform(0.5, 1.5, n) if weighted else None
+    ref = oracle.fill(axes, x.reshape(1, -1), w)
+    bins, stats, counts = gpu_fill(axes, x, w, flags=B.HIST_TRACK_COUNTS)
+    check_against_oracle(axes, x, w, bins, stats, counts, ref, RTOL, RTOL, what=f"zeros weighted={weighted}")
