@@ -53,7 +53,8 @@ enum {
   HIST_ERR_TIMEOUT = -6,  /* a bounded device wait gave up */
   HIST_ERR_LOCATOR = -7,  /* learned locator not trained / unusable */
   HIST_ERR_STATE = -8,    /* call not valid in the object's current state */
-  HIST_ERR_UNSUPPORTED = -9
+  HIST_ERR_UNSUPPORTED = -9,
+  HIST_ERR_TOO_LARGE = -10 /* size beyond a fixed maximum (hist_fill_bulk_noalloc) */
 };
 
 /* Axis kinds. */
@@ -133,6 +134,27 @@ int hist_counts(hist_t *h, uint64_t *counts);
  * values as in hist_fill_bulk; out: device int64 [n].  Asynchronous on
  * `stream`.  Does not change the histogram. */
 int hist_locate(hist_t *h, const double *values, int64_t n, int64_t *out, hist_stream_t stream);
+
+/* Allocation-free 1D fill.  The paper has no counterpart: this entry point
+ * serves callers that cannot call cudaMalloc -- code running under another
+ * framework's memory manager (which owns all device memory), allocation-free
+ * real-time loops, callers that must avoid the synchronisation an allocation
+ * may cause.  It fills one bulk of n events on a 1D axis (fixed or variable,
+ * nbins + 2 <= 1024) and OVERWRITES the caller's device outputs:
+ *   bins_out:  device double [nbins + 2], the bulk's bin contents;
+ *   stats_out: device double [5] = [N, sum w, sum w^2, sum wx, sum wx^2].
+ * values: device [n]; weights: device [n] or NULL (unit weights); flags: 0
+ * or HIST_STAT_OVERFLOWS.  Same semantics and accuracy as hist_book +
+ * hist_fill_bulk + hist_result on that bulk.  Asynchronous on `stream`.
+ * No device or host memory is allocated: the scratch is one fixed library
+ * array of about 5 MB per device, held until the process exits.  The first
+ * call on a device looks up that array's address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  Calls share the array:
+ * calls that overlap on the GPU (unordered streams or threads) race and give
+ * wrong results.  Errors: HIST_ERR_ARG, HIST_ERR_AXIS, HIST_ERR_TOO_LARGE
+ * (nbins + 2 > 1024), HIST_ERR_ALIGN, HIST_ERR_CUDA. */
+int hist_fill_bulk_noalloc(const hist_axis_t *axis, const double *values, const double *weights, int64_t n,
+                           uint32_t flags, double *bins_out, double *stats_out, hist_stream_t stream);
 
 /* Zero bins, counts and statistics (synchronous). */
 int hist_reset(hist_t *h);

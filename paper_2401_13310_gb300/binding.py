@@ -29,6 +29,7 @@ HIST_ERR_TIMEOUT = -6
 HIST_ERR_LOCATOR = -7
 HIST_ERR_STATE = -8
 HIST_ERR_UNSUPPORTED = -9
+HIST_ERR_TOO_LARGE = -10
 
 HIST_AXIS_FIXED = 0
 HIST_AXIS_VARIABLE = 1
@@ -83,6 +84,7 @@ def load(path: str | None = None):
             "hist_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "hist_version": (ctypes.c_char_p, []),
             "hist_axis_thresholds": (ctypes.c_int, [_P, _P]),
+            "hist_fill_bulk_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_uint32, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -208,6 +210,16 @@ def hist_axis_thresholds(axis) -> np.ndarray:
     del keep
     _check(rc, "hist_axis_thresholds")
     return out
+
+
+def hist_fill_bulk_noalloc(axis, values, weights, n: int, flags: int, bins_out, stats_out,
+                           stream=None) -> None:
+    """Allocation-free 1D fill into caller-owned device outputs (see hist.h)."""
+    arr, keep = make_axes([axis])
+    rc = load().hist_fill_bulk_noalloc(ctypes.addressof(arr), _ptr(values), _ptr(weights), int(n),
+                                       int(flags), _ptr(bins_out), _ptr(stats_out), _stream_ptr(stream))
+    del keep
+    _check(rc, "hist_fill_bulk_noalloc")
 
 
 # ---------------------------------------------------------------- owner ------

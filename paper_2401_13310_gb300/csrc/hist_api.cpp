@@ -252,6 +252,8 @@ const char* hist_strerror(int code) {
       return "invalid state for this call";
     case HIST_ERR_UNSUPPORTED:
       return "unsupported combination";
+    case HIST_ERR_TOO_LARGE:
+      return "size exceeds the fixed maximum of this entry point";
     default:
       return "unknown status";
   }
