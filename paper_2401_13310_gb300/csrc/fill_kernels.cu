@@ -115,6 +115,23 @@ __device__ __forceinline__ int bsearch_keys(const long long* T, int nkeys, long 
   return base;
 }
 
+// Largest k in [0, nkeys) with T[k] <= key, searching the 32-bit high words
+// Thi[k] = T[k] >> 32 (half the bytes and compares of a 64-bit search), then
+// stepping back over the few thresholds that share key's high word: any j
+// with Thi[j] < key >> 32 has T[j] < key, so only equal high words need the
+// full compare.
+__device__ __forceinline__ int bsearch_hi(const long long* T, const int* Thi, int nkeys, long long key) {
+  const int kh = (int)(key >> 32);
+  int base = 0, len = nkeys;
+  while (len > 1) {
+    const int half = len >> 1;
+    base = (Thi[base + half] <= kh) ? base + half : base;
+    len -= half;
+  }
+  while (T[base] > key) --base;  // T[0] = INT64_MIN ends the walk
+  return base;
+}
+
 __device__ __forceinline__ float bf16_to_f32(uint16_t h) { return __uint_as_float((unsigned)h << 16); }
 
 // Exact bin from the thresholds, starting at a guess k0 in [0, nbins+1]:
@@ -133,8 +150,8 @@ __device__ __noinline__ int locate_exact(const long long* T, int nbins, int k, u
 
 // Bin of one coordinate on one axis (Sec. 3.1 step 1), exact.
 // xf: the coordinate as FP32 (hi24), valid when in_f32 of its exponent field.
-__device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T, unsigned long long b, float xf,
-                                           bool f32ok) {
+__device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T, const int* Thi,
+                                           unsigned long long b, float xf, bool f32ok) {
   if (a.mode == LOC_AFFINE) {
     // v estimates 1 + q; t = floor(v) + 1.5*2^23 exactly while |v| < 2^22.
     // Outside that range either v is an integer (fr = 0, not sure) or the
@@ -166,6 +183,7 @@ __device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T,
     if (lo <= hi && T[lo] <= key && key < T[hi + 1]) return lo + bsearch_keys(T + lo, hi - lo + 1, key);
     return bsearch_keys(T, a.nbins + 2, key);
   }
+  if (Thi != nullptr) return bsearch_hi(T, Thi, a.nbins + 2, key);
   return bsearch_keys(T, a.nbins + 2, key);
 }
 
@@ -403,6 +421,7 @@ struct Filler {
   static constexpr int NS = NStats<NDIM>::NS;
   const FillParams& p;
   const long long* Tax[NDIM];
+  const int* Thi[NDIM];  // high words of the shared-memory thresholds (nullptr: global table)
   unsigned* sbins;
   double* sbins_f64;
   int stride1, stride2;
@@ -421,7 +440,7 @@ struct Filler {
     for (int d = 0; d < NDIM; ++d) {
       ef[d] = exp_field(cb[d]);
       xf[d] = hi24(cb[d]);
-      const int k = locate_axis(p.ax[d], Tax[d], cb[d], xf[d], in_f32(ef[d]));
+      const int k = locate_axis(p.ax[d], Tax[d], Thi[d], cb[d], xf[d], in_f32(ef[d]));
       inr = inr && ((unsigned)(k - 1) < (unsigned)p.ax[d].nbins);
       g += (long long)k * (d == 0 ? 1 : (d == 1 ? stride1 : stride2));
     }
@@ -568,15 +587,24 @@ __global__ void __launch_bounds__(256, HGB_MIN_BLOCKS) k_fill(const FillParams p
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nkeys = p.table_keys;
   long long* skeys = reinterpret_cast<long long*>(smem_raw);
-  unsigned char* after_keys = smem_raw + (((size_t)nkeys * 8 + 15) & ~(size_t)15);
+  int* shi = reinterpret_cast<int*>(smem_raw + (size_t)nkeys * 8);
+  unsigned char* after_keys = smem_raw + (((size_t)nkeys * 12 + 15) & ~(size_t)15);
   __shared__ double sred[8 * kMaxStats];
 
   Filler<NDIM, ACC, SMEM> f(p);
   f.sbins = reinterpret_cast<unsigned*>(after_keys);
   f.sbins_f64 = reinterpret_cast<double*>(after_keys);
-  for (int i = threadIdx.x; i < nkeys; i += blockDim.x) skeys[i] = p.T_concat[i];
+  for (int i = threadIdx.x; i < nkeys; i += blockDim.x) {
+    const long long t = p.T_concat[i];
+    skeys[i] = t;
+    shi[i] = (int)(t >> 32);
+  }
 #pragma unroll
-  for (int d = 0; d < NDIM; ++d) f.Tax[d] = (p.ax[d].smem_off >= 0) ? skeys + p.ax[d].smem_off : p.ax[d].T;
+  for (int d = 0; d < NDIM; ++d) {
+    const bool staged = p.ax[d].smem_off >= 0;
+    f.Tax[d] = staged ? skeys + p.ax[d].smem_off : p.ax[d].T;
+    f.Thi[d] = staged ? shi + p.ax[d].smem_off : nullptr;
+  }
   const int nb = (int)p.nbins_total;
   if (SMEM) {
     const int words = UNIT ? nb : 4 * nb;
@@ -702,7 +730,7 @@ __global__ void __launch_bounds__(256) k_locate(const FillParams p, long long* _
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
       const unsigned long long b = dbits(__ldcs(p.col[d] + i));
-      const int k = locate_axis(p.ax[d], p.ax[d].T, b, hi24(b), in_f32(exp_field(b)));
+      const int k = locate_axis(p.ax[d], p.ax[d].T, nullptr, b, hi24(b), in_f32(exp_field(b)));
       g += (long long)k * (d == 0 ? 1 : (d == 1 ? stride1 : stride2));
     }
     out[i] = g;
@@ -738,7 +766,7 @@ int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shap
   const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0);
   if (fn == nullptr) return -1;
   const int block = 256;
-  size_t smem = (((size_t)p.table_keys * 8 + 15) & ~(size_t)15);
+  size_t smem = (((size_t)p.table_keys * 12 + 15) & ~(size_t)15);
   if (p.smem_bins) smem += (size_t)p.nbins_total * part_bin_bytes(acc_mode, p.track_counts);
   if (smem > 48 * 1024) {
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;
