@@ -135,6 +135,48 @@ int hist_counts(hist_t *h, uint64_t *counts);
  * `stream`.  Does not change the histogram. */
 int hist_locate(hist_t *h, const double *values, int64_t n, int64_t *out, hist_stream_t stream);
 
+/* ---- learned locator (variable axes) ------------------------------------
+ * A trained piecewise-linear index model predicts the bin of a coordinate;
+ * an exact search inside a certified window corrects it, and a full binary
+ * search judges every window miss, so results stay bit-exact.  The model
+ * over S uniform segments of u = (xf - u0) * u_scale (xf: the coordinate
+ * truncated to FP32) has knots K[j] = base[j] + theta[j] (base: exact int32
+ * bin at the knot; theta: a bf16 residual), k^ = K[s] (1 - t) + K[s+1] t.
+ * Training: Adam on FP32 master weights minimising the mean squared error
+ * against (coordinate, index) pairs taken from the exact binning -- each
+ * bin j contributes (e_{j-1}, j - 1/2) and (its midpoint, j). */
+typedef struct {
+  int32_t segments; /* S; 0 = automatic (a power of two near nbins / 8, 16 .. 2^20) */
+  int32_t steps;    /* Adam steps; 0 = 400 */
+  float lr;         /* Adam learning rate, in bins; 0 = 0.05 */
+  int32_t apply;    /* nonzero: later fills of this axis use the model */
+} hist_locator_opts_t;
+
+typedef struct {
+  int32_t segments, steps;
+  int32_t window_untrained; /* certified half-window of the model before training */
+  int32_t window;           /* certified half-window after training */
+  double loss_untrained;    /* mean squared index error on the training pairs */
+  double loss;
+  double train_ms;          /* wall time of training and certification */
+} hist_locator_report_t;
+
+/* Train, certify and (opts->apply) install the learned locator of variable
+ * axis `axis` (0-based) on the GPU, with the library's own forward, backward
+ * and update kernels.  Synchronous.  opts may be NULL (defaults); report may
+ * be NULL.  Errors: HIST_ERR_ARG (bad axis index, fixed axis),
+ * HIST_ERR_LOCATOR (degenerate axis range in FP32), HIST_ERR_OOM,
+ * HIST_ERR_CUDA. */
+int hist_train_locator(hist_t *h, int axis, const hist_locator_opts_t *opts, hist_locator_report_t *report);
+
+/* One forward and backward pass of the locator's training loss on the GPU
+ * (the kernels hist_train_locator uses), for checking its gradients.  All
+ * pointers are host memory: base and theta [nseg + 1], x and target [n],
+ * grad [nseg + 1] (out, dL/dtheta), loss (out, mean squared error).
+ * Errors: HIST_ERR_ARG, HIST_ERR_OOM, HIST_ERR_CUDA. */
+int hist_locator_loss_grad(int nseg, float u0, float u_scale, const int32_t *base, const float *theta,
+                           const double *x, const float *target, int64_t n, double *loss, float *grad);
+
 /* Allocation-free 1D fill.  The paper has no counterpart: this entry point
  * serves callers that cannot call cudaMalloc -- code running under another
  * framework's memory manager (which owns all device memory), allocation-free

@@ -49,6 +49,18 @@ class HistError(RuntimeError):
         super().__init__(f"{where}: {strerror(code)} ({code})")
 
 
+class hist_locator_opts_t(ctypes.Structure):
+    _fields_ = [("segments", ctypes.c_int32), ("steps", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("apply", ctypes.c_int32)]
+
+
+class hist_locator_report_t(ctypes.Structure):
+    _fields_ = [("segments", ctypes.c_int32), ("steps", ctypes.c_int32),
+                ("window_untrained", ctypes.c_int32), ("window", ctypes.c_int32),
+                ("loss_untrained", ctypes.c_double), ("loss", ctypes.c_double),
+                ("train_ms", ctypes.c_double)]
+
+
 class hist_axis_t(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("nbins", ctypes.c_int32),
                 ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
@@ -85,6 +97,9 @@ def load(path: str | None = None):
             "hist_version": (ctypes.c_char_p, []),
             "hist_axis_thresholds": (ctypes.c_int, [_P, _P]),
             "hist_fill_bulk_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_uint32, _P, _P, _P]),
+            "hist_train_locator": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+            "hist_locator_loss_grad": (ctypes.c_int, [ctypes.c_int, ctypes.c_float, ctypes.c_float, _P, _P, _P,
+                                                      _P, ctypes.c_int64, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -222,6 +237,29 @@ def hist_fill_bulk_noalloc(axis, values, weights, n: int, flags: int, bins_out, 
     _check(rc, "hist_fill_bulk_noalloc")
 
 
+def hist_train_locator(h: int, axis: int, segments: int = 0, steps: int = 0, lr: float = 0.0,
+                       apply: bool = True) -> dict:
+    """Train, certify and (apply) install the learned locator of one variable axis."""
+    o = hist_locator_opts_t(int(segments), int(steps), float(lr), 1 if apply else 0)
+    r = hist_locator_report_t()
+    _check(load().hist_train_locator(h, int(axis), ctypes.byref(o), ctypes.byref(r)), "hist_train_locator")
+    return {f: getattr(r, f) for f, _ in hist_locator_report_t._fields_}
+
+
+def hist_locator_loss_grad(nseg: int, u0: float, u_scale: float, base, theta, x, target):
+    """GPU loss and gradient of the locator's training objective (host arrays)."""
+    base = np.ascontiguousarray(base, dtype=np.int32)
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    target = np.ascontiguousarray(target, dtype=np.float32)
+    grad = np.zeros(nseg + 1, dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(load().hist_locator_loss_grad(int(nseg), float(u0), float(u_scale), base.ctypes.data,
+                                         theta.ctypes.data, x.ctypes.data, target.ctypes.data, x.shape[0],
+                                         ctypes.byref(loss), grad.ctypes.data), "hist_locator_loss_grad")
+    return loss.value, grad
+
+
 # ---------------------------------------------------------------- owner ------
 
 class Hist:
@@ -252,6 +290,9 @@ class Hist:
             out = torch.empty(n, dtype=torch.int64, device=values.device)
         hist_locate(self.h, values, n, out, stream)
         return out
+
+    def train_locator(self, axis: int = 0, **kw) -> dict:
+        return hist_train_locator(self.h, axis, **kw)
 
     def result(self):
         return hist_result(self.h)

@@ -46,6 +46,7 @@
 #include <cstdint>
 
 #include "hist_internal.h"
+#include "learned_eval.cuh"
 
 namespace hgb {
 namespace {
@@ -167,21 +168,13 @@ __device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T,
   }
   const long long key = key_of(b);
   if (a.mode == LOC_LEARNED) {
-    // Piecewise-linear index model: k^ = base[s] + th0[s] + th1[s] * t,
-    // t = fractional position in segment s; then an exact search inside the
-    // certified window; the full binary search judges any miss.
-    const LearnedDev& m = a.lm;
-    float u = (est_float(b) - m.u0) * m.u_scale;
-    u = fminf(fmaxf(u, 0.0f), (float)m.nseg - 0.5f);
-    const int s = (int)u;
-    const float tt = u - (float)s;
-    const float kh = (float)m.base[s] + bf16_to_f32(m.th0[s]) + bf16_to_f32(m.th1[s]) * tt;
-    const int k0 = (int)floorf(kh + 0.5f);
-    int lo = k0 - m.window, hi = k0 + m.window;
-    lo = lo < 0 ? 0 : lo;
-    hi = hi > a.nbins + 1 ? a.nbins + 1 : hi;
+    // the trained index model, then an exact search of the certified window;
+    // a window that does not bracket the key falls back to the full search
+    const float kh = lm_eval(a.lm, est_float(b));
+    const int k0 = (int)floorf(__fadd_rn(kh, 0.5f));
+    const int lo = max(k0 - a.lm.window, 0);
+    const int hi = min(k0 + a.lm.window, a.nbins + 1);
     if (lo <= hi && T[lo] <= key && key < T[hi + 1]) return lo + bsearch_keys(T + lo, hi - lo + 1, key);
-    return bsearch_keys(T, a.nbins + 2, key);
   }
   if (Thi != nullptr) return bsearch_hi(T, Thi, a.nbins + 2, key);
   return bsearch_keys(T, a.nbins + 2, key);

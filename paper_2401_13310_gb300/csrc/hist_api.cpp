@@ -9,6 +9,7 @@
 
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -48,6 +49,9 @@ struct hist {
   int32_t smem_keys = 0;     // how many keys are staged into shared memory
   int32_t loc_mode[kMaxDim] = {0, 0, 0};
   float scale[kMaxDim] = {0, 0, 0}, offset[kMaxDim] = {0, 0, 0}, eps[kMaxDim] = {1, 1, 1};
+  std::vector<int64_t> T_host[kMaxDim];  // host copy of the thresholds
+  int2* lm_knots[kMaxDim] = {nullptr, nullptr, nullptr};
+  LearnedDev lm[kMaxDim] = {};
   bool smem_unit = true;     // unit-weight fills keep per-block bins in shared memory
   bool smem_weighted = true; // weighted fills likewise (16 bytes per bin)
   int fx_elo = kDefaultFxElo;
@@ -95,6 +99,7 @@ void free_state(hist* h) {
   cudaFree(h->g_stats);
   cudaFree(h->part_bins);
   cudaFree(h->part_stats);
+  for (int d = 0; d < kMaxDim; ++d) cudaFree(h->lm_knots[d]);
 }
 
 int acc_mode_of(uint32_t flags, bool unit) {
@@ -125,6 +130,7 @@ FillParams make_params(const hist* h, const double* values, const double* weight
     a.scale = h->scale[d];
     a.offset = h->offset[d];
     a.eps = h->eps[d];
+    a.lm = h->lm[d];
     p.col[d] = values + (size_t)d * (size_t)n;
   }
   p.w = weights;
@@ -306,6 +312,7 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
         build_variable_thresholds(a.nbins, a.edges, Td);
         h->loc_mode[d] = LOC_BSEARCH;
       }
+      h->T_host[d].assign(Td, Td + a.nbins + 3);
     }
     h->table_keys = (int32_t)T.size();
     // stage a prefix of the axes' tables into shared memory
@@ -482,3 +489,196 @@ int hist_counts(hist_t* h, uint64_t* counts) {
 }
 
 }  // extern "C"
+
+namespace {
+
+// FP32 value of a binary64 truncated to 24 significant bits (as the device's
+// est_float: saturating to +-0 and +-2^127 outside the FP32 range).
+float host_trunc24(double x) {
+  uint64_t b;
+  std::memcpy(&b, &x, 8);
+  const unsigned hi = (unsigned)(b >> 32);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  unsigned f = ((unsigned)(b >> 29) - 0xC0000000u) & 0x7FFFFFFFu;
+  f = (e < 897u) ? 0u : f;
+  f = (e > 1150u) ? 0x7F000000u : f;
+  f |= hi & 0x80000000u;
+  float r;
+  std::memcpy(&r, &f, 4);
+  return r;
+}
+
+// Largest k with T[k] <= key (host binary search over the thresholds).
+int host_bin_of_key(const std::vector<int64_t>& T, int64_t key) {
+  int lo = 0, hi = (int)T.size() - 2;  // answer in [0, nbins+1]
+  while (lo < hi) {
+    const int mid = lo + (hi - lo + 1) / 2;
+    if (T[mid] <= key)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  ~DevBuf() { cudaFree(p); }
+  int alloc(size_t count) { return dalloc(&p, count * sizeof(T)); }
+};
+
+int lm_certify(const LearnedDev& m, const long long* dT, int nbins, int* d_err, int* window) {
+  if (cudaMemset(d_err, 0, sizeof(int)) != cudaSuccess) return HIST_ERR_CUDA;
+  if (launch_lm_certify(m, dT, nbins, d_err, nullptr) != 0) return HIST_ERR_CUDA;
+  int err = 0;
+  if (cudaMemcpy(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return HIST_ERR_CUDA;
+  *window = err + 1;  // one more bin covers FP32 non-monotonicity between the evaluated ends
+  return HIST_OK;
+}
+
+}  // namespace
+
+extern "C" int hist_locator_loss_grad(int nseg, float u0, float u_scale, const int32_t* base, const float* theta,
+                                      const double* x, const float* target, int64_t n, double* loss, float* grad) {
+  if (nseg < 1 || base == nullptr || theta == nullptr || x == nullptr || target == nullptr || n < 1 ||
+      loss == nullptr || grad == nullptr)
+    return HIST_ERR_ARG;
+  DevBuf<int> d_base;
+  DevBuf<float> d_theta, d_target, d_grad;
+  DevBuf<unsigned long long> d_x;
+  DevBuf<double> d_loss;
+  int rc;
+  if ((rc = d_base.alloc(nseg + 1)) || (rc = d_theta.alloc(nseg + 1)) || (rc = d_grad.alloc(nseg + 1)) ||
+      (rc = d_target.alloc(n)) || (rc = d_x.alloc(n)) || (rc = d_loss.alloc(1)))
+    return rc;
+  if (cudaMemcpy(d_base.p, base, sizeof(int) * (nseg + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_theta.p, theta, sizeof(float) * (nseg + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_x.p, x, sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_target.p, target, sizeof(float) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(d_grad.p, 0, sizeof(float) * (nseg + 1)) != cudaSuccess ||
+      cudaMemset(d_loss.p, 0, sizeof(double)) != cudaSuccess)
+    return HIST_ERR_CUDA;
+  if (launch_lm_fwd_bwd(u0, u_scale, nseg, d_base.p, d_theta.p, d_x.p, d_target.p, n, d_grad.p, d_loss.p, nullptr) != 0)
+    return HIST_ERR_CUDA;
+  if (cudaMemcpy(grad, d_grad.p, sizeof(float) * (nseg + 1), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(loss, d_loss.p, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HIST_ERR_CUDA;
+  return HIST_OK;
+}
+
+extern "C" int hist_train_locator(hist_t* h, int axis, const hist_locator_opts_t* opts, hist_locator_report_t* report) {
+  if (h == nullptr || axis < 0 || axis >= h->ndim || h->kind[axis] != HIST_AXIS_VARIABLE) return HIST_ERR_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
+  if (cudaSetDevice(h->device) != cudaSuccess) return HIST_ERR_CUDA;
+  if (h->have_done && cudaEventSynchronize(h->done) != cudaSuccess) return HIST_ERR_CUDA;
+  const int nb = h->nbins[axis];
+  const std::vector<int64_t>& T = h->T_host[axis];
+  auto edge = [&](int j) { return host_double_of_key(T[j + 1]); };  // e_j, j = 0..nb
+  int S = opts && opts->segments > 0 ? opts->segments : 16;
+  if (!(opts && opts->segments > 0))
+    while (S < (1 << 20) && S * 8 < nb) S <<= 1;
+  if (S < 1 || S > (1 << 22)) return HIST_ERR_ARG;
+  const int steps = opts && opts->steps > 0 ? opts->steps : 400;
+  const float lr = opts && opts->lr > 0.0f ? opts->lr : 0.05f;
+  const float u0 = host_trunc24(edge(0));
+  const float un = host_trunc24(edge(nb));
+  if (!(un > u0)) return HIST_ERR_LOCATOR;
+  const float u_scale = (float)((double)S / ((double)un - (double)u0));
+  if (!std::isfinite(u_scale) || !(u_scale > 0.0f)) return HIST_ERR_LOCATOR;
+  // knots: exact bin at the knot position, residual = the fractional index
+  // there (the untrained model interpolates the in-bin position linearly)
+  std::vector<int> base(S + 1);
+  std::vector<float> theta(S + 1);
+  for (int j = 0; j <= S; ++j) {
+    const double xj = (double)u0 + (double)j / (double)u_scale;
+    const int k = host_bin_of_key(T, host_key(xj));
+    base[j] = k;
+    double frac = 0.0;
+    if (k >= 1 && k <= nb) frac = (xj - edge(k - 1)) / (edge(k) - edge(k - 1)) - 0.5;
+    else if (k == 0) frac = 0.5;
+    else frac = -0.5;
+    theta[j] = (float)frac;
+  }
+  // training pairs from the exact binning
+  const long long ns = 2LL * nb;
+  std::vector<unsigned long long> xs(ns);
+  std::vector<float> ys(ns);
+  for (int j = 1; j <= nb; ++j) {
+    const double a = edge(j - 1), b = edge(j);
+    const double mid = a + 0.5 * (b - a);
+    std::memcpy(&xs[2 * (j - 1)], &a, 8);
+    std::memcpy(&xs[2 * (j - 1) + 1], &mid, 8);
+    ys[2 * (j - 1)] = (float)j - 0.5f;
+    ys[2 * (j - 1) + 1] = (float)j;
+  }
+  DevBuf<int> d_base, d_err;
+  DevBuf<float> d_theta, d_m1, d_m2, d_grad, d_y;
+  DevBuf<unsigned long long> d_x;
+  DevBuf<double> d_loss;
+  int2* d_knots = nullptr;
+  int rc;
+  if ((rc = d_base.alloc(S + 1)) || (rc = d_theta.alloc(S + 1)) || (rc = d_m1.alloc(S + 1)) ||
+      (rc = d_m2.alloc(S + 1)) || (rc = d_grad.alloc(S + 1)) || (rc = d_y.alloc(ns)) || (rc = d_x.alloc(ns)) ||
+      (rc = d_loss.alloc(1)) || (rc = d_err.alloc(1)) || (rc = dalloc(&d_knots, sizeof(int2) * (S + 1))))
+    return rc;
+  auto fail = [&](int code) {
+    cudaFree(d_knots);
+    return code;
+  };
+  if (cudaMemcpy(d_base.p, base.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_theta.p, theta.data(), sizeof(float) * (S + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_x.p, xs.data(), 8 * ns, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_y.p, ys.data(), 4 * ns, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(d_m1.p, 0, sizeof(float) * (S + 1)) != cudaSuccess ||
+      cudaMemset(d_m2.p, 0, sizeof(float) * (S + 1)) != cudaSuccess)
+    return fail(HIST_ERR_CUDA);
+  const long long* dT = h->d_T + h->t_off[axis];
+  LearnedDev m;
+  m.knots = d_knots;
+  m.u0 = u0;
+  m.u_scale = u_scale;
+  m.nseg = S;
+  m.window = 0;
+  auto loss_pass = [&](double* out) -> int {
+    if (cudaMemset(d_grad.p, 0, sizeof(float) * (S + 1)) != cudaSuccess ||
+        cudaMemset(d_loss.p, 0, sizeof(double)) != cudaSuccess)
+      return HIST_ERR_CUDA;
+    if (launch_lm_fwd_bwd(u0, u_scale, S, d_base.p, d_theta.p, d_x.p, d_y.p, ns, d_grad.p, d_loss.p, nullptr) != 0)
+      return HIST_ERR_CUDA;
+    if (out && cudaMemcpy(out, d_loss.p, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return HIST_ERR_CUDA;
+    return HIST_OK;
+  };
+  double loss0 = 0.0, loss1 = 0.0;
+  int w0 = 0, w1 = 0;
+  if ((rc = loss_pass(&loss0)) != HIST_OK) return fail(rc);
+  if (launch_lm_pack(d_base.p, d_theta.p, d_knots, S + 1, nullptr) != 0) return fail(HIST_ERR_CUDA);
+  if ((rc = lm_certify(m, dT, nb, d_err.p, &w0)) != HIST_OK) return fail(rc);
+  for (int it = 1; it <= steps; ++it) {
+    if ((rc = loss_pass(nullptr)) != HIST_OK) return fail(rc);
+    if (launch_lm_adam(d_theta.p, d_m1.p, d_m2.p, d_grad.p, S + 1, lr, 0.9f, 0.999f, 1e-12f, it, nullptr) != 0)
+      return fail(HIST_ERR_CUDA);
+  }
+  if ((rc = loss_pass(&loss1)) != HIST_OK) return fail(rc);
+  if (launch_lm_pack(d_base.p, d_theta.p, d_knots, S + 1, nullptr) != 0) return fail(HIST_ERR_CUDA);
+  if ((rc = lm_certify(m, dT, nb, d_err.p, &w1)) != HIST_OK) return fail(rc);
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(HIST_ERR_CUDA);
+  if (report) {
+    report->segments = S;
+    report->steps = steps;
+    report->window_untrained = w0;
+    report->window = w1;
+    report->loss_untrained = loss0;
+    report->loss = loss1;
+    report->train_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (opts && opts->apply) {
+    cudaFree(h->lm_knots[axis]);
+    h->lm_knots[axis] = d_knots;
+    m.window = w1;
+    h->lm[axis] = m;
+    h->loc_mode[axis] = LOC_LEARNED;
+    return HIST_OK;
+  }
+  return fail(HIST_OK);
+}

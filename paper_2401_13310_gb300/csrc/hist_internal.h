@@ -37,12 +37,10 @@ enum AccMode : int32_t {
 };
 
 struct LearnedDev {
-  const int32_t* base;   // [nseg + 1] exact bin index at each segment start
-  const uint16_t* th0;   // [nseg] bf16 offset residual
-  const uint16_t* th1;   // [nseg] bf16 slope
-  float u0, u_scale;     // u = (xf - u0) * u_scale in [0, nseg)
+  const int2* knots;  // [nseg + 1] {exact bin at the segment boundary, bf16 residual in the low 16 bits}
+  float u0, u_scale;  // u = (xf - u0) * u_scale in [0, nseg)
   int32_t nseg;
-  int32_t window;        // certified half-width of the search window
+  int32_t window;     // certified half-width of the exact search window
 };
 
 struct AxisDev {
@@ -110,6 +108,15 @@ int launch_fill(const FillParams& p, int acc_mode, const LaunchShape& shape, voi
 int launch_reduce(const ReduceParams& r, void* stream);
 int launch_locate(const FillParams& p, long long* out, void* stream);
 int launch_normalize_fx(unsigned long long* g_lo, long long* g_hi, long long nbins, void* stream);
+
+// Learned locator (learned.cu).  All pointers are device pointers.
+int launch_lm_fwd_bwd(float u0, float u_scale, int nseg, const int* base, const float* theta,
+                      const unsigned long long* x, const float* target, long long n, float* grad, double* loss,
+                      void* stream);
+int launch_lm_adam(float* theta, float* m1, float* m2, const float* grad, int count, float lr, float b1, float b2,
+                   float eps, int step, void* stream);
+int launch_lm_pack(const int* base, const float* theta, int2* knots, int count, void* stream);
+int launch_lm_certify(const LearnedDev& m, const long long* T, int nbins, int* max_err, void* stream);
 size_t part_bin_bytes(int acc_mode, int track_counts);
 
 }  // namespace hgb
