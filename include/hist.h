@@ -135,6 +135,55 @@ int hist_counts(hist_t *h, uint64_t *counts);
  * `stream`.  Does not change the histogram. */
 int hist_locate(hist_t *h, const double *values, int64_t n, int64_t *out, hist_stream_t stream);
 
+/* ---- batched fill: many histograms, one event stream ---------------------
+ * The paper's conclusion names computing several histograms from the same
+ * data, and its kernels being small and launch-bound, as the next step.  A
+ * batch fills up to 128 booked 1D histograms from up to 4 columns and one
+ * weight column in one fused launch: each column and weight is read once
+ * per event; small histograms keep exact per-block bins in shared memory,
+ * large ones use exact global integer atomics; histograms that share a
+ * column and range share their statistics sums.  Results and accuracy per
+ * histogram are those of hist_fill_bulk. */
+typedef struct hist_batch hist_batch_t;
+
+#define HIST_BATCH_GRAPH (1u << 0) /* replay the fill's launches as a cached CUDA graph */
+
+/* Build a batch over hists[0..nh) (all 1D, same device); histogram i reads
+ * column col_of_hist[i] (0..3).  At most 2 distinct axis ranges per column.
+ * The batch references the histograms (they must outlive it) and owns its
+ * device descriptors and scratch.  Errors: HIST_ERR_ARG, HIST_ERR_UNSUPPORTED
+ * (ND histogram, too many ranges per column), HIST_ERR_OOM, HIST_ERR_CUDA. */
+int hist_batch_create(hist_t *const *hists, int nh, const int32_t *col_of_hist, uint32_t flags,
+                      hist_batch_t **out);
+
+/* Fill every histogram of the batch with the same n events: cols is a host
+ * array of ncols device column pointers ([n] binary64 each), weights a
+ * device [n] array or NULL (unit weights).  Asynchronous on `stream`,
+ * ordered after earlier fills of the member histograms; fills accumulate.
+ * Errors: HIST_ERR_ARG, HIST_ERR_ALIGN, HIST_ERR_CUDA. */
+int hist_batch_fill(hist_batch_t *b, const double *const *cols, int ncols, const double *weights, int64_t n,
+                    hist_stream_t stream);
+
+typedef struct {
+  int32_t candidates;      /* configurations timed */
+  int32_t smem_bytes;      /* chosen shared-memory budget for block-private bins */
+  int32_t blocks_per_sm;   /* chosen occupancy */
+  int32_t smem_hists;      /* histograms kept in shared memory */
+  double best_ms;          /* time of the chosen configuration on the sample */
+  double worst_ms;         /* slowest candidate */
+} hist_batch_tuning_t;
+
+/* Autotune the batch: time the candidate privatisation budgets (which
+ * histograms keep shared-memory bins) and occupancies on the given sample of
+ * events, writing into scratch accumulators (the member histograms are not
+ * changed), and keep the fastest for later fills.  Synchronous.  report may
+ * be NULL.  Errors: as hist_batch_fill. */
+int hist_batch_tune(hist_batch_t *b, const double *const *cols, int ncols, const double *weights, int64_t n,
+                    hist_batch_tuning_t *report);
+
+/* Release the batch (not its histograms).  NULL is a no-op. */
+void hist_batch_free(hist_batch_t *b);
+
 /* ---- learned locator (variable axes) ------------------------------------
  * A trained piecewise-linear index model predicts the bin of a coordinate;
  * an exact search inside a certified window corrects it, and a full binary

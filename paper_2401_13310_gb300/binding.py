@@ -61,6 +61,15 @@ class hist_locator_report_t(ctypes.Structure):
                 ("train_ms", ctypes.c_double)]
 
 
+class hist_batch_tuning_t(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("smem_hists", ctypes.c_int32),
+                ("best_ms", ctypes.c_double), ("worst_ms", ctypes.c_double)]
+
+
+HIST_BATCH_GRAPH = 1 << 0
+
+
 class hist_axis_t(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("nbins", ctypes.c_int32),
                 ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
@@ -98,6 +107,10 @@ def load(path: str | None = None):
             "hist_axis_thresholds": (ctypes.c_int, [_P, _P]),
             "hist_fill_bulk_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_uint32, _P, _P, _P]),
             "hist_train_locator": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+            "hist_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_uint32, _P]),
+            "hist_batch_fill": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
+            "hist_batch_tune": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
+            "hist_batch_free": (None, [_P]),
             "hist_locator_loss_grad": (ctypes.c_int, [ctypes.c_int, ctypes.c_float, ctypes.c_float, _P, _P, _P,
                                                       _P, ctypes.c_int64, _P, _P]),
         }
@@ -258,6 +271,65 @@ def hist_locator_loss_grad(nseg: int, u0: float, u_scale: float, base, theta, x,
                                          theta.ctypes.data, x.ctypes.data, target.ctypes.data, x.shape[0],
                                          ctypes.byref(loss), grad.ctypes.data), "hist_locator_loss_grad")
     return loss.value, grad
+
+
+def _col_array(cols):
+    arr = (ctypes.c_void_p * len(cols))()
+    for i, c in enumerate(cols):
+        arr[i] = _ptr(c)
+    return arr
+
+
+def hist_batch_create(hists, col_of_hist, flags: int = 0) -> int:
+    hs = (ctypes.c_void_p * len(hists))(*[int(h) for h in hists])
+    cols = np.ascontiguousarray(col_of_hist, dtype=np.int32)
+    out = ctypes.c_void_p()
+    _check(load().hist_batch_create(hs, len(hists), cols.ctypes.data, int(flags), ctypes.byref(out)),
+           "hist_batch_create")
+    return out.value
+
+
+def hist_batch_fill(b: int, cols, weights, n: int, stream=None) -> None:
+    arr = _col_array(cols)
+    _check(load().hist_batch_fill(b, arr, len(cols), _ptr(weights), int(n), _stream_ptr(stream)),
+           "hist_batch_fill")
+
+
+def hist_batch_tune(b: int, cols, weights, n: int) -> dict:
+    arr = _col_array(cols)
+    r = hist_batch_tuning_t()
+    _check(load().hist_batch_tune(b, arr, len(cols), _ptr(weights), int(n), ctypes.byref(r)), "hist_batch_tune")
+    return {f: getattr(r, f) for f, _ in hist_batch_tuning_t._fields_}
+
+
+def hist_batch_free(b: int) -> None:
+    load().hist_batch_free(b)
+
+
+class Batch:
+    """Owns a batch over Hist objects (which must outlive it)."""
+
+    def __init__(self, hists, col_of_hist, flags: int = 0):
+        self.hists = list(hists)
+        self.b = hist_batch_create([h.h for h in self.hists], col_of_hist, flags)
+
+    def fill(self, cols, weights=None, stream=None) -> None:
+        n = int(cols[0].shape[-1])
+        hist_batch_fill(self.b, list(cols), weights, n, stream)
+
+    def tune(self, cols, weights=None) -> dict:
+        return hist_batch_tune(self.b, list(cols), weights, int(cols[0].shape[-1]))
+
+    def close(self) -> None:
+        if self.b:
+            hist_batch_free(self.b)
+            self.b = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- owner ------

@@ -1,0 +1,264 @@
+// batch.cu -- many 1D histograms filled from one event stream in one launch.
+//
+// The paper's closing remarks point at computing several histograms from the
+// same data, and at its kernels being small and launch-bound.  Here one
+// persistent launch reads every column and the weight once per event and
+// fills all histograms of the batch:
+//  * histograms are sorted by column; the per-column work (the FP32 view of
+//    the coordinate, its range flags) and the per-event weight work (the
+//    exact fixed-point value) happen once per event, not once per histogram;
+//  * each thread holds kEv events in registers and walks the histograms
+//    outermost, so a histogram's descriptor is read once per kEv events;
+//  * small histograms keep block-private bins in shared memory: the low 64
+//    bits of the exact fixed-point sum as two u32 words updated by
+//    carry-propagating atomics, the rare carry out of bit 63 going straight
+//    to the histogram's global high word; at the end each block adds its
+//    words into the global accumulators with 64-bit integer atomics (exact,
+//    so the order does not matter);
+//  * large histograms add every event to the global accumulators with two
+//    64-bit integer atomics (exact);
+//  * statistics depend only on the column, the weight and the in-range test,
+//    so histograms with the same column and range share one statistics
+//    group, accumulated in binary64 per thread (the binary64 pipe is
+//    otherwise idle in this compute-bound kernel: a few operations per
+//    event against thousands of others), reduced per block in a fixed order
+//    and added to every member histogram by a second kernel.
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "device_common.cuh"
+#include "hist_internal.h"
+
+namespace hgb {
+namespace {
+
+constexpr int kEv = 4;  // events per thread per iteration
+
+// binary64 statistics of one group: sum w^2 (or nothing for unit weights),
+// sum wx, sum wx^2 -- terms rounded as in the definition.
+struct GroupStats {
+  double s2, s3, s4;
+};
+
+template <bool UNIT, bool SMEM>
+__device__ __forceinline__ void batch_add(const BatchHistDev& d, unsigned* sbins, int k, long long V, bool wok,
+                                          unsigned long long wb) {
+  if (UNIT) {
+    if (SMEM)
+      atomicAdd(&sbins[d.sbin_off + k], 1u);
+    else
+      atomicAdd(&d.g_unit[k], 1ull);
+    return;
+  }
+  if (!wok) {
+    atomicAdd(&d.g_f64[k], __longlong_as_double((long long)wb));
+    return;
+  }
+  if (V == 0) return;
+  if (SMEM) {
+    // low 64 bits in shared memory (two words, carry-chained); a carry out
+    // of bit 63 (or the sign extension of a negative addend) goes to the
+    // global high word, scaled by 2^32 in its carry-save representation
+    unsigned* a = &sbins[d.sbin_off + 2 * k];
+    const unsigned v0 = (unsigned)V;
+    const unsigned o0 = atomicAdd(a, v0);
+    const unsigned c0 = (o0 + v0 < o0) ? 1u : 0u;
+    const unsigned a1 = (unsigned)((unsigned long long)V >> 32) + c0;
+    const unsigned c1a = (a1 < c0) ? 1u : 0u;
+    const unsigned o1 = atomicAdd(a + 1, a1);
+    const unsigned c1 = c1a | ((o1 + a1 < o1) ? 1u : 0u);
+    const int top = (int)(V >> 63) + (int)c1;  // -1, 0 or 1 units of 2^64
+    if (top != 0)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&d.g_hi[k]), (unsigned long long)((long long)top << 32));
+  } else {
+    atomicAdd(&d.g_lo[k], (unsigned long long)(unsigned)V);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&d.g_hi[k]), (unsigned long long)(V >> 32));
+  }
+}
+
+template <bool UNIT>
+__global__ void __launch_bounds__(256, 2) k_batch_fill(const __grid_constant__ BatchParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nkeys = p.table_keys;
+  long long* skeys = reinterpret_cast<long long*>(smem_raw);
+  int* shi = reinterpret_cast<int*>(smem_raw + (size_t)nkeys * 8);
+  const size_t off_bins = ((size_t)nkeys * 12 + 15) & ~(size_t)15;
+  unsigned* sbins = reinterpret_cast<unsigned*>(smem_raw + off_bins);
+  const size_t off_desc = off_bins + (((size_t)p.sbin_words * 4 + 15) & ~(size_t)15);
+  BatchHistDev* sdesc = reinterpret_cast<BatchHistDev*>(smem_raw + off_desc);
+  __shared__ double sred[8][kBatchMaxGroups * 3];
+
+  for (int i = threadIdx.x; i < nkeys; i += blockDim.x) {
+    const long long t = p.T_concat[i];
+    skeys[i] = t;
+    shi[i] = (int)(t >> 32);
+  }
+  for (int i = threadIdx.x; i < p.sbin_words; i += blockDim.x) sbins[i] = 0u;
+  {
+    const int words = (int)(sizeof(BatchHistDev) / 4) * p.nh;
+    const unsigned* src = reinterpret_cast<const unsigned*>(p.hists);
+    unsigned* dst = reinterpret_cast<unsigned*>(sdesc);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+
+  GroupStats gs[kBatchMaxGroups];
+#pragma unroll
+  for (int g = 0; g < kBatchMaxGroups; ++g) gs[g].s2 = gs[g].s3 = gs[g].s4 = 0.0;
+
+  const long long n = p.n;
+  const long long nthreads = (long long)gridDim.x * blockDim.x;
+  const unsigned long long* wq = reinterpret_cast<const unsigned long long*>(p.w);
+  for (long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x; base < n; base += kEv * nthreads) {
+    // kEv events per thread, each load coalesced across the warp
+    bool valid[kEv];
+    unsigned long long wb[kEv];
+    long long V[kEv];
+    bool wok[kEv];
+#pragma unroll
+    for (int e = 0; e < kEv; ++e) {
+      const long long i = base + e * nthreads;
+      valid[e] = i < n;
+      wb[e] = (UNIT || !valid[e]) ? 0x3FF0000000000000ull : __ldcs(wq + i);
+      wok[e] = UNIT ? true : fx_of(wb[e], p.fx_elo, &V[e]);
+      if (UNIT) V[e] = 0;
+    }
+#pragma unroll
+    for (int c = 0; c < kBatchMaxCols; ++c) {
+      if (c >= p.ncols) break;
+      const unsigned long long* cq = reinterpret_cast<const unsigned long long*>(p.col[c]);
+      unsigned long long xb[kEv];
+      float xf[kEv];
+      bool f32ok[kEv];
+#pragma unroll
+      for (int e = 0; e < kEv; ++e) {
+        const long long i = base + e * nthreads;
+        xb[e] = valid[e] ? __ldcs(cq + i) : 0ull;
+        xf[e] = hi24(xb[e]);
+        f32ok[e] = in_f32(exp_field(xb[e]));
+      }
+      // every histogram of this column
+      for (int h = p.col_begin[c]; h < p.col_begin[c + 1]; ++h) {
+        const BatchHistDev d = sdesc[h];  // a copy: the shared bins' atomics cannot alias it
+        const bool staged = d.ax.smem_off >= 0;
+        const long long* T = staged ? skeys + d.ax.smem_off : d.ax.T;
+        const int* Thi = staged ? shi + d.ax.smem_off : nullptr;
+        const bool in_smem = d.sbin_off >= 0;
+#pragma unroll
+        for (int e = 0; e < kEv; ++e) {
+          if (!valid[e]) continue;
+          const int k = locate_axis(d.ax, T, Thi, xb[e], xf[e], f32ok[e]);
+          if (in_smem)
+            batch_add<UNIT, true>(d, sbins, k, V[e], wok[e], wb[e]);
+          else
+            batch_add<UNIT, false>(d, sbins, k, V[e], wok[e], wb[e]);
+        }
+      }
+      // statistics groups of this column
+#pragma unroll
+      for (int j = 0; j < kBatchGroupsPerCol; ++j) {
+        if (j >= p.ngroups_col[c]) break;
+        const int g = c * kBatchGroupsPerCol + j;
+        const long long lo = p.group_lo[g], hi = p.group_hi[g];
+#pragma unroll
+        for (int e = 0; e < kEv; ++e) {
+          if (!valid[e]) continue;
+          const long long key = key_of(xb[e]);
+          if (!(p.stat_overflows || (key >= lo && key < hi))) continue;
+          const double x = __longlong_as_double((long long)xb[e]);
+          const double w = __longlong_as_double((long long)wb[e]);
+          const double wx = UNIT ? x : __dmul_rn(w, x);
+          if (!UNIT) gs[g].s2 = __fma_rn(w, w, gs[g].s2);
+          gs[g].s3 = __dadd_rn(gs[g].s3, wx);
+          gs[g].s4 = __fma_rn(wx, x, gs[g].s4);
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // block-private bins -> the histograms' exact global accumulators
+  for (int h = 0; h < p.nh; ++h) {
+    const BatchHistDev& d = sdesc[h];
+    if (d.sbin_off < 0) continue;
+    const int nb = d.ax.nbins + 2;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+      if (UNIT) {
+        const unsigned c = sbins[d.sbin_off + k];
+        if (c) atomicAdd(&d.g_unit[k], (unsigned long long)c);
+      } else {
+        const unsigned a0 = sbins[d.sbin_off + 2 * k], a1 = sbins[d.sbin_off + 2 * k + 1];
+        if (a0) atomicAdd(&d.g_lo[k], (unsigned long long)a0);
+        if (a1) atomicAdd(reinterpret_cast<unsigned long long*>(&d.g_hi[k]), (unsigned long long)a1);
+      }
+    }
+  }
+  // per-block statistics partials, one fixed reduction order
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int g = 0; g < kBatchMaxGroups; ++g) {
+    double v[3] = {gs[g].s2, gs[g].s3, gs[g].s4};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[q] = __dadd_rn(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
+      if (lane == 0) sred[warp][g * 3 + q] = v[q];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kBatchMaxGroups * 3; t += blockDim.x) {
+    double v = 0.0;
+    for (int wi = 0; wi < nwarps; ++wi) v = __dadd_rn(v, sred[wi][t]);
+    const int g = t / 3, q = t % 3;
+    p.part_stats[((size_t)blockIdx.x * kBatchMaxGroups + g) * kMaxStats + 2 + q] = v;
+  }
+}
+
+// Thread (h, k) adds statistic k of histogram h's group, summed over the
+// blocks in order, into the histogram's statistics.
+__global__ void k_batch_reduce(const BatchReduceParams r) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int h = t / 3, q = t % 3;
+  if (h >= r.nh) return;
+  const int g = r.hist_group[h];
+  const int k = 2 + q;
+  double s = 0.0;
+  for (int b = 0; b < r.nblocks; ++b) s = __dadd_rn(s, r.part_stats[((size_t)b * kBatchMaxGroups + g) * kMaxStats + k]);
+  r.hist_stats[h][k] = __dadd_rn(r.hist_stats[h][k], s);
+}
+
+}  // namespace
+
+int batch_max_blocks_per_sm(int block, size_t smem, int* per_sm) {
+  const void* fn = reinterpret_cast<const void*>(&k_batch_fill<false>);
+  const void* fu = reinterpret_cast<const void*>(&k_batch_fill<true>);
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;
+    if (cudaFuncSetAttribute(fu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;
+  }
+  int a = 0, b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fn, block, smem) != cudaSuccess) return -2;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fu, block, smem) != cudaSuccess) return -2;
+  *per_sm = a < b ? a : b;
+  return 0;
+}
+
+int launch_batch_fill(const BatchParams& p, int block, int grid, size_t smem, void* stream) {
+  const void* fn = (p.w == nullptr) ? reinterpret_cast<const void*>(&k_batch_fill<true>)
+                                    : reinterpret_cast<const void*>(&k_batch_fill<false>);
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;
+  }
+  void* args[] = {const_cast<BatchParams*>(&p)};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, (cudaStream_t)stream) == cudaSuccess ? 0 : -2;
+}
+
+int launch_batch_reduce(const BatchReduceParams& r, void* stream) {
+  const int threads = r.nh * 3;
+  k_batch_reduce<<<(threads + 127) / 128, 128, 0, (cudaStream_t)stream>>>(r);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+}  // namespace hgb

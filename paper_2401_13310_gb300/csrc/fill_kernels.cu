@@ -45,209 +45,18 @@
 
 #include <cstdint>
 
+#include "device_common.cuh"
 #include "hist_internal.h"
-#include "learned_eval.cuh"
 
 namespace hgb {
 namespace {
-
-constexpr unsigned long long kMag = 0x7FFFFFFFFFFFFFFFull;
-constexpr unsigned long long kExpInf = 0x7FF0000000000000ull;
-constexpr unsigned long long kMant = 0x000FFFFFFFFFFFFFull;
-constexpr unsigned long long kHidden = 0x0010000000000000ull;
 #ifndef HGB_MIN_BLOCKS
 #define HGB_MIN_BLOCKS 1
 #endif
+#ifndef HGB_MIN_BLOCKS_1D
+#define HGB_MIN_BLOCKS_1D 4  // 1D kernels fit in 64 registers: four 256-thread blocks per SM
+#endif
 constexpr int kFlushIters = 32;  // two events per iteration: 64 events between binary64 flushes
-constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
-
-__device__ __forceinline__ unsigned long long dbits(double x) {
-  return (unsigned long long)__double_as_longlong(x);
-}
-
-
-// Ordered key of a binary64: compares like the double; -0 and +0 both map to
-// 0; every NaN maps to kNanKey, above +inf (the overflow bin).
-__device__ __forceinline__ long long key_of(unsigned long long b) {
-  const unsigned long long mag = b & kMag;
-  long long k = (long long)mag;
-  k = ((long long)b < 0) ? -k : k;
-  return (mag > kExpInf) ? kNanKey : k;
-}
-
-// FP32 value of a binary64 with the significand truncated to 24 bits, built
-// with integer operations (a binary64 -> FP32 conversion would use the
-// binary64 pipe).  |x| < 2^-126 gives +-0, |x| >= 2^128 (and inf/NaN) +-2^127.
-__device__ __forceinline__ float est_float(unsigned long long b) {
-  const unsigned hi = (unsigned)(b >> 32);
-  const unsigned sgn = hi & 0x80000000u;
-  const unsigned e = (hi >> 20) & 0x7FFu;
-  unsigned f = ((unsigned)(b >> 29) - 0xC0000000u) & 0x7FFFFFFFu;
-  f = (e < 897u) ? 0u : f;
-  f = (e > 1150u) ? 0x7F000000u : f;
-  return __uint_as_float(f | sgn);
-}
-
-// The same value without the saturation: only meaningful when in_f32(b).
-__device__ __forceinline__ float hi24(unsigned long long b) {
-  const unsigned hi = (unsigned)(b >> 32);
-  return __uint_as_float((((unsigned)(b >> 29) - 0xC0000000u) & 0x7FFFFFFFu) | (hi & 0x80000000u));
-}
-
-// Biased exponent field of a binary64, in place (bits 20..30 of the high word).
-__device__ __forceinline__ unsigned exp_field(unsigned long long b) { return (unsigned)(b >> 32) & 0x7FF00000u; }
-
-// |x| in [2^-126, 2^128): hi24 is exact truncation (zeros, subnormals,
-// huge values, inf and NaN are all outside).
-__device__ __forceinline__ bool in_f32(unsigned ef) { return ef - 0x38100000u < 0x0FE00000u; }
-
-// |x| in [2^-40, 2^40): the double-word statistics path is accurate and no
-// product of statistics terms over- or underflows FP32.
-__device__ __forceinline__ bool in_ff(unsigned ef) { return ef - (983u << 20) < (80u << 20); }
-
-// Largest k in [0, nkeys) with T[k] <= key (T[0] = INT64_MIN).
-__device__ __forceinline__ int bsearch_keys(const long long* T, int nkeys, long long key) {
-  int base = 0, len = nkeys;
-  while (len > 1) {
-    const int half = len >> 1;
-    base = (T[base + half] <= key) ? base + half : base;
-    len -= half;
-  }
-  return base;
-}
-
-// Largest k in [0, nkeys) with T[k] <= key, searching the 32-bit high words
-// Thi[k] = T[k] >> 32 (half the bytes and compares of a 64-bit search), then
-// stepping back over the few thresholds that share key's high word: any j
-// with Thi[j] < key >> 32 has T[j] < key, so only equal high words need the
-// full compare.
-__device__ __forceinline__ int bsearch_hi(const long long* T, const int* Thi, int nkeys, long long key) {
-  const int kh = (int)(key >> 32);
-  int base = 0, len = nkeys;
-  while (len > 1) {
-    const int half = len >> 1;
-    base = (Thi[base + half] <= kh) ? base + half : base;
-    len -= half;
-  }
-  while (T[base] > key) --base;  // T[0] = INT64_MIN ends the walk
-  return base;
-}
-
-__device__ __forceinline__ float bf16_to_f32(uint16_t h) { return __uint_as_float((unsigned)h << 16); }
-
-// Exact bin from the thresholds, starting at a guess k0 in [0, nbins+1]:
-// one step each way, then a full binary search if still not bracketed.
-__device__ __noinline__ int locate_exact(const long long* T, int nbins, int k, unsigned long long b) {
-  const long long key = key_of(b);
-  if (key < T[k]) {
-    --k;
-    if (key < T[k]) k = bsearch_keys(T, nbins + 2, key);
-  } else if (key >= T[k + 1]) {
-    ++k;
-    if (key >= T[k + 1]) k = bsearch_keys(T, nbins + 2, key);
-  }
-  return k;
-}
-
-// Bin of one coordinate on one axis (Sec. 3.1 step 1), exact.
-// xf: the coordinate as FP32 (hi24), valid when in_f32 of its exponent field.
-__device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T, const int* Thi,
-                                           unsigned long long b, float xf, bool f32ok) {
-  if (a.mode == LOC_AFFINE) {
-    // v estimates 1 + q; t = floor(v) + 1.5*2^23 exactly while |v| < 2^22.
-    // Outside that range either v is an integer (fr = 0, not sure) or the
-    // clamp below puts k in the right flow bin.
-    const float v = __fmaf_rn(xf, a.scale, a.offset);
-    const float t = __fadd_rd(v, kMagic);
-    int k = __float_as_int(t) - 0x4B400000;
-    const float fr = __fsub_rn(v, __fsub_rn(t, kMagic));
-    const bool sure = f32ok && (fabsf(__fsub_rn(fr, 0.5f)) < 0.5f - a.eps);
-    k = min(max(k, 0), a.nbins + 1);
-    if (sure) return k;
-    return locate_exact(T, a.nbins, k, b);
-  }
-  const long long key = key_of(b);
-  if (a.mode == LOC_LEARNED) {
-    // the trained index model, then an exact search of the certified window;
-    // a window that does not bracket the key falls back to the full search
-    const float kh = lm_eval(a.lm, est_float(b));
-    const int k0 = (int)floorf(__fadd_rn(kh, 0.5f));
-    const int lo = max(k0 - a.lm.window, 0);
-    const int hi = min(k0 + a.lm.window, a.nbins + 1);
-    if (lo <= hi && T[lo] <= key && key < T[hi + 1]) return lo + bsearch_keys(T + lo, hi - lo + 1, key);
-  }
-  if (Thi != nullptr) return bsearch_hi(T, Thi, a.nbins + 2, key);
-  return bsearch_keys(T, a.nbins + 2, key);
-}
-
-// ---------------------------------------------------------------- FP32 double-word
-
-struct FF {
-  float hi, lo;
-};
-
-// hi + lo with hi = the leading 24 significant bits of x (hi24) and lo the
-// remaining 29 bits rounded to 24 (|x - hi - lo| <= 2^-48 |x|), for |x| in
-// [2^-40, 2^40).  Integer operations and one u32 -> f32 conversion only.
-__device__ __forceinline__ FF ff_split(unsigned long long b, float hi) {
-  const unsigned hi32 = (unsigned)(b >> 32);
-  const float scale = __uint_as_float(((hi32 >> 20) - 948u) << 23);  // 2^(e-1075), sign bit shifted out
-  const float lo = __fmul_rn(__uint2float_rn((unsigned)b & 0x1FFFFFFFu), scale);
-  FF r;
-  r.hi = hi;
-  r.lo = __uint_as_float(__float_as_uint(lo) | (hi32 & 0x80000000u));
-  return r;
-}
-
-// a * b as an unevaluated sum p + e (a.lo * b.lo, <= 2^-48 |ab|, is dropped).
-__device__ __forceinline__ FF ff_mul(FF a, FF b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  return {p, e};
-}
-
-// s += t with TwoSum on the high parts (Knuth): the rounding error of
-// s.hi + t.hi is recovered exactly and folded into s.lo.
-__device__ __forceinline__ void ff_acc(FF& s, FF t) {
-  const float sum = __fadd_rn(s.hi, t.hi);
-  const float bp = __fsub_rn(sum, s.hi);
-  const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(sum, bp)), __fsub_rn(t.hi, bp));
-  s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, err));
-  s.hi = sum;
-}
-
-// Exact FP32 -> binary64 widening with integer operations (the conversion
-// instruction runs on the binary64 pipe at half its add rate).  Normal
-// values and zeros only; the double-word parts here are never subnormal.
-__device__ __forceinline__ double f32_to_f64_bits(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
-  const unsigned long long mag =
-      ((unsigned long long)(((u >> 23) & 0xFFu) + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
-  return __longlong_as_double((long long)(((u & 0x7FFFFFFFu) == 0u) ? sgn : (sgn | mag)));
-}
-
-__device__ __forceinline__ double ff_to_double(FF s) {
-  return __dadd_rn(f32_to_f64_bits(s.hi), f32_to_f64_bits(s.lo));
-}
-
-// ---------------------------------------------------------------- fixed point
-
-// Weight -> signed fixed-point integer V = trunc(|w| * 2^(1065 - elo)) * sign.
-// Returns false (slow path: zeros, tiny, huge, inf, NaN) unless the biased
-// exponent is in [elo, elo + 16).  With the significand M (hidden bit
-// included) pre-shifted left by 10, V = (M << 10) >> (20 - (e - elo)) --
-// always a right shift by 5..20, so no bit of an in-window weight above
-// 2^-42 |w| is lost.  |V| < 2^58.
-__device__ __forceinline__ bool fx_of(unsigned long long wb, int elo, long long* V) {
-  const unsigned rel = ((unsigned)(wb >> 52) & 0x7FFu) - (unsigned)elo;
-  const unsigned long long M10 = ((wb << 10) & (kMant << 10)) | (kHidden << 10);
-  const unsigned long long U = M10 >> ((20u - rel) & 63u);
-  *V = ((long long)wb < 0) ? -(long long)U : (long long)U;
-  return rel < 16u;
-}
 
 // ---------------------------------------------------------------- statistics
 
@@ -408,7 +217,7 @@ __device__ __forceinline__ void load_pair(const double* __restrict__ p, long lon
 // ---------------------------------------------------------------- fill kernel
 
 // Per-thread state of one fill launch and the three steps for one event.
-template <int NDIM, int ACC, bool SMEM>
+template <int NDIM, int ACC, bool SMEM, int LOC>
 struct Filler {
   static constexpr bool UNIT = (ACC == ACC_UNIT);
   static constexpr int NS = NStats<NDIM>::NS;
@@ -433,7 +242,7 @@ struct Filler {
     for (int d = 0; d < NDIM; ++d) {
       ef[d] = exp_field(cb[d]);
       xf[d] = hi24(cb[d]);
-      const int k = locate_axis(p.ax[d], Tax[d], Thi[d], cb[d], xf[d], in_f32(ef[d]));
+      const int k = locate_mode<LOC>(p.ax[d], Tax[d], Thi[d], cb[d], xf[d], in_f32(ef[d]));
       inr = inr && ((unsigned)(k - 1) < (unsigned)p.ax[d].nbins);
       g += (long long)k * (d == 0 ? 1 : (d == 1 ? stride1 : stride2));
     }
@@ -452,8 +261,12 @@ struct Filler {
       } else if (V != 0) {
         if (SMEM) {
           // 96-bit add with carries: each atomic returns the old word, so the
-          // carry it produced is known exactly whatever the interleaving
-          unsigned* a = &sbins[4 * g];
+          // carry it produced is known exactly whatever the interleaving.  The
+          // low 64 bits live in shared memory; the rare top-word increment
+          // (a carry out of bit 63, or the sign of a negative addend not
+          // absorbed by a carry) goes straight to the global high word, which
+          // holds the sum in units of 2^32.
+          unsigned* a = &sbins[2 * g];
           const unsigned v0 = (unsigned)V;
           const unsigned o0 = atomicAdd(a, v0);
           const unsigned c0 = (o0 + v0 < o0) ? 1u : 0u;
@@ -461,8 +274,9 @@ struct Filler {
           const unsigned c1a = (a1 < c0) ? 1u : 0u;
           const unsigned o1 = atomicAdd(a + 1, a1);
           const unsigned c1 = c1a | ((o1 + a1 < o1) ? 1u : 0u);
-          const unsigned a2 = (unsigned)(V >> 63) + c1;
-          if (a2 != 0u) atomicAdd(a + 2, a2);
+          const int top = (int)(V >> 63) + (int)c1;
+          if (top != 0)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&p.g_hi[g]), (unsigned long long)((long long)top << 32));
         } else {
           atomicAdd(&p.g_lo[g], (unsigned long long)(unsigned)V);
           atomicAdd(reinterpret_cast<unsigned long long*>(&p.g_hi[g]), (unsigned long long)(V >> 32));
@@ -470,7 +284,7 @@ struct Filler {
       }
       if (p.track_counts) {
         if (SMEM)
-          atomicAdd(&sbins[4 * g + 3], 1u);
+          atomicAdd(&sbins[2 * (int)p.nbins_total + g], 1u);
         else
           atomicAdd(&p.g_count[g], 1ull);
       }
@@ -530,8 +344,8 @@ __device__ __forceinline__ void load_pair(const double* __restrict__ p, long lon
 // All full pairs of events, grid-strided.  The next pair's loads are issued
 // before the current pair is processed, so each thread keeps two pairs of
 // loads in flight across the long per-event work.
-template <int NDIM, int ACC, bool SMEM, bool VEC>
-__device__ __forceinline__ void fill_pairs(Filler<NDIM, ACC, SMEM>& f, long long npairs) {
+template <int NDIM, int ACC, bool SMEM, int LOC, bool VEC>
+__device__ __forceinline__ void fill_pairs(Filler<NDIM, ACC, SMEM, LOC>& f, long long npairs) {
   const FillParams& p = f.p;
   const long long nthreads = (long long)gridDim.x * blockDim.x;
   int iters = 0;
@@ -573,8 +387,8 @@ __device__ __forceinline__ void fill_pairs(Filler<NDIM, ACC, SMEM>& f, long long
   }
 }
 
-template <int NDIM, int ACC, bool SMEM>
-__global__ void __launch_bounds__(256, HGB_MIN_BLOCKS) k_fill(const FillParams p) {
+template <int NDIM, int ACC, bool SMEM, int LOC>
+__global__ void __launch_bounds__(256, NDIM == 1 ? HGB_MIN_BLOCKS_1D : HGB_MIN_BLOCKS) k_fill(const FillParams p) {
   constexpr bool UNIT = (ACC == ACC_UNIT);
   constexpr int NS = NStats<NDIM>::NS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -584,7 +398,7 @@ __global__ void __launch_bounds__(256, HGB_MIN_BLOCKS) k_fill(const FillParams p
   unsigned char* after_keys = smem_raw + (((size_t)nkeys * 12 + 15) & ~(size_t)15);
   __shared__ double sred[8 * kMaxStats];
 
-  Filler<NDIM, ACC, SMEM> f(p);
+  Filler<NDIM, ACC, SMEM, LOC> f(p);
   f.sbins = reinterpret_cast<unsigned*>(after_keys);
   f.sbins_f64 = reinterpret_cast<double*>(after_keys);
   for (int i = threadIdx.x; i < nkeys; i += blockDim.x) {
@@ -600,7 +414,7 @@ __global__ void __launch_bounds__(256, HGB_MIN_BLOCKS) k_fill(const FillParams p
   }
   const int nb = (int)p.nbins_total;
   if (SMEM) {
-    const int words = UNIT ? nb : 4 * nb;
+    const int words = (UNIT ? 1 : (ACC == ACC_FX ? (p.track_counts ? 3 : 2) : 4)) * nb;
     for (int i = threadIdx.x; i < words; i += blockDim.x) f.sbins[i] = 0u;
   }
   f.stride1 = p.ax[0].nbins + 2;
@@ -615,9 +429,9 @@ __global__ void __launch_bounds__(256, HGB_MIN_BLOCKS) k_fill(const FillParams p
   // every full pair of events, then the odd last event
   const long long n = p.n;
   if (p.aligned)
-    fill_pairs<NDIM, ACC, SMEM, true>(f, n >> 1);
+    fill_pairs<NDIM, ACC, SMEM, LOC, true>(f, n >> 1);
   else
-    fill_pairs<NDIM, ACC, SMEM, false>(f, n >> 1);
+    fill_pairs<NDIM, ACC, SMEM, LOC, false>(f, n >> 1);
   if ((n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
     unsigned long long c[NDIM];
 #pragma unroll
@@ -638,8 +452,14 @@ __global__ void __launch_bounds__(256, HGB_MIN_BLOCKS) k_fill(const FillParams p
       for (int i = threadIdx.x; i < nb; i += blockDim.x) out[i] = f.sbins[i];
     } else {
       uint4* out = reinterpret_cast<uint4*>(p.part_bins) + (size_t)blockIdx.x * nb;
-      const uint4* sb4 = reinterpret_cast<const uint4*>(f.sbins);
-      for (int i = threadIdx.x; i < nb; i += blockDim.x) out[i] = sb4[i];
+      if (ACC == ACC_FX) {
+        // {low word, next word, top word (kept in global), entries}
+        for (int i = threadIdx.x; i < nb; i += blockDim.x)
+          out[i] = make_uint4(f.sbins[2 * i], f.sbins[2 * i + 1], 0u, p.track_counts ? f.sbins[2 * nb + i] : 0u);
+      } else {
+        const uint4* sb4 = reinterpret_cast<const uint4*>(f.sbins);
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) out[i] = sb4[i];
+      }
     }
   }
   block_reduce_stats<NS>(f.st.d, p.part_stats + (size_t)blockIdx.x * kMaxStats, sred);
@@ -731,13 +551,20 @@ __global__ void __launch_bounds__(256) k_locate(const FillParams p, long long* _
 }
 
 template <int NDIM, int ACC, bool SMEM>
-const void* fill_fn() {
-  return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM>);
+const void* fill_fn(int loc) {
+  if constexpr (NDIM > 1) {
+    return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, -1>);
+  } else {
+    if (loc == LOC_AFFINE) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_AFFINE>);
+    if (loc == LOC_LEARNED) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_LEARNED>);
+    return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_BSEARCH>);
+  }
 }
 
-const void* pick_fill(int ndim, int acc, bool smem) {
+// 1D kernels are specialised per locate mode; ND kernels choose per axis at run time.
+const void* pick_fill(int ndim, int acc, bool smem, int loc) {
 #define HGB_PICK(N, A) \
-  if (ndim == N && acc == A) return smem ? fill_fn<N, A, true>() : fill_fn<N, A, false>();
+  if (ndim == N && acc == A) return smem ? fill_fn<N, A, true>(loc) : fill_fn<N, A, false>(loc);
   HGB_PICK(1, ACC_UNIT)
   HGB_PICK(1, ACC_FX)
   HGB_PICK(1, ACC_F64)
@@ -755,12 +582,18 @@ const void* pick_fill(int ndim, int acc, bool smem) {
 
 size_t part_bin_bytes(int acc_mode, int /*track_counts*/) { return acc_mode == ACC_UNIT ? 4 : 16; }
 
+size_t smem_bin_bytes(int acc_mode, int track_counts) {
+  if (acc_mode == ACC_UNIT) return 4;
+  if (acc_mode == ACC_FX) return track_counts ? 12 : 8;
+  return 16;
+}
+
 int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shape) {
-  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0);
+  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0, p.ax[0].mode);
   if (fn == nullptr) return -1;
   const int block = 256;
   size_t smem = (((size_t)p.table_keys * 12 + 15) & ~(size_t)15);
-  if (p.smem_bins) smem += (size_t)p.nbins_total * part_bin_bytes(acc_mode, p.track_counts);
+  if (p.smem_bins) smem += (size_t)p.nbins_total * smem_bin_bytes(acc_mode, p.track_counts);
   if (smem > 48 * 1024) {
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;
   }
@@ -778,7 +611,7 @@ int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shap
 }
 
 int launch_fill(const FillParams& p, int acc_mode, const LaunchShape& s, void* stream) {
-  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0);
+  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0, p.ax[0].mode);
   if (fn == nullptr) return -1;
   void* args[] = {const_cast<FillParams*>(&p)};
   const cudaError_t e = cudaLaunchKernel(fn, dim3(s.grid), dim3(s.block), args, s.smem, (cudaStream_t)stream);

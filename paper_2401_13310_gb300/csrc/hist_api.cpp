@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -28,7 +29,10 @@ namespace {
 
 constexpr int kDefaultFxElo = 1015;             // |w| in [2^-8, 2^8) summed exactly
 constexpr size_t kSmemTableBudget = 64 * 1024;  // threshold keys staged per block
-constexpr size_t kSmemBinsBudget = 96 * 1024;   // per-block bins (keeps >= 2 blocks per SM)
+#ifndef HGB_SMEM_BINS_BUDGET
+#define HGB_SMEM_BINS_BUDGET (96 * 1024)
+#endif
+constexpr size_t kSmemBinsBudget = HGB_SMEM_BINS_BUDGET;  // per-block bins (96 KB keeps >= 2 blocks per SM)
 
 }  // namespace
 
@@ -52,6 +56,7 @@ struct hist {
   std::vector<int64_t> T_host[kMaxDim];  // host copy of the thresholds
   int2* lm_knots[kMaxDim] = {nullptr, nullptr, nullptr};
   LearnedDev lm[kMaxDim] = {};
+  int config_version = 0;    // bumped when a locator is installed (batches rebuild descriptors)
   bool smem_unit = true;     // unit-weight fills keep per-block bins in shared memory
   bool smem_weighted = true; // weighted fills likewise (16 bytes per bin)
   int fx_elo = kDefaultFxElo;
@@ -329,8 +334,9 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
     }
     // weighted fills use the precision mode; unit fills always count
     h->acc_mode = acc_mode_of(flags, false);
-    h->smem_unit = (size_t)total * 4 <= kSmemBinsBudget;
-    h->smem_weighted = (size_t)total * 16 <= kSmemBinsBudget;
+    h->smem_unit = (size_t)total * smem_bin_bytes(ACC_UNIT, 0) <= kSmemBinsBudget;
+    h->smem_weighted = (size_t)total * smem_bin_bytes(h->acc_mode, (flags & HIST_TRACK_COUNTS) ? 1 : 0) <=
+                       kSmemBinsBudget;
     const size_t nb = (size_t)total;
     if ((rc = dalloc(&h->g_lo, nb * 8)) != HIST_OK) break;
     if ((rc = dalloc(&h->g_hi, nb * 8)) != HIST_OK) break;
@@ -678,7 +684,466 @@ extern "C" int hist_train_locator(hist_t* h, int axis, const hist_locator_opts_t
     m.window = w1;
     h->lm[axis] = m;
     h->loc_mode[axis] = LOC_LEARNED;
+    ++h->config_version;
     return HIST_OK;
   }
   return fail(HIST_OK);
+}
+
+// ============================================================== batches ====
+
+struct hist_batch {
+  std::vector<hist*> hs;     // member histograms, sorted by column
+  std::vector<int> col;      // column of each (sorted order)
+  int ncols = 0;             // columns referenced (max column + 1)
+  int device = 0, sm_count = 0;
+  uint32_t flags = 0;
+  int col_begin[kBatchMaxCols + 1] = {};
+  int ngroups_col[kBatchMaxCols] = {};
+  long long group_lo[kBatchMaxGroups] = {}, group_hi[kBatchMaxGroups] = {};
+  std::vector<int> group;    // statistics group of each member
+  // staged threshold tables
+  long long* d_T = nullptr;
+  int table_keys = 0;
+  std::vector<int> t_off;    // offset of each member's table in d_T, -1 = not staged
+  // descriptors
+  BatchHistDev* d_desc = nullptr;
+  BatchHistDev* d_desc_tune = nullptr;
+  int* d_group = nullptr;
+  double** d_stats = nullptr;
+  double** d_stats_tune = nullptr;
+  std::vector<int> built_versions;
+  // tuning scratch accumulators (one block of memory per member)
+  std::vector<void*> scratch;
+  double* d_part_stats = nullptr;
+  int part_blocks = 0;
+  // configuration
+  int smem_budget = 96 * 1024;
+  int grid = 0;
+  size_t smem = 0;
+  std::vector<int> sbin_off;
+  int sbin_words = 0;
+  cudaEvent_t done = nullptr;  // completion of the batch's last fill or tuning run
+  bool have_done = false;
+  // graph cache
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const double*> g_cols;
+  const double* g_w = nullptr;
+  int64_t g_n = -1;
+};
+
+namespace {
+
+constexpr int kBatchTableKeys = 2048;  // threshold keys staged per block (24 KB with high words)
+
+void batch_release(hist_batch* b) {
+  if (b->have_done) cudaEventSynchronize(b->done);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  cudaFree(b->d_T);
+  cudaFree(b->d_desc);
+  cudaFree(b->d_desc_tune);
+  cudaFree(b->d_group);
+  cudaFree(b->d_stats);
+  cudaFree(b->d_stats_tune);
+  cudaFree(b->d_part_stats);
+  for (void* q : b->scratch) cudaFree(q);
+}
+
+// Which members keep block-private bins in shared memory under a budget:
+// the smallest first (two words per bin, enough for unit and weighted fills).
+void batch_place(hist_batch* b, int budget) {
+  const int nh = (int)b->hs.size();
+  std::vector<int> order(nh);
+  for (int i = 0; i < nh; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->hs[x]->nbins[0] < b->hs[y]->nbins[0]; });
+  b->sbin_off.assign(nh, -1);
+  int words = 0;
+  for (int i : order) {
+    const int need = 2 * (b->hs[i]->nbins[0] + 2);
+    if ((long long)(words + need) * 4 > budget) break;
+    b->sbin_off[i] = words;
+    words += need;
+  }
+  b->sbin_words = words;
+  b->smem_budget = budget;
+}
+
+size_t batch_smem_bytes(const hist_batch* b) {
+  return (((size_t)b->table_keys * 12 + 15) & ~(size_t)15) + (((size_t)b->sbin_words * 4 + 15) & ~(size_t)15) +
+         sizeof(BatchHistDev) * b->hs.size();
+}
+
+// Upload descriptors for the current placement and locators; `tune` points
+// the accumulators at the scratch copies instead of the histograms'.
+int batch_upload(hist_batch* b) {
+  const int nh = (int)b->hs.size();
+  std::vector<BatchHistDev> real(nh), tune(nh);
+  std::vector<double*> st(nh), st_tune(nh);
+  for (int i = 0; i < nh; ++i) {
+    hist* h = b->hs[i];
+    BatchHistDev d;
+    std::memset(&d, 0, sizeof(d));
+    d.ax.T = h->d_T + h->t_off[0];
+    d.ax.nbins = h->nbins[0];
+    d.ax.mode = h->loc_mode[0];
+    d.ax.smem_off = b->t_off[i];
+    d.ax.scale = h->scale[0];
+    d.ax.offset = h->offset[0];
+    d.ax.eps = h->eps[0];
+    d.ax.lm = h->lm[0];
+    d.col = b->col[i];
+    d.group = b->group[i];
+    d.sbin_off = b->sbin_off[i];
+    d.g_lo = h->g_lo;
+    d.g_hi = h->g_hi;
+    d.g_unit = h->g_unit;
+    d.g_f64 = h->g_f64;
+    real[i] = d;
+    unsigned char* sc = static_cast<unsigned char*>(b->scratch[i]);
+    const size_t nbb = (size_t)(h->nbins[0] + 2) * 8;
+    d.g_lo = reinterpret_cast<unsigned long long*>(sc);
+    d.g_hi = reinterpret_cast<long long*>(sc + nbb);
+    d.g_unit = reinterpret_cast<unsigned long long*>(sc + 2 * nbb);
+    d.g_f64 = reinterpret_cast<double*>(sc + 3 * nbb);
+    tune[i] = d;
+    st[i] = h->g_stats;
+    st_tune[i] = reinterpret_cast<double*>(sc + 4 * nbb);
+  }
+  if (cudaMemcpy(b->d_desc, real.data(), sizeof(BatchHistDev) * nh, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_desc_tune, tune.data(), sizeof(BatchHistDev) * nh, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_stats, st.data(), sizeof(double*) * nh, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_stats_tune, st_tune.data(), sizeof(double*) * nh, cudaMemcpyHostToDevice) != cudaSuccess)
+    return HIST_ERR_CUDA;
+  b->built_versions.resize(nh);
+  for (int i = 0; i < nh; ++i) b->built_versions[i] = b->hs[i]->config_version;
+  if (b->exec) {  // descriptors are baked into a captured graph only by pointer; contents changed is fine
+  }
+  return HIST_OK;
+}
+
+int batch_configure(hist_batch* b, int budget) {
+  // the bins' budget is what remains of the per-block shared memory after
+  // the staged tables and the descriptors (and the kernel's static arrays)
+  int maxopt = 0;
+  if (cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess)
+    return HIST_ERR_CUDA;
+  const size_t fixed = (((size_t)b->table_keys * 12 + 15) & ~(size_t)15) + sizeof(BatchHistDev) * b->hs.size() + 16 +
+                       8 * 1024;
+  if ((size_t)maxopt <= fixed) return HIST_ERR_UNSUPPORTED;
+  if ((size_t)budget > (size_t)maxopt - fixed) budget = (int)((size_t)maxopt - fixed);
+  batch_place(b, budget);
+  b->smem = batch_smem_bytes(b);
+  int per_sm = 0;
+  if (batch_max_blocks_per_sm(256, b->smem, &per_sm) != 0 || per_sm < 1) return HIST_ERR_CUDA;
+  b->grid = per_sm * b->sm_count;
+  if (b->grid > b->part_blocks) {
+    cudaFree(b->d_part_stats);
+    b->d_part_stats = nullptr;
+    b->part_blocks = 0;
+    int rc = dalloc(&b->d_part_stats, (size_t)b->grid * kBatchMaxGroups * kMaxStats * sizeof(double));
+    if (rc != HIST_OK) return rc;
+    b->part_blocks = b->grid;
+  }
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return batch_upload(b);
+}
+
+int batch_check_args(const hist_batch* b, const double* const* cols, int ncols, const double* weights, int64_t n) {
+  if (cols == nullptr || n < 0 || ncols < b->ncols) return HIST_ERR_ARG;
+  for (int c = 0; c < b->ncols; ++c) {
+    if (n > 0 && cols[c] == nullptr) return HIST_ERR_ARG;
+    if (((uintptr_t)cols[c]) & 7u) return HIST_ERR_ALIGN;
+  }
+  if (((uintptr_t)weights) & 7u) return HIST_ERR_ALIGN;
+  return HIST_OK;
+}
+
+BatchParams batch_params(const hist_batch* b, const double* const* cols, const double* weights, int64_t n,
+                         bool tune) {
+  BatchParams p;
+  std::memset(&p, 0, sizeof(p));
+  for (int c = 0; c < b->ncols; ++c) p.col[c] = cols[c];
+  p.w = weights;
+  p.hists = tune ? b->d_desc_tune : b->d_desc;
+  p.T_concat = b->d_T;
+  p.part_stats = b->d_part_stats;
+  p.n = n;
+  p.ncols = b->ncols;
+  p.nh = (int)b->hs.size();
+  p.ngroups = kBatchMaxGroups;
+  p.fx_elo = kDefaultFxElo;
+  p.table_keys = b->table_keys;
+  p.sbin_words = b->sbin_words;
+  p.stat_overflows = (b->hs[0]->flags & HIST_STAT_OVERFLOWS) ? 1 : 0;
+  p.aligned = 1;
+  for (int c = 0; c <= kBatchMaxCols; ++c) p.col_begin[c] = b->col_begin[c];
+  for (int c = 0; c < kBatchMaxCols; ++c) p.ngroups_col[c] = b->ngroups_col[c];
+  for (int g = 0; g < kBatchMaxGroups; ++g) {
+    p.group_lo[g] = b->group_lo[g];
+    p.group_hi[g] = b->group_hi[g];
+  }
+  return p;
+}
+
+int batch_launch(const hist_batch* b, const BatchParams& p, bool tune, cudaStream_t s) {
+  if (launch_batch_fill(p, 256, b->grid, b->smem, s) != 0) return HIST_ERR_CUDA;
+  BatchReduceParams r;
+  std::memset(&r, 0, sizeof(r));
+  r.part_stats = b->d_part_stats;
+  r.nblocks = b->grid;
+  r.nh = (int)b->hs.size();
+  r.ngroups = kBatchMaxGroups;
+  r.nstats = 5;
+  r.hist_group = b->d_group;
+  r.hist_stats = tune ? b->d_stats_tune : b->d_stats;
+  if (launch_batch_reduce(r, s) != 0) return HIST_ERR_CUDA;
+  return HIST_OK;
+}
+
+}  // namespace
+
+extern "C" int hist_batch_create(hist_t* const* hists, int nh, const int32_t* col_of_hist, uint32_t flags,
+                                 hist_batch_t** out) {
+  if (out == nullptr || hists == nullptr || col_of_hist == nullptr || nh < 1 || nh > 128) return HIST_ERR_ARG;
+  if (flags & ~HIST_BATCH_GRAPH) return HIST_ERR_ARG;
+  *out = nullptr;
+  const uint32_t stat_flag = hists[0] ? (hists[0]->flags & HIST_STAT_OVERFLOWS) : 0;
+  for (int i = 0; i < nh; ++i) {
+    if (hists[i] == nullptr || col_of_hist[i] < 0 || col_of_hist[i] >= kBatchMaxCols) return HIST_ERR_ARG;
+    if (hists[i]->ndim != 1) return HIST_ERR_UNSUPPORTED;
+    if (hists[i]->device != hists[0]->device) return HIST_ERR_ARG;
+    if ((hists[i]->flags & HIST_STAT_OVERFLOWS) != stat_flag) return HIST_ERR_UNSUPPORTED;
+    for (int j = 0; j < i; ++j)
+      if (hists[j] == hists[i]) return HIST_ERR_ARG;
+  }
+  hist_batch* b = new (std::nothrow) hist_batch();
+  if (b == nullptr) return HIST_ERR_OOM;
+  int rc = HIST_OK;
+  do {
+    b->flags = flags;
+    b->device = hists[0]->device;
+    b->sm_count = hists[0]->sm_count;
+    if (cudaSetDevice(b->device) != cudaSuccess) {
+      rc = HIST_ERR_CUDA;
+      break;
+    }
+    std::vector<int> order(nh);
+    for (int i = 0; i < nh; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return col_of_hist[x] < col_of_hist[y]; });
+    for (int i : order) {
+      b->hs.push_back(hists[i]);
+      b->col.push_back(col_of_hist[i]);
+    }
+    b->ncols = b->col.back() + 1;
+    for (int c = 0; c <= kBatchMaxCols; ++c) {
+      int k = 0;
+      while (k < nh && b->col[k] < c) ++k;
+      b->col_begin[c] = k;
+    }
+    // statistics groups: distinct (column, range) pairs, at most two per column
+    b->group.assign(nh, 0);
+    for (int i = 0; i < nh; ++i) {
+      const hist* h = b->hs[i];
+      const long long lo = h->T_host[0][1], hi = h->T_host[0][h->nbins[0] + 1];
+      const int c = b->col[i];
+      int found = -1;
+      for (int j = 0; j < b->ngroups_col[c]; ++j) {
+        const int g = c * kBatchGroupsPerCol + j;
+        if (b->group_lo[g] == lo && b->group_hi[g] == hi) found = g;
+      }
+      if (found < 0) {
+        if (b->ngroups_col[c] >= kBatchGroupsPerCol) {
+          rc = HIST_ERR_UNSUPPORTED;
+          break;
+        }
+        found = c * kBatchGroupsPerCol + b->ngroups_col[c]++;
+        b->group_lo[found] = lo;
+        b->group_hi[found] = hi;
+      }
+      b->group[i] = found;
+    }
+    if (rc != HIST_OK) break;
+    // stage the smallest search tables
+    b->t_off.assign(nh, -1);
+    std::vector<int> by_size(nh);
+    for (int i = 0; i < nh; ++i) by_size[i] = i;
+    std::stable_sort(by_size.begin(), by_size.end(), [&](int x, int y) { return b->hs[x]->nbins[0] < b->hs[y]->nbins[0]; });
+    std::vector<int64_t> T;
+    for (int i : by_size) {
+      const std::vector<int64_t>& Th = b->hs[i]->T_host[0];
+      if (T.size() + Th.size() > (size_t)kBatchTableKeys) continue;
+      b->t_off[i] = (int)T.size();
+      T.insert(T.end(), Th.begin(), Th.end());
+    }
+    b->table_keys = (int)T.size();
+    if ((rc = dalloc(&b->d_T, std::max<size_t>(T.size(), 1) * 8)) != HIST_OK) break;
+    if (!T.empty() && cudaMemcpy(b->d_T, T.data(), T.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+      rc = HIST_ERR_CUDA;
+      break;
+    }
+    if ((rc = dalloc(&b->d_desc, sizeof(BatchHistDev) * nh)) != HIST_OK) break;
+    if ((rc = dalloc(&b->d_desc_tune, sizeof(BatchHistDev) * nh)) != HIST_OK) break;
+    if ((rc = dalloc(&b->d_group, sizeof(int) * nh)) != HIST_OK) break;
+    if ((rc = dalloc(&b->d_stats, sizeof(double*) * nh)) != HIST_OK) break;
+    if ((rc = dalloc(&b->d_stats_tune, sizeof(double*) * nh)) != HIST_OK) break;
+    if (cudaMemcpy(b->d_group, b->group.data(), sizeof(int) * nh, cudaMemcpyHostToDevice) != cudaSuccess) {
+      rc = HIST_ERR_CUDA;
+      break;
+    }
+    for (int i = 0; i < nh && rc == HIST_OK; ++i) {
+      void* q = nullptr;
+      rc = dalloc(&q, (size_t)(b->hs[i]->nbins[0] + 2) * 32 + kMaxStats * sizeof(double));
+      if (rc == HIST_OK) b->scratch.push_back(q);
+    }
+    if (rc != HIST_OK) break;
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+      rc = HIST_ERR_CUDA;
+      break;
+    }
+    rc = batch_configure(b, 96 * 1024);
+  } while (false);
+  if (rc != HIST_OK) {
+    batch_release(b);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return HIST_OK;
+}
+
+extern "C" void hist_batch_free(hist_batch_t* b) {
+  if (b == nullptr) return;
+  cudaSetDevice(b->device);
+  batch_release(b);  // waits for the batch's own last work; never touches the member histograms
+  delete b;
+}
+
+extern "C" int hist_batch_fill(hist_batch_t* b, const double* const* cols, int ncols, const double* weights,
+                               int64_t n, hist_stream_t stream) {
+  if (b == nullptr) return HIST_ERR_ARG;
+  int rc = batch_check_args(b, cols, ncols, weights, n);
+  if (rc != HIST_OK || n == 0) return rc;
+  if (cudaSetDevice(b->device) != cudaSuccess) return HIST_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (size_t i = 0; i < b->hs.size(); ++i)
+    if (b->hs[i]->config_version != b->built_versions[i]) {
+      if ((rc = batch_upload(b)) != HIST_OK) return rc;
+      break;
+    }
+  for (hist* h : b->hs)
+    if ((rc = order_after_previous(h, s)) != HIST_OK) return rc;
+  const BatchParams p = batch_params(b, cols, weights, n, false);
+  if (b->flags & HIST_BATCH_GRAPH) {
+    std::vector<const double*> cv(cols, cols + b->ncols);
+    if (b->exec == nullptr || cv != b->g_cols || weights != b->g_w || n != b->g_n) {
+      if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+      }
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HIST_ERR_CUDA;
+      rc = batch_launch(b, p, false, b->cap_stream);
+      if (cudaStreamEndCapture(b->cap_stream, &graph) != cudaSuccess || rc != HIST_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return HIST_ERR_CUDA;
+      }
+      const cudaError_t e = cudaGraphInstantiate(&b->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        b->exec = nullptr;
+        return HIST_ERR_CUDA;
+      }
+      b->g_cols = cv;
+      b->g_w = weights;
+      b->g_n = n;
+    }
+    if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return HIST_ERR_CUDA;
+  } else {
+    if ((rc = batch_launch(b, p, false, s)) != HIST_OK) return rc;
+  }
+  if (cudaEventRecord(b->done, s) != cudaSuccess) return HIST_ERR_CUDA;
+  b->have_done = true;
+  for (hist* h : b->hs) {
+    if (cudaEventRecord(h->done, s) != cudaSuccess) return HIST_ERR_CUDA;
+    h->have_done = true;
+    h->n_entries += n;
+    if (weights != nullptr && !(h->flags & HIST_TRACK_COUNTS)) h->counts_complete = false;
+    if (weights != nullptr) {
+      // direct global adds grow g_lo by < 2^32 per event: fold before 2^31 events
+      h->fx_global_since_norm += n;
+      if (h->fx_global_since_norm > (int64_t)1 << 31) {
+        if (launch_normalize_fx(h->g_lo, h->g_hi, h->nbins_total, s) != 0) return HIST_ERR_CUDA;
+        h->fx_global_since_norm = 0;
+      }
+    }
+  }
+  if (weights != nullptr)
+    for (hist* h : b->hs)
+      if (h->flags & HIST_TRACK_COUNTS) h->counts_complete = false;  // batches do not count weighted entries
+  return HIST_OK;
+}
+
+extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int ncols, const double* weights,
+                               int64_t n, hist_batch_tuning_t* report) {
+  if (b == nullptr || n <= 0) return HIST_ERR_ARG;
+  int rc = batch_check_args(b, cols, ncols, weights, n);
+  if (rc != HIST_OK) return rc;
+  if (cudaSetDevice(b->device) != cudaSuccess) return HIST_ERR_CUDA;
+  for (hist* h : b->hs)
+    if (h->have_done && cudaEventSynchronize(h->done) != cudaSuccess) return HIST_ERR_CUDA;
+  const int budgets[] = {16 * 1024, 48 * 1024, 96 * 1024, 144 * 1024, 200 * 1024};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HIST_ERR_CUDA;
+  double best = 1e300, worst = 0.0;
+  int best_budget = b->smem_budget, tried = 0;
+  int last_budget = -1;
+  for (int budget : budgets) {
+    if ((rc = batch_configure(b, budget)) != HIST_OK) break;
+    if (b->smem_budget == last_budget) continue;
+    last_budget = b->smem_budget;
+    budget = b->smem_budget;
+    const BatchParams p = batch_params(b, cols, weights, n, true);
+    if ((rc = batch_launch(b, p, true, nullptr)) != HIST_OK) break;  // warm-up
+    cudaEventRecord(e0, nullptr);
+    for (int r = 0; r < 3 && rc == HIST_OK; ++r) rc = batch_launch(b, p, true, nullptr);
+    cudaEventRecord(e1, nullptr);
+    if (rc != HIST_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = HIST_ERR_CUDA;
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= 3.0f;
+    ++tried;
+    if (ms < best) {
+      best = ms;
+      best_budget = budget;
+    }
+    worst = std::max(worst, (double)ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaDeviceSynchronize() != cudaSuccess) return HIST_ERR_CUDA;
+  if (rc != HIST_OK) return rc;
+  if ((rc = batch_configure(b, best_budget)) != HIST_OK) return rc;
+  if (report) {
+    report->candidates = tried;
+    report->smem_bytes = best_budget;
+    int per_sm = 0;
+    batch_max_blocks_per_sm(256, b->smem, &per_sm);
+    report->blocks_per_sm = per_sm;
+    int nsm = 0;
+    for (int o : b->sbin_off) nsm += (o >= 0);
+    report->smem_hists = nsm;
+    report->best_ms = best;
+    report->worst_ms = worst;
+  }
+  return HIST_OK;
 }

@@ -96,6 +96,52 @@ struct ReduceParams {
   double* g_stats;
 };
 
+// ---- batched fill: many 1D histograms from one event stream -------------
+constexpr int kBatchMaxCols = 4;       // columns per batch
+constexpr int kBatchGroupsPerCol = 2;  // statistics ranges per column
+constexpr int kBatchMaxGroups = kBatchMaxCols * kBatchGroupsPerCol;
+
+struct BatchHistDev {
+  AxisDev ax;                   // T: global thresholds; smem_off: staged keys (-1: global)
+  int32_t col;                  // column read by this histogram
+  int32_t group;                // statistics group (same column and range)
+  int32_t sbin_off;             // word offset of its per-block bins in shared memory, -1: global atomics
+  int32_t pad;
+  unsigned long long* g_lo;     // the histogram's accumulators (or tuning scratch)
+  long long* g_hi;
+  unsigned long long* g_unit;
+  double* g_f64;
+};
+
+struct BatchParams {
+  const double* col[kBatchMaxCols];
+  const double* w;              // nullptr: unit weights
+  const BatchHistDev* hists;    // device [nh]
+  const long long* T_concat;    // staged keys of all staged axes, back to back
+  double* part_stats;           // [grid][kBatchMaxGroups][kMaxStats]
+  long long n;
+  int32_t ncols, nh, ngroups, fx_elo;
+  int32_t table_keys;           // staged keys (8-byte keys + 4-byte high words each)
+  int32_t sbin_words;           // shared-memory words of all block-private bins
+  int32_t stat_overflows;
+  int32_t aligned;
+  int32_t col_begin[kBatchMaxCols + 1];  // histograms sorted by column: [col_begin[c], col_begin[c+1])
+  int32_t ngroups_col[kBatchMaxCols];    // statistics groups of column c: ids c * kBatchGroupsPerCol + j
+  long long group_lo[kBatchMaxGroups];   // statistics range of a group: key in [lo, hi)
+  long long group_hi[kBatchMaxGroups];
+};
+
+struct BatchReduceParams {
+  const double* part_stats;
+  int32_t nblocks, nh, ngroups, nstats;
+  const int* hist_group;        // device [nh]
+  double* const* hist_stats;    // device [nh] pointers to each histogram's statistics
+};
+
+int launch_batch_fill(const BatchParams& p, int block, int grid, size_t smem, void* stream);
+int batch_max_blocks_per_sm(int block, size_t smem, int* per_sm);
+int launch_batch_reduce(const BatchReduceParams& r, void* stream);
+
 // Launchers (fill_kernels.cu).
 struct LaunchShape {
   int grid;
@@ -118,5 +164,6 @@ int launch_lm_adam(float* theta, float* m1, float* m2, const float* grad, int co
 int launch_lm_pack(const int* base, const float* theta, int2* knots, int count, void* stream);
 int launch_lm_certify(const LearnedDev& m, const long long* T, int nbins, int* max_err, void* stream);
 size_t part_bin_bytes(int acc_mode, int track_counts);
+size_t smem_bin_bytes(int acc_mode, int track_counts);  // per bin, block-private shared memory
 
 }  // namespace hgb
