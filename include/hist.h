@@ -139,20 +139,31 @@ int hist_locate(hist_t *h, const double *values, int64_t n, int64_t *out, hist_s
  * The paper's conclusion names computing several histograms from the same
  * data, and its kernels being small and launch-bound, as the next step.  A
  * batch fills up to 128 booked 1D histograms from up to 4 columns and one
- * weight column in one fused launch: each column and weight is read once
- * per event; small histograms keep exact per-block bins in shared memory,
- * large ones use exact global integer atomics; histograms that share a
- * column and range share their statistics sums.  Results and accuracy per
- * histogram are those of hist_fill_bulk. */
+ * weight column in one fused launch, with one of two privatisation
+ * strategies:
+ *   wide   -- every block fills every histogram from its share of the
+ *             events; small histograms keep exact per-block bins in shared
+ *             memory, large ones use exact global integer atomics;
+ *   sliced -- the batch's bins are cut into slices of one block's shared
+ *             memory (large histograms span several slices); each block
+ *             fills one slice from a share of the events, every bin stays
+ *             in shared memory, and the slices sweep the event stream
+ *             together so that each event is read from HBM once (from L2
+ *             by the other slices).
+ * Histograms that share a column and range share their statistics sums.
+ * Results and accuracy per histogram are those of hist_fill_bulk. */
 typedef struct hist_batch hist_batch_t;
 
-#define HIST_BATCH_GRAPH (1u << 0) /* replay the fill's launches as a cached CUDA graph */
+#define HIST_BATCH_GRAPH (1u << 0)  /* replay the fill's launches as a cached CUDA graph */
+#define HIST_BATCH_WIDE (1u << 1)   /* start with the wide strategy (default: sliced when the */
+#define HIST_BATCH_SLICED (1u << 2) /* bins outgrow one block's shared memory, else wide) */
 
 /* Build a batch over hists[0..nh) (all 1D, same device); histogram i reads
- * column col_of_hist[i] (0..3).  At most 2 distinct axis ranges per column.
+ * column col_of_hist[i] (0..3).  At most 16 distinct (column, axis range)
+ * pairs (statistics groups).
  * The batch references the histograms (they must outlive it) and owns its
  * device descriptors and scratch.  Errors: HIST_ERR_ARG, HIST_ERR_UNSUPPORTED
- * (ND histogram, too many ranges per column), HIST_ERR_OOM, HIST_ERR_CUDA. */
+ * (ND histogram, more than 16 statistics groups), HIST_ERR_OOM, HIST_ERR_CUDA. */
 int hist_batch_create(hist_t *const *hists, int nh, const int32_t *col_of_hist, uint32_t flags,
                       hist_batch_t **out);
 
@@ -171,15 +182,31 @@ typedef struct {
   int32_t smem_hists;      /* histograms kept in shared memory */
   double best_ms;          /* time of the chosen configuration on the sample */
   double worst_ms;         /* slowest candidate */
+  int32_t strategy;        /* chosen strategy: 0 wide, 1 sliced */
+  int32_t slices;          /* sliced: slices of the chosen plan (0 for wide) */
+  int32_t replicas;        /* sliced: blocks per slice */
+  int32_t cost_cap_tenths; /* sliced: work cap per slice of the chosen plan, tenths of one histogram */
 } hist_batch_tuning_t;
 
-/* Autotune the batch: time the candidate privatisation budgets (which
- * histograms keep shared-memory bins) and occupancies on the given sample of
+/* Autotune the batch: time the candidate strategies, shared-memory budgets
+ * (which histograms keep shared-memory bins; the slice size) and work caps
+ * per slice, each with the occupancy it allows, on the given sample of
  * events, writing into scratch accumulators (the member histograms are not
  * changed), and keep the fastest for later fills.  Synchronous.  report may
  * be NULL.  Errors: as hist_batch_fill. */
 int hist_batch_tune(hist_batch_t *b, const double *const *cols, int ncols, const double *weights, int64_t n,
                     hist_batch_tuning_t *report);
+
+/* Pin the batch's configuration instead of tuning it: strategy 0 (wide) or
+ * 1 (sliced), the shared-memory budget per block in bytes, and for the
+ * sliced strategy the work cap per slice in tenths of one histogram's
+ * locate-and-add and the pacing window in tiles of 2048 events (-1 the
+ * default, 0 no pacing).  info (may be NULL) receives the resulting plan
+ * (with best_ms = worst_ms = 0).  Waits for the batch's earlier fills.
+ * Errors: HIST_ERR_ARG, HIST_ERR_UNSUPPORTED (the plan does not fit one
+ * block's shared memory), HIST_ERR_OOM, HIST_ERR_CUDA. */
+int hist_batch_configure(hist_batch_t *b, int32_t strategy, int32_t smem_bytes, int32_t cost_cap_tenths,
+                         int32_t pace_tiles, hist_batch_tuning_t *info);
 
 /* Release the batch (not its histograms).  NULL is a no-op. */
 void hist_batch_free(hist_batch_t *b);

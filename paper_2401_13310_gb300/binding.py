@@ -64,10 +64,14 @@ class hist_locator_report_t(ctypes.Structure):
 class hist_batch_tuning_t(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("smem_hists", ctypes.c_int32),
-                ("best_ms", ctypes.c_double), ("worst_ms", ctypes.c_double)]
+                ("best_ms", ctypes.c_double), ("worst_ms", ctypes.c_double),
+                ("strategy", ctypes.c_int32), ("slices", ctypes.c_int32),
+                ("replicas", ctypes.c_int32), ("cost_cap_tenths", ctypes.c_int32)]
 
 
 HIST_BATCH_GRAPH = 1 << 0
+HIST_BATCH_WIDE = 1 << 1
+HIST_BATCH_SLICED = 1 << 2
 
 
 class hist_axis_t(ctypes.Structure):
@@ -110,6 +114,8 @@ def load(path: str | None = None):
             "hist_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_uint32, _P]),
             "hist_batch_fill": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
             "hist_batch_tune": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
+            "hist_batch_configure": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                    ctypes.c_int32, _P]),
             "hist_batch_free": (None, [_P]),
             "hist_locator_loss_grad": (ctypes.c_int, [ctypes.c_int, ctypes.c_float, ctypes.c_float, _P, _P, _P,
                                                       _P, ctypes.c_int64, _P, _P]),
@@ -302,6 +308,14 @@ def hist_batch_tune(b: int, cols, weights, n: int) -> dict:
     return {f: getattr(r, f) for f, _ in hist_batch_tuning_t._fields_}
 
 
+def hist_batch_configure(b: int, strategy: int, smem_bytes: int, cost_cap_tenths: int = 30,
+                         pace_tiles: int = -1) -> dict:
+    r = hist_batch_tuning_t()
+    _check(load().hist_batch_configure(b, int(strategy), int(smem_bytes), int(cost_cap_tenths), int(pace_tiles),
+                                       ctypes.byref(r)), "hist_batch_configure")
+    return {f: getattr(r, f) for f, _ in hist_batch_tuning_t._fields_}
+
+
 def hist_batch_free(b: int) -> None:
     load().hist_batch_free(b)
 
@@ -319,6 +333,9 @@ class Batch:
 
     def tune(self, cols, weights=None) -> dict:
         return hist_batch_tune(self.b, list(cols), weights, int(cols[0].shape[-1]))
+
+    def configure(self, strategy: int, smem_bytes: int, cost_cap_tenths: int = 30, pace_tiles: int = -1) -> dict:
+        return hist_batch_configure(self.b, strategy, smem_bytes, cost_cap_tenths, pace_tiles)
 
     def close(self) -> None:
         if self.b:

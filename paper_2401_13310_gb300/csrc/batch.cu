@@ -17,17 +17,16 @@
 //    so the order does not matter);
 //  * large histograms add every event to the global accumulators with two
 //    64-bit integer atomics (exact);
-//  * statistics depend only on the column, the weight and the in-range test,
-//    so histograms with the same column and range share one statistics
-//    group, accumulated in binary64 per thread (the binary64 pipe is
-//    otherwise idle in this compute-bound kernel: a few operations per
-//    event against thousands of others), reduced per block in a fixed order
-//    and added to every member histogram by a second kernel.
+//  * statistics are shared by the histograms with the same column and range
+//    and accumulated once per event for the column's common core (see
+//    batch_stats.cuh), binary64 per thread: the binary64 pipe is otherwise
+//    idle in this kernel; a second kernel adds each histogram's sums.
 
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
+#include "batch_stats.cuh"
 #include "device_common.cuh"
 #include "hist_internal.h"
 
@@ -35,12 +34,6 @@ namespace hgb {
 namespace {
 
 constexpr int kEv = 4;  // events per thread per iteration
-
-// binary64 statistics of one group: sum w^2 (or nothing for unit weights),
-// sum wx, sum wx^2 -- terms rounded as in the definition.
-struct GroupStats {
-  double s2, s3, s4;
-};
 
 template <bool UNIT, bool SMEM>
 __device__ __forceinline__ void batch_add(const BatchHistDev& d, unsigned* sbins, int k, long long V, bool wok,
@@ -88,7 +81,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_fill(const __grid_constant__ B
   unsigned* sbins = reinterpret_cast<unsigned*>(smem_raw + off_bins);
   const size_t off_desc = off_bins + (((size_t)p.sbin_words * 4 + 15) & ~(size_t)15);
   BatchHistDev* sdesc = reinterpret_cast<BatchHistDev*>(smem_raw + off_desc);
-  __shared__ double sred[8][kBatchMaxGroups * 3];
+  __shared__ double sred[8 * kStatSlots * 3];
 
   for (int i = threadIdx.x; i < nkeys; i += blockDim.x) {
     const long long t = p.T_concat[i];
@@ -104,9 +97,11 @@ __global__ void __launch_bounds__(256, 2) k_batch_fill(const __grid_constant__ B
   }
   __syncthreads();
 
-  GroupStats gs[kBatchMaxGroups];
+  double core[kBatchMaxCols][3];
 #pragma unroll
-  for (int g = 0; g < kBatchMaxGroups; ++g) gs[g].s2 = gs[g].s3 = gs[g].s4 = 0.0;
+  for (int c = 0; c < kBatchMaxCols; ++c) core[c][0] = core[c][1] = core[c][2] = 0.0;
+  double tail[kBatchMaxGroups * 3];
+  for (int t = 0; t < kBatchMaxGroups * 3; ++t) tail[t] = 0.0;
 
   const long long n = p.n;
   const long long nthreads = (long long)gridDim.x * blockDim.x;
@@ -156,24 +151,11 @@ __global__ void __launch_bounds__(256, 2) k_batch_fill(const __grid_constant__ B
             batch_add<UNIT, false>(d, sbins, k, V[e], wok[e], wb[e]);
         }
       }
-      // statistics groups of this column
+      // statistics of this column
+      if (p.st.group_begin[c] < p.st.group_begin[c + 1]) {
 #pragma unroll
-      for (int j = 0; j < kBatchGroupsPerCol; ++j) {
-        if (j >= p.ngroups_col[c]) break;
-        const int g = c * kBatchGroupsPerCol + j;
-        const long long lo = p.group_lo[g], hi = p.group_hi[g];
-#pragma unroll
-        for (int e = 0; e < kEv; ++e) {
-          if (!valid[e]) continue;
-          const long long key = key_of(xb[e]);
-          if (!(p.stat_overflows || (key >= lo && key < hi))) continue;
-          const double x = __longlong_as_double((long long)xb[e]);
-          const double w = __longlong_as_double((long long)wb[e]);
-          const double wx = UNIT ? x : __dmul_rn(w, x);
-          if (!UNIT) gs[g].s2 = __fma_rn(w, w, gs[g].s2);
-          gs[g].s3 = __dadd_rn(gs[g].s3, wx);
-          gs[g].s4 = __fma_rn(wx, x, gs[g].s4);
-        }
+        for (int e = 0; e < kEv; ++e)
+          if (valid[e]) stat_event<UNIT>(p.st, c, key_of(xb[e]), xb[e], wb[e], core[c], tail);
       }
     }
   }
@@ -196,37 +178,24 @@ __global__ void __launch_bounds__(256, 2) k_batch_fill(const __grid_constant__ B
     }
   }
   // per-block statistics partials, one fixed reduction order
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-#pragma unroll
-  for (int g = 0; g < kBatchMaxGroups; ++g) {
-    double v[3] = {gs[g].s2, gs[g].s3, gs[g].s4};
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v[q] = __dadd_rn(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
-      if (lane == 0) sred[warp][g * 3 + q] = v[q];
-    }
-  }
   __syncthreads();
-  for (int t = threadIdx.x; t < kBatchMaxGroups * 3; t += blockDim.x) {
-    double v = 0.0;
-    for (int wi = 0; wi < nwarps; ++wi) v = __dadd_rn(v, sred[wi][t]);
-    const int g = t / 3, q = t % 3;
-    p.part_stats[((size_t)blockIdx.x * kBatchMaxGroups + g) * kMaxStats + 2 + q] = v;
-  }
+  block_stats_store(core, tail, sred, p.part_stats + (size_t)blockIdx.x * kStatSlots * 3);
 }
 
-// Thread (h, k) adds statistic k of histogram h's group, summed over the
-// blocks in order, into the histogram's statistics.
+// Thread (h, q) adds statistic 2 + q of histogram h: its column's core sum
+// plus its group's tail sum, block partials taken in block order.
 __global__ void k_batch_reduce(const BatchReduceParams r) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int h = t / 3, q = t % 3;
   if (h >= r.nh) return;
-  const int g = r.hist_group[h];
-  const int k = 2 + q;
+  const int c = r.hist_col[h], g = r.hist_group[h];
   double s = 0.0;
-  for (int b = 0; b < r.nblocks; ++b) s = __dadd_rn(s, r.part_stats[((size_t)b * kBatchMaxGroups + g) * kMaxStats + k]);
-  r.hist_stats[h][k] = __dadd_rn(r.hist_stats[h][k], s);
+  for (int b = 0; b < r.nblocks; ++b) {
+    const double* part = r.part_stats + (size_t)b * kStatSlots * 3;
+    s = __dadd_rn(s, part[c * 3 + q]);
+    s = __dadd_rn(s, part[(kBatchMaxCols + g) * 3 + q]);
+  }
+  r.hist_stats[h][2 + q] = __dadd_rn(r.hist_stats[h][2 + q], s);
 }
 
 }  // namespace

@@ -198,21 +198,6 @@ __device__ __forceinline__ void block_reduce_stats(const double* d, double* out,
 
 // ---------------------------------------------------------------- loads
 
-// Two consecutive binary64 values as raw bits (no double-typed value ever
-// flows through the hot loop, so nothing can be scheduled on the binary64
-// pipe by accident).
-__device__ __forceinline__ void load_pair(const double* __restrict__ p, long long i, bool vec, bool two,
-                                          unsigned long long& a, unsigned long long& b) {
-  const unsigned long long* q = reinterpret_cast<const unsigned long long*>(p);
-  if (vec && two) {
-    const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(q + i));
-    a = v.x;
-    b = v.y;
-  } else {
-    a = __ldcs(q + i);
-    b = two ? __ldcs(q + i + 1) : 0ull;
-  }
-}
 
 // ---------------------------------------------------------------- fill kernel
 

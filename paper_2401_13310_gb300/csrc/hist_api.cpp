@@ -15,6 +15,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -699,8 +700,8 @@ struct hist_batch {
   int device = 0, sm_count = 0;
   uint32_t flags = 0;
   int col_begin[kBatchMaxCols + 1] = {};
-  int ngroups_col[kBatchMaxCols] = {};
-  long long group_lo[kBatchMaxGroups] = {}, group_hi[kBatchMaxGroups] = {};
+  BatchStatsSpec st = {};     // statistics groups and the cores of the columns
+  int group_col[kBatchMaxGroups] = {};
   std::vector<int> group;    // statistics group of each member
   // staged threshold tables
   long long* d_T = nullptr;
@@ -710,6 +711,7 @@ struct hist_batch {
   BatchHistDev* d_desc = nullptr;
   BatchHistDev* d_desc_tune = nullptr;
   int* d_group = nullptr;
+  int* d_col = nullptr;
   double** d_stats = nullptr;
   double** d_stats_tune = nullptr;
   std::vector<int> built_versions;
@@ -725,6 +727,27 @@ struct hist_batch {
   int sbin_words = 0;
   cudaEvent_t done = nullptr;  // completion of the batch's last fill or tuning run
   bool have_done = false;
+  // strategy: 0 wide (batch.cu), 1 sliced (batch_slices.cu)
+  int strategy = 0;
+  // sliced plan
+  std::vector<SliceDev> slices;
+  std::vector<SliceFragDev> frags;        // pointers filled at upload
+  std::vector<int> frag_member;           // member of each fragment
+  std::vector<int64_t> slice_keys;
+  int max_frags = 0, max_keys = 0, max_words = 0;
+  size_t own_bytes = 0;                   // largest slice's own keys, bins and fragments
+  int shared_frags = 0, shared_keys = 0, shared_words = 0;
+  int shared_col_begin[kBatchMaxCols + 1] = {};
+  int slice_replicas = 1, slice_window = 0;
+  int pace_tiles = -1;                    // pacing window in tiles: -1 default, 0 off
+  double slice_cap = 0.0;
+  SliceDev* d_slices = nullptr;
+  SliceFragDev* d_frags = nullptr;
+  SliceFragDev* d_frags_tune = nullptr;
+  long long* d_slice_keys = nullptr;
+  int* d_done = nullptr;
+  long long done_cap = 0;
+  size_t slices_cap = 0, frags_cap = 0, keys_cap = 0;
   // graph cache
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -746,9 +769,15 @@ void batch_release(hist_batch* b) {
   cudaFree(b->d_desc);
   cudaFree(b->d_desc_tune);
   cudaFree(b->d_group);
+  cudaFree(b->d_col);
   cudaFree(b->d_stats);
   cudaFree(b->d_stats_tune);
   cudaFree(b->d_part_stats);
+  cudaFree(b->d_slices);
+  cudaFree(b->d_frags);
+  cudaFree(b->d_frags_tune);
+  cudaFree(b->d_slice_keys);
+  cudaFree(b->d_done);
   for (void* q : b->scratch) cudaFree(q);
 }
 
@@ -779,6 +808,7 @@ size_t batch_smem_bytes(const hist_batch* b) {
 // Upload descriptors for the current placement and locators; `tune` points
 // the accumulators at the scratch copies instead of the histograms'.
 int batch_upload(hist_batch* b) {
+  if (b->have_done && cudaEventSynchronize(b->done) != cudaSuccess) return HIST_ERR_CUDA;
   const int nh = (int)b->hs.size();
   std::vector<BatchHistDev> real(nh), tune(nh);
   std::vector<double*> st(nh), st_tune(nh);
@@ -824,6 +854,276 @@ int batch_upload(hist_batch* b) {
   return HIST_OK;
 }
 
+// ---- sliced strategy: planning (see batch_slices.cu) ----
+constexpr double kSliceTestCost = 0.15;  // key range test of a split fragment, in units of one locate + add
+constexpr double kSliceEventCost = 0.5;  // loading and converting one event, per slice
+constexpr double kSliceStatCost = 0.3;   // one statistics group
+constexpr long long kSliceMinFragBins = 64;
+constexpr int kSliceBlock = 512, kSliceTile = 2048;
+constexpr int kSliceDefaultBudget = 96 * 1024;
+constexpr double kSliceDefaultCap = 3.0;
+constexpr int kSliceDefaultWindow = 512;  // tiles of 2048 events: 32 MB of four columns
+
+SliceFragDev slice_frag(const hist* h, long long a, long long m) {
+  SliceFragDev d;
+  std::memset(&d, 0, sizeof(d));
+  d.ax.T = h->d_T + h->t_off[0];
+  d.ax.nbins = h->nbins[0];
+  d.ax.mode = h->loc_mode[0];
+  d.ax.smem_off = -1;
+  d.ax.scale = h->scale[0];
+  d.ax.offset = h->offset[0];
+  d.ax.eps = h->eps[0];
+  d.ax.lm = h->lm[0];
+  d.a = (int)a;
+  d.b = (int)(a + m);
+  d.Ta = h->T_host[0][a];
+  d.Tb = h->T_host[0][a + m];
+  d.whole = (a == 0 && m == h->nbins[0] + 2) ? 1 : 0;
+  return d;
+}
+
+// Stage the fragment's keys (non-affine axes) and reserve its bins.
+void slice_place(const hist* h, SliceFragDev& d, std::vector<int64_t>& keys, int* nkeys, int* nwords) {
+  d.bin_off = *nwords;
+  *nwords += 2 * (d.b - d.a);
+  if (h->loc_mode[0] == LOC_AFFINE) {
+    d.key_off = -1;
+    d.top = 0;
+    return;
+  }
+  d.key_off = *nkeys;
+  const int nint = d.b - d.a - 1;
+  for (int k = d.a + 1; k < d.b; ++k) keys.push_back(h->T_host[0][k]);
+  *nkeys += nint;
+  int top = nint > 0 ? 1 : 0;
+  while (nint > 0 && top * 2 <= nint) top *= 2;
+  d.top = top;
+}
+
+// The plan: the smallest members (up to `shared_cap` bytes) are held whole
+// by every block; the others are cut into slices of at most `budget` bytes
+// (with the shared part) and about `cap` units of per-event work, a whole
+// histogram costing one unit and a fragment its range test plus its share
+// of the bins.
+void slice_plan(hist_batch* b, int budget, double cap) {
+  b->slices.clear();
+  b->frags.clear();
+  b->frag_member.clear();
+  b->slice_keys.clear();
+  const long long desc = (long long)sizeof(SliceFragDev);
+  const int nh = (int)b->hs.size();
+  auto bytes_of = [&](int i) {
+    const hist* h = b->hs[i];
+    return (long long)(h->nbins[0] + 2) * (h->loc_mode[0] == LOC_AFFINE ? 8 : 16) + desc;
+  };
+  // shared members: smallest first, up to half the budget
+  std::vector<int> order(nh);
+  for (int i = 0; i < nh; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->hs[x]->nbins[0] < b->hs[y]->nbins[0]; });
+  std::vector<char> shared(nh, 0);
+  long long used = 0;
+  for (int i : order) {
+    if (used + bytes_of(i) > budget / 2) break;
+    shared[i] = 1;
+    used += bytes_of(i);
+  }
+  int nkeys = 0, nwords = 0;
+  for (int c = 0; c <= kBatchMaxCols; ++c) b->shared_col_begin[c] = 0;
+  for (int c = 0; c < kBatchMaxCols; ++c) {
+    b->shared_col_begin[c] = (int)b->frags.size();
+    for (int i = b->col_begin[c]; i < b->col_begin[c + 1]; ++i) {
+      if (!shared[i]) continue;
+      SliceFragDev d = slice_frag(b->hs[i], 0, b->hs[i]->nbins[0] + 2);
+      slice_place(b->hs[i], d, b->slice_keys, &nkeys, &nwords);
+      b->frags.push_back(d);
+      b->frag_member.push_back(i);
+    }
+  }
+  b->shared_col_begin[kBatchMaxCols] = (int)b->frags.size();
+  b->shared_frags = (int)b->frags.size();
+  b->shared_keys = nkeys;
+  b->shared_words = nwords;
+  const long long room_all = (long long)budget - used;
+  // slices of the other members, column by column, smallest first
+  for (int c = 0; c < b->ncols; ++c) {
+    std::vector<int> mem;
+    for (int i = b->col_begin[c]; i < b->col_begin[c + 1]; ++i)
+      if (!shared[i]) mem.push_back(i);
+    std::stable_sort(mem.begin(), mem.end(), [&](int x, int y) { return b->hs[x]->nbins[0] < b->hs[y]->nbins[0]; });
+    SliceDev cur;
+    std::memset(&cur, 0, sizeof(cur));
+    bool open = false;
+    double cost = 0.0;
+    long long bytes = 0;
+    auto open_slice = [&]() {
+      std::memset(&cur, 0, sizeof(cur));
+      cur.col = c;
+      cur.frag_begin = cur.frag_end = (int)b->frags.size();
+      cur.key_base = (int)b->slice_keys.size();
+      cost = kSliceEventCost;
+      bytes = 0;
+      open = true;
+    };
+    auto close_slice = [&]() {
+      if (open && cur.frag_end > cur.frag_begin) b->slices.push_back(cur);
+      open = false;
+    };
+    for (int i : mem) {
+      const hist* h = b->hs[i];
+      const long long nbt = h->nbins[0] + 2;
+      const long long per_bin = h->loc_mode[0] == LOC_AFFINE ? 8 : 16;
+      long long a = 0;
+      while (a < nbt) {
+        if (!open) open_slice();
+        const bool fresh = cur.frag_end == cur.frag_begin;
+        const long long rest = nbt - a;
+        const long long by_bytes = std::max(0LL, (room_all - bytes - desc) / per_bin);
+        const double room = cap - cost;
+        long long m;
+        if (a == 0 && rest <= by_bytes && room >= 1.0)
+          m = rest;
+        else
+          m = std::min(std::min(rest, by_bytes), (long long)std::max(0.0, (room - kSliceTestCost) * (double)nbt));
+        if (fresh)
+          m = std::max(m, std::min(rest, std::max(1LL, by_bytes)));
+        else if (m < std::min(rest, kSliceMinFragBins)) {
+          close_slice();
+          continue;
+        }
+        SliceFragDev d = slice_frag(h, a, m);
+        int nk = cur.nkeys, nw = cur.nwords;
+        slice_place(h, d, b->slice_keys, &nk, &nw);
+        cur.nkeys = nk;
+        cur.nwords = nw;
+        b->frags.push_back(d);
+        b->frag_member.push_back(i);
+        cur.frag_end = (int)b->frags.size();
+        cost += d.whole ? 1.0 : kSliceTestCost + (double)m / (double)nbt;
+        bytes += per_bin * m + desc;
+        a += m;
+      }
+    }
+    close_slice();
+  }
+  if (b->slices.empty()) {  // everything is shared: one slice without fragments of its own
+    SliceDev d;
+    std::memset(&d, 0, sizeof(d));
+    d.col = b->col[0];
+    d.frag_begin = d.frag_end = (int)b->frags.size();
+    d.key_base = (int)b->slice_keys.size();
+    b->slices.push_back(d);
+  }
+  b->max_frags = b->max_keys = b->max_words = 0;
+  b->own_bytes = 0;
+  for (const SliceDev& sd : b->slices) {
+    b->max_frags = std::max(b->max_frags, sd.frag_end - sd.frag_begin);
+    b->max_keys = std::max(b->max_keys, sd.nkeys);
+    b->max_words = std::max(b->max_words, sd.nwords);
+    b->own_bytes = std::max(b->own_bytes, slice_smem_bytes(sd.nkeys, sd.nwords, sd.frag_end - sd.frag_begin));
+  }
+  b->slice_cap = cap;
+}
+
+// Upload the slice plan with the accumulators of the members (and of their
+// tuning scratch).
+int slice_upload(hist_batch* b) {
+  if (b->have_done && cudaEventSynchronize(b->done) != cudaSuccess) return HIST_ERR_CUDA;
+  const size_t nf = b->frags.size();
+  std::vector<SliceFragDev> real(b->frags), tune(b->frags);
+  for (size_t f = 0; f < nf; ++f) {
+    const int i = b->frag_member[f];
+    hist* h = b->hs[i];
+    real[f].g_lo = h->g_lo;
+    real[f].g_hi = h->g_hi;
+    real[f].g_unit = h->g_unit;
+    real[f].g_f64 = h->g_f64;
+    real[f].ax.T = h->d_T + h->t_off[0];
+    real[f].ax.lm = h->lm[0];
+    tune[f].ax = real[f].ax;
+    unsigned char* sc = static_cast<unsigned char*>(b->scratch[i]);
+    const size_t nbb = (size_t)(h->nbins[0] + 2) * 8;
+    tune[f].g_lo = reinterpret_cast<unsigned long long*>(sc);
+    tune[f].g_hi = reinterpret_cast<long long*>(sc + nbb);
+    tune[f].g_unit = reinterpret_cast<unsigned long long*>(sc + 2 * nbb);
+    tune[f].g_f64 = reinterpret_cast<double*>(sc + 3 * nbb);
+  }
+  // grow the device copies only when the plan outgrows them (a captured
+  // graph holds these pointers and is dropped when they move)
+  if (b->slices.size() > b->slices_cap || nf > b->frags_cap || b->slice_keys.size() > b->keys_cap) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    cudaFree(b->d_slices);
+    cudaFree(b->d_frags);
+    cudaFree(b->d_frags_tune);
+    cudaFree(b->d_slice_keys);
+    b->d_slices = nullptr;
+    b->d_frags = b->d_frags_tune = nullptr;
+    b->d_slice_keys = nullptr;
+    b->slices_cap = b->frags_cap = b->keys_cap = 0;
+    const size_t ns = std::max(b->slices.size(), (size_t)64), nfc = std::max(nf, (size_t)128);
+    const size_t nk = std::max(b->slice_keys.size(), (size_t)1);
+    int rc;
+    if ((rc = dalloc(&b->d_slices, sizeof(SliceDev) * ns)) != HIST_OK) return rc;
+    if ((rc = dalloc(&b->d_frags, sizeof(SliceFragDev) * nfc)) != HIST_OK) return rc;
+    if ((rc = dalloc(&b->d_frags_tune, sizeof(SliceFragDev) * nfc)) != HIST_OK) return rc;
+    if ((rc = dalloc(&b->d_slice_keys, nk * 8)) != HIST_OK) return rc;
+    b->slices_cap = ns;
+    b->frags_cap = nfc;
+    b->keys_cap = nk;
+  }
+  if (cudaMemcpy(b->d_slices, b->slices.data(), sizeof(SliceDev) * b->slices.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(b->d_frags, real.data(), sizeof(SliceFragDev) * nf, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_frags_tune, tune.data(), sizeof(SliceFragDev) * nf, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (!b->slice_keys.empty() && cudaMemcpy(b->d_slice_keys, b->slice_keys.data(), b->slice_keys.size() * 8,
+                                            cudaMemcpyHostToDevice) != cudaSuccess))
+    return HIST_ERR_CUDA;
+  return HIST_OK;
+}
+
+int batch_part_stats(hist_batch* b) {
+  if (b->grid <= b->part_blocks) return HIST_OK;
+  cudaFree(b->d_part_stats);
+  b->d_part_stats = nullptr;
+  b->part_blocks = 0;
+  int rc = dalloc(&b->d_part_stats, (size_t)b->grid * kStatSlots * 3 * sizeof(double));
+  if (rc != HIST_OK) return rc;
+  b->part_blocks = b->grid;
+  return HIST_OK;
+}
+
+int slice_configure(hist_batch* b, int budget, double cap) {
+  int maxopt = 0;
+  if (cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess)
+    return HIST_ERR_CUDA;
+  const int limit = maxopt - 10 * 1024;  // the kernel's static arrays
+  if (budget > limit - 256) budget = limit - 256;
+  slice_plan(b, budget, cap);
+  if (b->slices.empty()) return HIST_ERR_UNSUPPORTED;
+  b->smem = slice_smem_bytes(b->shared_keys, b->shared_words, b->shared_frags) + b->own_bytes;
+  if (b->smem > (size_t)limit) return HIST_ERR_UNSUPPORTED;
+  int per_sm = 0;
+  if (slice_max_blocks_per_sm(kSliceBlock, b->smem, &per_sm) != 0 || per_sm < 1) return HIST_ERR_CUDA;
+  const int resident = per_sm * b->sm_count;
+  const int ns = (int)b->slices.size();
+  b->slice_replicas = std::max(1, resident / ns);
+  b->grid = ns * b->slice_replicas;
+  b->slice_window = b->pace_tiles < 0 ? std::max(4 * b->slice_replicas, kSliceDefaultWindow)
+                                      : (b->pace_tiles == 0 ? 0 : std::max(4 * b->slice_replicas, b->pace_tiles));
+  b->smem_budget = budget;
+  b->strategy = 1;
+  int rc = batch_part_stats(b);
+  if (rc != HIST_OK) return rc;
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return slice_upload(b);
+}
+
 int batch_configure(hist_batch* b, int budget) {
   // the bins' budget is what remains of the per-block shared memory after
   // the staged tables and the descriptors (and the kernel's static arrays)
@@ -839,14 +1139,9 @@ int batch_configure(hist_batch* b, int budget) {
   int per_sm = 0;
   if (batch_max_blocks_per_sm(256, b->smem, &per_sm) != 0 || per_sm < 1) return HIST_ERR_CUDA;
   b->grid = per_sm * b->sm_count;
-  if (b->grid > b->part_blocks) {
-    cudaFree(b->d_part_stats);
-    b->d_part_stats = nullptr;
-    b->part_blocks = 0;
-    int rc = dalloc(&b->d_part_stats, (size_t)b->grid * kBatchMaxGroups * kMaxStats * sizeof(double));
-    if (rc != HIST_OK) return rc;
-    b->part_blocks = b->grid;
-  }
+  b->strategy = 0;
+  int rc = batch_part_stats(b);
+  if (rc != HIST_OK) return rc;
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
@@ -876,30 +1171,71 @@ BatchParams batch_params(const hist_batch* b, const double* const* cols, const d
   p.n = n;
   p.ncols = b->ncols;
   p.nh = (int)b->hs.size();
-  p.ngroups = kBatchMaxGroups;
   p.fx_elo = kDefaultFxElo;
   p.table_keys = b->table_keys;
   p.sbin_words = b->sbin_words;
-  p.stat_overflows = (b->hs[0]->flags & HIST_STAT_OVERFLOWS) ? 1 : 0;
   p.aligned = 1;
   for (int c = 0; c <= kBatchMaxCols; ++c) p.col_begin[c] = b->col_begin[c];
-  for (int c = 0; c < kBatchMaxCols; ++c) p.ngroups_col[c] = b->ngroups_col[c];
-  for (int g = 0; g < kBatchMaxGroups; ++g) {
-    p.group_lo[g] = b->group_lo[g];
-    p.group_hi[g] = b->group_hi[g];
-  }
+  p.st = b->st;
   return p;
 }
 
-int batch_launch(const hist_batch* b, const BatchParams& p, bool tune, cudaStream_t s) {
-  if (launch_batch_fill(p, 256, b->grid, b->smem, s) != 0) return HIST_ERR_CUDA;
+// Pacing counters of the sliced strategy for n events (before any capture).
+int batch_reserve(hist_batch* b, int64_t n) {
+  if (b->strategy != 1) return HIST_OK;
+  const long long nt = (n + kSliceTile - 1) / kSliceTile;
+  if (nt <= b->done_cap) return HIST_OK;
+  cudaFree(b->d_done);
+  b->d_done = nullptr;
+  b->done_cap = 0;
+  const int rc = dalloc(&b->d_done, (size_t)nt * sizeof(int));
+  if (rc != HIST_OK) return rc;
+  b->done_cap = nt;
+  return HIST_OK;
+}
+
+int batch_launch(const hist_batch* b, const double* const* cols, const double* weights, int64_t n, bool tune,
+                 cudaStream_t s) {
+  if (b->strategy == 1) {
+    SliceParams p;
+    std::memset(&p, 0, sizeof(p));
+    for (int c = 0; c < b->ncols; ++c) p.col[c] = cols[c];
+    p.w = weights;
+    p.slices = b->d_slices;
+    p.frags = tune ? b->d_frags_tune : b->d_frags;
+    p.keys = b->d_slice_keys;
+    p.part_stats = b->d_part_stats;
+    p.n = n;
+    p.ntiles = (n + kSliceTile - 1) / kSliceTile;
+    p.nslices = (int)b->slices.size();
+    p.replicas = b->slice_replicas;
+    p.tile = kSliceTile;
+    p.window = b->slice_window;
+    p.done = (p.window > 0 && p.ntiles <= b->done_cap) ? b->d_done : nullptr;
+    if (p.done == nullptr) p.window = 0;
+    p.ncols = b->ncols;
+    p.shared_frags = b->shared_frags;
+    for (int c = 0; c <= kBatchMaxCols; ++c) p.shared_col_begin[c] = b->shared_col_begin[c];
+    p.shared_keys = b->shared_keys;
+    p.shared_words = b->shared_words;
+    p.max_frags = b->max_frags;
+    p.max_keys = b->max_keys;
+    p.max_words = b->max_words;
+    p.fx_elo = kDefaultFxElo;
+    p.st = b->st;
+    if (p.done != nullptr && cudaMemsetAsync(p.done, 0, (size_t)p.ntiles * sizeof(int), s) != cudaSuccess)
+      return HIST_ERR_CUDA;
+    if (launch_slice_fill(p, kSliceBlock, b->grid, b->smem, s) != 0) return HIST_ERR_CUDA;
+  } else {
+    const BatchParams p = batch_params(b, cols, weights, n, tune);
+    if (launch_batch_fill(p, 256, b->grid, b->smem, s) != 0) return HIST_ERR_CUDA;
+  }
   BatchReduceParams r;
   std::memset(&r, 0, sizeof(r));
   r.part_stats = b->d_part_stats;
   r.nblocks = b->grid;
   r.nh = (int)b->hs.size();
-  r.ngroups = kBatchMaxGroups;
-  r.nstats = 5;
+  r.hist_col = b->d_col;
   r.hist_group = b->d_group;
   r.hist_stats = tune ? b->d_stats_tune : b->d_stats;
   if (launch_batch_reduce(r, s) != 0) return HIST_ERR_CUDA;
@@ -911,7 +1247,8 @@ int batch_launch(const hist_batch* b, const BatchParams& p, bool tune, cudaStrea
 extern "C" int hist_batch_create(hist_t* const* hists, int nh, const int32_t* col_of_hist, uint32_t flags,
                                  hist_batch_t** out) {
   if (out == nullptr || hists == nullptr || col_of_hist == nullptr || nh < 1 || nh > 128) return HIST_ERR_ARG;
-  if (flags & ~HIST_BATCH_GRAPH) return HIST_ERR_ARG;
+  if (flags & ~(HIST_BATCH_GRAPH | HIST_BATCH_WIDE | HIST_BATCH_SLICED)) return HIST_ERR_ARG;
+  if ((flags & HIST_BATCH_WIDE) && (flags & HIST_BATCH_SLICED)) return HIST_ERR_ARG;
   *out = nullptr;
   const uint32_t stat_flag = hists[0] ? (hists[0]->flags & HIST_STAT_OVERFLOWS) : 0;
   for (int i = 0; i < nh; ++i) {
@@ -946,27 +1283,54 @@ extern "C" int hist_batch_create(hist_t* const* hists, int nh, const int32_t* co
       while (k < nh && b->col[k] < c) ++k;
       b->col_begin[c] = k;
     }
-    // statistics groups: distinct (column, range) pairs, at most two per column
+    // statistics groups: distinct (column, range) pairs, in column order;
+    // with HIST_STAT_OVERFLOWS every event counts, so one group per column
     b->group.assign(nh, 0);
-    for (int i = 0; i < nh; ++i) {
+    int ngroups = 0;
+    for (int c = 0; c <= kBatchMaxCols; ++c) b->st.group_begin[c] = 0;
+    for (int i = 0; i < nh && rc == HIST_OK; ++i) {
       const hist* h = b->hs[i];
-      const long long lo = h->T_host[0][1], hi = h->T_host[0][h->nbins[0] + 1];
+      long long lo = h->T_host[0][1], hi = h->T_host[0][h->nbins[0] + 1];
+      if (stat_flag) {
+        lo = std::numeric_limits<long long>::min();
+        hi = std::numeric_limits<long long>::max();
+      }
       const int c = b->col[i];
       int found = -1;
-      for (int j = 0; j < b->ngroups_col[c]; ++j) {
-        const int g = c * kBatchGroupsPerCol + j;
-        if (b->group_lo[g] == lo && b->group_hi[g] == hi) found = g;
-      }
+      for (int g = 0; g < ngroups; ++g)
+        if (b->group_col[g] == c && b->st.group_lo[g] == lo && b->st.group_hi[g] == hi) found = g;
       if (found < 0) {
-        if (b->ngroups_col[c] >= kBatchGroupsPerCol) {
+        if (ngroups >= kBatchMaxGroups) {
           rc = HIST_ERR_UNSUPPORTED;
           break;
         }
-        found = c * kBatchGroupsPerCol + b->ngroups_col[c]++;
-        b->group_lo[found] = lo;
-        b->group_hi[found] = hi;
+        found = ngroups++;
+        b->group_col[found] = c;
+        b->st.group_lo[found] = lo;
+        b->st.group_hi[found] = hi;
       }
       b->group[i] = found;
+    }
+    if (rc != HIST_OK) break;
+    // members are sorted by column, so their groups are too
+    for (int c = 0; c < kBatchMaxCols; ++c) {
+      int g0 = 0;
+      while (g0 < ngroups && b->group_col[g0] < c) ++g0;
+      int g1 = g0;
+      while (g1 < ngroups && b->group_col[g1] == c) ++g1;
+      b->st.group_begin[c] = g0;
+      b->st.group_begin[c + 1] = g1;
+      long long lo = std::numeric_limits<long long>::max(), hi = std::numeric_limits<long long>::min();
+      if (g1 > g0) {
+        lo = std::numeric_limits<long long>::min();
+        hi = std::numeric_limits<long long>::max();
+        for (int g = g0; g < g1; ++g) {
+          lo = std::max(lo, b->st.group_lo[g]);
+          hi = std::min(hi, b->st.group_hi[g]);
+        }
+      }
+      b->st.core_lo[c] = lo;
+      b->st.core_hi[c] = hi;
     }
     if (rc != HIST_OK) break;
     // stage the smallest search tables
@@ -992,7 +1356,9 @@ extern "C" int hist_batch_create(hist_t* const* hists, int nh, const int32_t* co
     if ((rc = dalloc(&b->d_group, sizeof(int) * nh)) != HIST_OK) break;
     if ((rc = dalloc(&b->d_stats, sizeof(double*) * nh)) != HIST_OK) break;
     if ((rc = dalloc(&b->d_stats_tune, sizeof(double*) * nh)) != HIST_OK) break;
-    if (cudaMemcpy(b->d_group, b->group.data(), sizeof(int) * nh, cudaMemcpyHostToDevice) != cudaSuccess) {
+    if ((rc = dalloc(&b->d_col, sizeof(int) * nh)) != HIST_OK) break;
+    if (cudaMemcpy(b->d_group, b->group.data(), sizeof(int) * nh, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_col, b->col.data(), sizeof(int) * nh, cudaMemcpyHostToDevice) != cudaSuccess) {
       rc = HIST_ERR_CUDA;
       break;
     }
@@ -1007,7 +1373,11 @@ extern "C" int hist_batch_create(hist_t* const* hists, int nh, const int32_t* co
       rc = HIST_ERR_CUDA;
       break;
     }
-    rc = batch_configure(b, 96 * 1024);
+    if ((rc = batch_configure(b, 96 * 1024)) != HIST_OK) break;
+    bool all_shared = true;
+    for (int o : b->sbin_off) all_shared &= o >= 0;
+    if ((flags & HIST_BATCH_SLICED) || (!all_shared && !(flags & HIST_BATCH_WIDE)))
+      rc = slice_configure(b, kSliceDefaultBudget, kSliceDefaultCap);
   } while (false);
   if (rc != HIST_OK) {
     batch_release(b);
@@ -1035,11 +1405,12 @@ extern "C" int hist_batch_fill(hist_batch_t* b, const double* const* cols, int n
   for (size_t i = 0; i < b->hs.size(); ++i)
     if (b->hs[i]->config_version != b->built_versions[i]) {
       if ((rc = batch_upload(b)) != HIST_OK) return rc;
+      if (b->strategy == 1 && (rc = slice_upload(b)) != HIST_OK) return rc;
       break;
     }
   for (hist* h : b->hs)
     if ((rc = order_after_previous(h, s)) != HIST_OK) return rc;
-  const BatchParams p = batch_params(b, cols, weights, n, false);
+  if ((rc = batch_reserve(b, n)) != HIST_OK) return rc;
   if (b->flags & HIST_BATCH_GRAPH) {
     std::vector<const double*> cv(cols, cols + b->ncols);
     if (b->exec == nullptr || cv != b->g_cols || weights != b->g_w || n != b->g_n) {
@@ -1049,7 +1420,7 @@ extern "C" int hist_batch_fill(hist_batch_t* b, const double* const* cols, int n
       }
       cudaGraph_t graph = nullptr;
       if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HIST_ERR_CUDA;
-      rc = batch_launch(b, p, false, b->cap_stream);
+      rc = batch_launch(b, cols, weights, n, false, b->cap_stream);
       if (cudaStreamEndCapture(b->cap_stream, &graph) != cudaSuccess || rc != HIST_OK) {
         if (graph) cudaGraphDestroy(graph);
         return HIST_ERR_CUDA;
@@ -1066,7 +1437,7 @@ extern "C" int hist_batch_fill(hist_batch_t* b, const double* const* cols, int n
     }
     if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return HIST_ERR_CUDA;
   } else {
-    if ((rc = batch_launch(b, p, false, s)) != HIST_OK) return rc;
+    if ((rc = batch_launch(b, cols, weights, n, false, s)) != HIST_OK) return rc;
   }
   if (cudaEventRecord(b->done, s) != cudaSuccess) return HIST_ERR_CUDA;
   b->have_done = true;
@@ -1077,7 +1448,7 @@ extern "C" int hist_batch_fill(hist_batch_t* b, const double* const* cols, int n
     if (weights != nullptr && !(h->flags & HIST_TRACK_COUNTS)) h->counts_complete = false;
     if (weights != nullptr) {
       // direct global adds grow g_lo by < 2^32 per event: fold before 2^31 events
-      h->fx_global_since_norm += n;
+      h->fx_global_since_norm += std::max<int64_t>(n, b->grid);
       if (h->fx_global_since_norm > (int64_t)1 << 31) {
         if (launch_normalize_fx(h->g_lo, h->g_hi, h->nbins_total, s) != 0) return HIST_ERR_CUDA;
         h->fx_global_since_norm = 0;
@@ -1090,6 +1461,30 @@ extern "C" int hist_batch_fill(hist_batch_t* b, const double* const* cols, int n
   return HIST_OK;
 }
 
+namespace {
+void batch_report(const hist_batch* b, hist_batch_tuning_t* r) {
+  std::memset(r, 0, sizeof(*r));
+  r->candidates = 1;
+  r->smem_bytes = b->smem_budget;
+  int per_sm = 0;
+  if (b->strategy == 0)
+    batch_max_blocks_per_sm(256, b->smem, &per_sm);
+  else
+    slice_max_blocks_per_sm(kSliceBlock, b->smem, &per_sm);
+  r->blocks_per_sm = per_sm;
+  int nsm = 0;
+  if (b->strategy == 0)
+    for (int o : b->sbin_off) nsm += (o >= 0);
+  else
+    nsm = (int)b->hs.size();
+  r->smem_hists = nsm;
+  r->strategy = b->strategy;
+  r->slices = b->strategy == 1 ? (int)b->slices.size() : 0;
+  r->replicas = b->strategy == 1 ? b->slice_replicas : 0;
+  r->cost_cap_tenths = b->strategy == 1 ? (int)(10.0 * b->slice_cap + 0.5) : 0;
+}
+}  // namespace
+
 extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int ncols, const double* weights,
                                int64_t n, hist_batch_tuning_t* report) {
   if (b == nullptr || n <= 0) return HIST_ERR_ARG;
@@ -1098,21 +1493,39 @@ extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int n
   if (cudaSetDevice(b->device) != cudaSuccess) return HIST_ERR_CUDA;
   for (hist* h : b->hs)
     if (h->have_done && cudaEventSynchronize(h->done) != cudaSuccess) return HIST_ERR_CUDA;
-  const int budgets[] = {16 * 1024, 48 * 1024, 96 * 1024, 144 * 1024, 200 * 1024};
+  // candidates: the wide strategy at five budgets, the sliced one at three
+  // budgets times three work caps (unless the batch was created with a fixed
+  // strategy)
+  struct Cand {
+    int strategy, budget;
+    double cap;
+  };
+  std::vector<Cand> cands;
+  if (!(b->flags & HIST_BATCH_SLICED))
+    for (int kb : {16, 48, 96, 144, 200}) cands.push_back({0, kb * 1024, 0.0});
+  if (!(b->flags & HIST_BATCH_WIDE))
+    for (int kb : {48, 96, 200})
+      for (double cap : {1.5, 3.0, 6.0}) cands.push_back({1, kb * 1024, cap});
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HIST_ERR_CUDA;
   double best = 1e300, worst = 0.0;
-  int best_budget = b->smem_budget, tried = 0;
-  int last_budget = -1;
-  for (int budget : budgets) {
-    if ((rc = batch_configure(b, budget)) != HIST_OK) break;
-    if (b->smem_budget == last_budget) continue;
-    last_budget = b->smem_budget;
-    budget = b->smem_budget;
-    const BatchParams p = batch_params(b, cols, weights, n, true);
-    if ((rc = batch_launch(b, p, true, nullptr)) != HIST_OK) break;  // warm-up
+  Cand best_c = cands.front();
+  int tried = 0, last_wide = -1;
+  for (const Cand& c : cands) {
+    rc = c.strategy == 0 ? batch_configure(b, c.budget) : slice_configure(b, c.budget, c.cap);
+    if (rc == HIST_ERR_UNSUPPORTED) {
+      rc = HIST_OK;
+      continue;
+    }
+    if (rc != HIST_OK) break;
+    if (c.strategy == 0) {  // budgets clamp to the same placement: time it once
+      if (b->smem_budget == last_wide) continue;
+      last_wide = b->smem_budget;
+    }
+    if ((rc = batch_reserve(b, n)) != HIST_OK) break;
+    if ((rc = batch_launch(b, cols, weights, n, true, nullptr)) != HIST_OK) break;  // warm-up
     cudaEventRecord(e0, nullptr);
-    for (int r = 0; r < 3 && rc == HIST_OK; ++r) rc = batch_launch(b, p, true, nullptr);
+    for (int r = 0; r < 3 && rc == HIST_OK; ++r) rc = batch_launch(b, cols, weights, n, true, nullptr);
     cudaEventRecord(e1, nullptr);
     if (rc != HIST_OK || cudaEventSynchronize(e1) != cudaSuccess) {
       rc = HIST_ERR_CUDA;
@@ -1124,7 +1537,8 @@ extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int n
     ++tried;
     if (ms < best) {
       best = ms;
-      best_budget = budget;
+      best_c = c;
+      best_c.budget = b->smem_budget;
     }
     worst = std::max(worst, (double)ms);
   }
@@ -1132,18 +1546,27 @@ extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int n
   cudaEventDestroy(e1);
   if (cudaDeviceSynchronize() != cudaSuccess) return HIST_ERR_CUDA;
   if (rc != HIST_OK) return rc;
-  if ((rc = batch_configure(b, best_budget)) != HIST_OK) return rc;
+  rc = best_c.strategy == 0 ? batch_configure(b, best_c.budget) : slice_configure(b, best_c.budget, best_c.cap);
+  if (rc != HIST_OK) return rc;
   if (report) {
+    batch_report(b, report);
     report->candidates = tried;
-    report->smem_bytes = best_budget;
-    int per_sm = 0;
-    batch_max_blocks_per_sm(256, b->smem, &per_sm);
-    report->blocks_per_sm = per_sm;
-    int nsm = 0;
-    for (int o : b->sbin_off) nsm += (o >= 0);
-    report->smem_hists = nsm;
     report->best_ms = best;
     report->worst_ms = worst;
   }
+  return HIST_OK;
+}
+
+extern "C" int hist_batch_configure(hist_batch_t* b, int32_t strategy, int32_t smem_bytes, int32_t cost_cap_tenths,
+                                    int32_t pace_tiles, hist_batch_tuning_t* info) {
+  if (b == nullptr || (strategy != 0 && strategy != 1) || smem_bytes < 1024 ||
+      (strategy == 1 && cost_cap_tenths < 10) || pace_tiles < -1)
+    return HIST_ERR_ARG;
+  b->pace_tiles = pace_tiles;
+  if (cudaSetDevice(b->device) != cudaSuccess) return HIST_ERR_CUDA;
+  if (b->have_done && cudaEventSynchronize(b->done) != cudaSuccess) return HIST_ERR_CUDA;
+  const int rc = strategy == 0 ? batch_configure(b, smem_bytes) : slice_configure(b, smem_bytes, 0.1 * cost_cap_tenths);
+  if (rc != HIST_OK) return rc;
+  if (info) batch_report(b, info);
   return HIST_OK;
 }

@@ -97,9 +97,23 @@ struct ReduceParams {
 };
 
 // ---- batched fill: many 1D histograms from one event stream -------------
-constexpr int kBatchMaxCols = 4;       // columns per batch
-constexpr int kBatchGroupsPerCol = 2;  // statistics ranges per column
-constexpr int kBatchMaxGroups = kBatchMaxCols * kBatchGroupsPerCol;
+constexpr int kBatchMaxCols = 4;     // columns per batch
+constexpr int kBatchMaxGroups = 16;  // statistics groups: distinct (column, range) pairs
+constexpr int kStatSlots = kBatchMaxCols + kBatchMaxGroups;  // partial sums: a core per column, a tail per group
+
+// Statistics of a batch.  The statistics of a 1D histogram depend only on
+// its column and its in-range test, so members with the same column and
+// range share a group.  The groups of a column overlap on a common core
+// [core_lo, core_hi) (keys; empty when lo >= hi): an event in the core adds
+// to the column's core sums once, for all its groups; only the rare event
+// outside it walks the column's groups and adds to the tail sums of those
+// whose range holds it.  A group's sums are its column's core plus its tail.
+struct BatchStatsSpec {
+  long long core_lo[kBatchMaxCols], core_hi[kBatchMaxCols];
+  long long group_lo[kBatchMaxGroups], group_hi[kBatchMaxGroups];
+  int32_t group_begin[kBatchMaxCols + 1];  // groups sorted by column: [group_begin[c], group_begin[c+1])
+  int32_t pad;
+};
 
 struct BatchHistDev {
   AxisDev ax;                   // T: global thresholds; smem_off: staged keys (-1: global)
@@ -118,25 +132,78 @@ struct BatchParams {
   const double* w;              // nullptr: unit weights
   const BatchHistDev* hists;    // device [nh]
   const long long* T_concat;    // staged keys of all staged axes, back to back
-  double* part_stats;           // [grid][kBatchMaxGroups][kMaxStats]
+  double* part_stats;           // [grid][kStatSlots][3]: sum w^2, sum wx, sum wx^2
   long long n;
-  int32_t ncols, nh, ngroups, fx_elo;
+  int32_t ncols, nh, fx_elo;
   int32_t table_keys;           // staged keys (8-byte keys + 4-byte high words each)
   int32_t sbin_words;           // shared-memory words of all block-private bins
-  int32_t stat_overflows;
   int32_t aligned;
   int32_t col_begin[kBatchMaxCols + 1];  // histograms sorted by column: [col_begin[c], col_begin[c+1])
-  int32_t ngroups_col[kBatchMaxCols];    // statistics groups of column c: ids c * kBatchGroupsPerCol + j
-  long long group_lo[kBatchMaxGroups];   // statistics range of a group: key in [lo, hi)
-  long long group_hi[kBatchMaxGroups];
+  BatchStatsSpec st;
 };
 
 struct BatchReduceParams {
   const double* part_stats;
-  int32_t nblocks, nh, ngroups, nstats;
+  int32_t nblocks, nh;
+  const int* hist_col;          // device [nh]
   const int* hist_group;        // device [nh]
   double* const* hist_stats;    // device [nh] pointers to each histogram's statistics
 };
+
+// Sliced strategy: the large histograms' bins are cut into slices that
+// each fit one block's shared memory; a slice is a run of fragments (a
+// histogram's bin range [a, b)), all on one column.  Block (slice s,
+// replica r) fills slice s from the event tiles t = r, r + R, r + 2R, ...
+// so the R replicas of every slice sweep the stream together and each tile
+// is read from HBM once and from L2 by every slice.  The small histograms
+// are held whole by every block (the "shared" fragments) and filled, with
+// the statistics, by one block per tile (the slice (t / R) mod S), which
+// spreads that work and its hot bins over every block.
+struct SliceFragDev {
+  AxisDev ax;                   // T: global thresholds (fixed axes' rare exact step)
+  long long Ta, Tb;             // the fragment holds the keys [Ta, Tb) = [T[a], T[b])
+  int32_t a, b;                 // bins [a, b) of the histogram (flows included)
+  int32_t key_off;              // shared offset of T[a+1 .. b-1] (non-affine axes); -1: affine locate
+  int32_t top;                  // largest power of two <= b - a - 1 (0 if none)
+  int32_t bin_off;              // shared word offset of bin a (two words per bin)
+  int32_t whole;                // 1: a = 0 and b = nbins + 2 (no range test)
+  unsigned long long* g_lo;     // the histogram's accumulators (bin 0 based) or tuning scratch
+  long long* g_hi;
+  unsigned long long* g_unit;
+  double* g_f64;
+};
+
+struct SliceDev {
+  int32_t col;                  // column of every fragment
+  int32_t frag_begin, frag_end; // its fragments [frag_begin, frag_end) of the plan
+  int32_t key_base, nkeys;      // its keys in the concatenated key array
+  int32_t nwords;               // shared words of its bins
+};
+
+struct SliceParams {
+  const double* col[kBatchMaxCols];
+  const double* w;              // nullptr: unit weights
+  const SliceDev* slices;       // device [nslices]
+  const SliceFragDev* frags;    // device: shared fragments first, then the slices'
+  const long long* keys;        // concatenated keys: the shared fragments' first
+  double* part_stats;           // [grid][kStatSlots][3]
+  int* done;                    // [ntiles] slices finished per tile (pacing only), or nullptr
+  long long n;
+  long long ntiles;
+  int32_t nslices, replicas, ncols;
+  int32_t tile;                 // events per tile
+  int32_t window;               // a block starts tile t once tile t - window is done everywhere (0: off)
+  int32_t shared_frags;         // fragments [0, shared_frags) are the small histograms, by column:
+  int32_t shared_col_begin[kBatchMaxCols + 1];  // [shared_col_begin[c], shared_col_begin[c+1])
+  int32_t shared_keys, shared_words;            // their keys (at 0) and bin words (at 0)
+  int32_t max_frags, max_keys, max_words;       // largest slice (shared-memory sizing)
+  int32_t fx_elo;
+  BatchStatsSpec st;
+};
+
+int launch_slice_fill(const SliceParams& p, int block, int grid, size_t smem, void* stream);
+int slice_max_blocks_per_sm(int block, size_t smem, int* per_sm);
+size_t slice_smem_bytes(int keys, int words, int frags);
 
 int launch_batch_fill(const BatchParams& p, int block, int grid, size_t smem, void* stream);
 int batch_max_blocks_per_sm(int block, size_t smem, int* per_sm);

@@ -1,12 +1,15 @@
 """The batched fill: every histogram of a batch filled from one event stream
 in one launch must match the CPU oracle filled one histogram at a time
-(counts exact, sums within 1e-12 of sum |term|)."""
+(counts exact, sums within 1e-12 of sum |term|), under both privatisation
+strategies (wide: per-block shared bins for the small histograms, global
+atomics for the rest; sliced: every bin in shared memory, large histograms
+cut into fragments across blocks)."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2401_13310_gb300 import workloads as W
-from tests.helpers import assert_sums_close, to_device
+from tests.helpers import assert_sums_close, edge_probe_values, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -35,9 +38,13 @@ def _check(bw, hists, weights, what):
         assert_sums_close(stats[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, f"{what} hist {i} stats")
 
 
+STRATEGIES = {"wide": 1 << 1, "sliced": 1 << 2}
+
+
+@pytest.mark.parametrize("strategy", ["wide", "sliced"])
 @pytest.mark.parametrize("weighted", [True, False])
 @pytest.mark.parametrize("learned", [False, True])
-def test_batch_matches_oracle(B, weighted, learned):
+def test_batch_matches_oracle(B, strategy, weighted, learned):
     bw = W.cfg4(n=200_003)
     hists = [B.Hist([ax]) for ax in bw.axes]
     batch = None
@@ -46,11 +53,11 @@ def test_batch_matches_oracle(B, weighted, learned):
             for h, ax in zip(hists, bw.axes):
                 if ax["kind"] == "variable":
                     h.train_locator(0)
-        batch = B.Batch(hists, bw.col_of_hist)
+        batch = B.Batch(hists, bw.col_of_hist, STRATEGIES[strategy])
         cols = [to_device(np.ascontiguousarray(bw.columns[c])) for c in range(3)]
         w = to_device(bw.weights) if weighted else None
         batch.fill(cols, w)
-        _check(bw, hists, bw.weights if weighted else None, f"w={weighted} learned={learned}")
+        _check(bw, hists, bw.weights if weighted else None, f"{strategy} w={weighted} learned={learned}")
     finally:
         if batch is not None:
             batch.close()
@@ -102,3 +109,58 @@ def test_batch_rejects_nd_and_bad_columns(B):
     finally:
         h1.close()
         h2.close()
+
+
+@pytest.mark.parametrize("strategy", ["wide", "sliced"])
+def test_batch_edges_specials_and_odd_weights(B, strategy):
+    """Every threshold of every axis and its neighbouring doubles (so every
+    fragment boundary of a cut histogram), signed zeros, infinities, NaN,
+    subnormals; weights of both signs, zero, and outside the fixed-point
+    window (the binary64 slow path)."""
+    rng = np.random.default_rng(33)
+    axes, col_of_hist = W.batch_axes(64)
+    per_col = [[], [], []]
+    for ax, c in zip(axes, col_of_hist):
+        per_col[c].append(edge_probe_values(ax, B.hist_axis_thresholds(ax), rng, nrand=500))
+    streams = [np.concatenate(v) for v in per_col]
+    n = max(len(v) for v in streams)
+    cols = np.empty((3, n))
+    for c in range(3):
+        v = np.resize(streams[c], n)
+        cols[c] = v[rng.permutation(n)]
+    w = rng.uniform(-2.0, 2.0, n)
+    w[::97] = 0.0
+    w[1::89] = 1e-5
+    w[2::83] = -3e3
+    bw = W.BatchWorkload("edges", axes, col_of_hist, cols, w, {})
+    hists = [B.Hist([ax]) for ax in axes]
+    batch = None
+    try:
+        batch = B.Batch(hists, col_of_hist, STRATEGIES[strategy])
+        batch.fill([to_device(np.ascontiguousarray(cols[c])) for c in range(3)], to_device(w))
+        _check(bw, hists, w, f"{strategy} edges")
+    finally:
+        if batch is not None:
+            batch.close()
+        for h in hists:
+            h.close()
+
+
+def test_batch_unit_weights_many_edges_tuned(B):
+    """Unit weights into eight histograms of 100 .. 10^4 mixture-quantile
+    edges, after tuning (whichever strategy wins): counts exact."""
+    bw = W.cfg5(n=300_007, nhist=8, scale=0.01)
+    hists = [B.Hist([ax]) for ax in bw.axes]
+    batch = None
+    try:
+        batch = B.Batch(hists, bw.col_of_hist, B.HIST_BATCH_GRAPH)
+        col = to_device(np.ascontiguousarray(bw.columns[0]))
+        rep = batch.tune([col], None)
+        assert rep["candidates"] >= 6
+        batch.fill([col], None)
+        _check(bw, hists, None, f"tuned strategy {rep['strategy']}")
+    finally:
+        if batch is not None:
+            batch.close()
+        for h in hists:
+            h.close()
