@@ -12,9 +12,16 @@ CUDA events on the launching stream).  ``e2e`` is the same metric through the
 same public calls with the inputs copied each step from pinned host memory
 and the result read back.  ``roofline`` is the dominant fill kernel's
 algorithmic HBM bytes (16 per event: x and w read once) per launch over its
-measured launch time, against the measured HBM copy bandwidth.
-``cpu_baseline`` times the CPU oracle (chunk-parallel, all host cores) on the
-same workload drawn on the host.
+average launch time (the library's own event pairs around the fill kernel,
+without the partial-sum reduction), against the measured HBM copy bandwidth;
+``traffic`` is the DRAM bytes per launch that ncu counted for the same kernel
+source (scaled from a 2e7-event capture by events), or null once the kernel
+sources differ from the ones measured.  ``forms`` times the other forms on
+the same GPU: the batched workload (64 histograms on one event stream, plain
+per-histogram fills against the fused batch) and the learned-locator workload
+(8 variable axes with 1e4..1e6 edges; binary search against the learned
+locator, plain and batched).  ``cpu_baseline`` times the CPU oracle
+(chunk-parallel, all host cores) on the same workload drawn on the host.
 
 --impl reference times the CPU oracle itself as the reference arm (bounded
 samples of the same workload per step).
@@ -40,6 +47,23 @@ BYTES_PER_EVENT = 16  # binary64 coordinate + binary64 weight, each read once
 METRIC = "Gevents/s filled"
 WORKLOAD = ("1d_weighted_1e8x2: (a) 1000 fixed bins [-5,5) x~N(0,1); "
             "(b) 500 log bins [1,1000] x~Exp(30); w~U[0.5,1.5)")
+
+
+# DRAM bytes per event that ncu counted for the fill kernel of each fill
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 2e7
+# events), valid for the kernel sources with this digest only.
+TRAFFIC = {"digest": "f0b43c3bca99017a", "a_fixed1000": (320045824 + 6800128) / 2e7,
+           "b_var500": (320037632 + 4615680) / 2e7}
+KERNEL_SOURCES = ["fill_kernels.cu", "device_common.cuh", "learned_eval.cuh"]
+
+
+def kernel_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2401_13310_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def peaks():
@@ -128,18 +152,110 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-def cpu_baseline(n_per_fill: int, threads: int):
-    """The CPU oracle on host-drawn inputs of the same workload."""
+def _timed(fn, reps: int) -> float:
+    """Average milliseconds of fn() over reps calls (one warm-up first),
+    CUDA events on the current stream."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_forms(B, W, hbm: float, args) -> dict:
+    """The batched and learned forms beside the plain one, same GPU."""
+    import torch
+    out = {}
+    # batched: 64 histograms (10 .. 1e5 bins, fixed and variable) on the
+    # columns pT, phi, eta with binary64 weights
+    n4 = args.batch_events
+    bw = W.cfg4(n=n4, device="cuda")
+    cols = [bw.columns[c].contiguous() for c in range(3)]
+    w = bw.weights
+    del bw.columns
+    hists = [B.Hist([ax]) for ax in bw.axes]
+
+    def plain4():
+        for h, c in zip(hists, bw.col_of_hist):
+            h.fill(cols[c], w)
+    t_plain = _timed(plain4, 3)
+    batch = B.Batch(hists, bw.col_of_hist, B.HIST_BATCH_GRAPH)
+    tune = batch.tune([c[:4_000_000] for c in cols], w[:4_000_000])
+    t_fused = _timed(lambda: batch.fill(cols, w), 3)
+    nh = len(hists)
+    out["batched64"] = {
+        "events": n4, "histograms": nh,
+        "plain_ms": t_plain, "fused_ms": t_fused, "fused_speedup": t_plain / t_fused,
+        "plain_gfills_per_s": n4 * nh / (t_plain * 1e-3) / 1e9,
+        "fused_gfills_per_s": n4 * nh / (t_fused * 1e-3) / 1e9,
+        "plain_hbm_frac": 16 * n4 * nh / (t_plain * 1e-3) / 1e9 / hbm,
+        "fused_hbm_frac": 32 * n4 / (t_fused * 1e-3) / 1e9 / hbm,
+        "tuning": tune,
+    }
+    batch.close()
+    for h in hists:
+        h.close()
+    del cols, w
+    torch.cuda.empty_cache()
+    # learned locator: 8 variable axes, 1e4 .. 1e6 mixture-quantile edges,
+    # unit weights, one column of mixture draws
+    n5 = args.learned_events
+    lw = W.cfg5(n=n5, device="cuda")
+    col = lw.columns[0].contiguous()
+    del lw.columns
+    hists = [B.Hist([ax]) for ax in lw.axes]
+
+    def plain5():
+        for h in hists:
+            h.fill(col, None)
+    res = {"events": n5, "histograms": len(hists)}
+    res["plain_bsearch_ms"] = _timed(plain5, 2)
+    batch = B.Batch(hists, lw.col_of_hist, B.HIST_BATCH_GRAPH | B.HIST_BATCH_WIDE)
+    res["fused_bsearch_ms"] = _timed(lambda: batch.fill([col], None), 2)
+    batch.close()
+    t0 = time.perf_counter()
+    reports = [h.train_locator(0) for h in hists]
+    res["train_s"] = time.perf_counter() - t0
+    res["windows"] = [r["window"] for r in reports]
+    res["plain_learned_ms"] = _timed(plain5, 2)
+    batch = B.Batch(hists, lw.col_of_hist, B.HIST_BATCH_GRAPH | B.HIST_BATCH_WIDE)
+    res["fused_learned_ms"] = _timed(lambda: batch.fill([col], None), 2)
+    batch.close()
+    for h in hists:
+        h.close()
+    del col
+    torch.cuda.empty_cache()
+    res["learned_vs_bsearch_plain"] = res["plain_bsearch_ms"] / res["plain_learned_ms"]
+    res["learned_vs_bsearch_fused"] = res["fused_bsearch_ms"] / res["fused_learned_ms"]
+    best = min(res["fused_learned_ms"], res["plain_learned_ms"])
+    res["best_learned_gfills_per_s"] = n5 * len(hists) / (best * 1e-3) / 1e9
+    res["best_learned_hbm_frac"] = 8 * n5 / (res["fused_learned_ms"] * 1e-3) / 1e9 / hbm
+    out["learned8"] = res
+    return out
+
+
+def cpu_baseline(n_per_fill: int, threads: int, min_seconds: float = 10.0):
+    """The CPU oracle on host-drawn inputs of the same workload, repeated
+    over the sample until at least min_seconds of oracle time."""
     import oracle
     from paper_2401_13310_gb300 import workloads as W
     oracle.build()
     wa = W.cfg2a(n=n_per_fill)
     wb = W.cfg2b(n=n_per_fill)
-    t0 = time.perf_counter()
-    oracle.fill(wa.axes, wa.values, wa.weights, threads=threads)
-    oracle.fill(wb.axes, wb.values, wb.weights, threads=threads)
-    dt = time.perf_counter() - t0
-    return 2 * n_per_fill / dt / 1e9, dt
+    reps, dt = 0, 0.0
+    while dt < min_seconds:
+        t0 = time.perf_counter()
+        oracle.fill(wa.axes, wa.values, wa.weights, threads=threads)
+        oracle.fill(wb.axes, wb.values, wb.weights, threads=threads)
+        dt += time.perf_counter() - t0
+        reps += 1
+    return 2 * n_per_fill * reps / dt / 1e9, dt, reps
 
 
 def run_reference(args):
@@ -204,6 +320,8 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    B.hist_set_kernel_timing(ha.h, True)
+    B.hist_set_kernel_timing(hb.h, True)
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     sampler = ClockSampler(local)
@@ -226,19 +344,29 @@ def run_ours(args):
     ms_total = max_over_ranks(t_start.elapsed_time(t_end), world)
     ms_a = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
     ms_b = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    ka_ms, ka_n = B.hist_kernel_time(ha.h)
+    kb_ms, kb_n = B.hist_kernel_time(hb.h)
+    B.hist_set_kernel_timing(ha.h, False)
+    B.hist_set_kernel_timing(hb.h, False)
     events_total = 2 * n * args.steps * world
     value = events_total / (ms_total * 1e-3) / 1e9
 
     hbm, peak_src = peaks()
-    avg_a, avg_b = sum(ms_a) / len(ms_a), sum(ms_b) / len(ms_b)
-    dom_ms, dom = (avg_a, "a_fixed1000") if avg_a >= avg_b else (avg_b, "b_var500")
+    kern_a, kern_b = ka_ms / max(ka_n, 1), kb_ms / max(kb_n, 1)
+    dom_ms, dom = (kern_a, "a_fixed1000") if kern_a >= kern_b else (kern_b, "b_var500")
     achieved = BYTES_PER_EVENT * n / (dom_ms * 1e-3) / 1e9
+    traffic = None
+    if TRAFFIC["digest"] == kernel_digest() and TRAFFIC.get(dom) is not None:
+        traffic = TRAFFIC[dom] * n
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "kernel": f"k_fill (1D, fixed-point) on {dom}",
-                "peak_source": peak_src,
-                "per_fill_ms": {"a_fixed1000": avg_a, "b_var500": avg_b},
-                "frac_a": BYTES_PER_EVENT * n / (avg_a * 1e-3) / 1e9 / hbm,
-                "frac_b": BYTES_PER_EVENT * n / (avg_b * 1e-3) / 1e9 / hbm}
+                "frac": achieved / hbm, "traffic": traffic,
+                "kernel": f"k_fill (1D, fixed-point bins in shared memory) on {dom}",
+                "peak_source": f"{peak_src} (HBM copy, burst)",
+                "algorithmic_bytes_per_launch": BYTES_PER_EVENT * n,
+                "kernel_ms": {"a_fixed1000": kern_a, "b_var500": kern_b},
+                "fill_call_ms": {"a_fixed1000": sum(ms_a) / len(ms_a), "b_var500": sum(ms_b) / len(ms_b)},
+                "frac_a": BYTES_PER_EVENT * n / (kern_a * 1e-3) / 1e9 / hbm,
+                "frac_b": BYTES_PER_EVENT * n / (kern_b * 1e-3) / 1e9 / hbm}
 
     # ---- end to end: host inputs copied every step, result read back
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
@@ -264,13 +392,22 @@ def run_ours(args):
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
     del host, dev
 
+    forms = None
+    if not args.no_forms:
+        ha.close()
+        hb.close()
+        del wa, wb
+        torch.cuda.empty_cache()
+        forms = measure_forms(B, W, hbm, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = len(os.sched_getaffinity(0))
-        v, dt = cpu_baseline(args.cpu_events, threads)
+        v, dt, reps = cpu_baseline(args.cpu_events, threads)
         cpu = {"value": v, "unit": "Gevents/s", "cores": threads, "kind": "oracle",
                "sample": f"{args.cpu_events} events of each of (a) and (b), drawn on the host "
-                         f"(numpy PCG64), chunk-parallel oracle, {dt:.1f} s"}
+                         f"(numpy PCG64), filled {reps} times by the chunk-parallel oracle "
+                         f"({threads} threads), {dt:.1f} s"}
 
     if rank == 0:
         line = {
@@ -282,11 +419,12 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (1.6 GB per fill), no flush",
                        "precision": args.prec, "parallelism": f"dp{world} (independent events per rank)"},
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-            "gpu_launches": 4 * args.steps, "clocks": clocks,
+            "gpu_launches": 4 * args.steps, "clocks": clocks, "forms": forms,
         }
         print(json.dumps(line), flush=True)
-    ha.close()
-    hb.close()
+    if forms is None:
+        ha.close()
+        hb.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -302,9 +440,12 @@ def main():
     ap.add_argument("--events", type=int, default=N_EVENTS)
     ap.add_argument("--prec", choices=["fp64", "f64atomic"], default="fp64")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--cpu-events", type=int, default=N_EVENTS)
+    ap.add_argument("--cpu-events", type=int, default=50_000_000)
     ap.add_argument("--ref-events", type=int, default=20_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--batch-events", type=int, default=50_000_000)
+    ap.add_argument("--learned-events", type=int, default=1_000_000_000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

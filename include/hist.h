@@ -135,6 +135,15 @@ int hist_counts(hist_t *h, uint64_t *counts);
  * `stream`.  Does not change the histogram. */
 int hist_locate(hist_t *h, const double *values, int64_t n, int64_t *out, hist_stream_t stream);
 
+/* Kernel timing (measurement aid; the paper has no counterpart): while on,
+ * every hist_fill_bulk records a pair of CUDA events on its stream around
+ * the fill kernel alone (not the partial-sum reduction that follows).
+ * hist_kernel_time waits for the last recorded pair, returns the summed
+ * milliseconds and the number of timed launches since the previous call,
+ * and starts a new count.  Errors: HIST_ERR_ARG, HIST_ERR_CUDA. */
+int hist_set_kernel_timing(hist_t *h, int on);
+int hist_kernel_time(hist_t *h, double *ms, int64_t *launches);
+
 /* ---- batched fill: many histograms, one event stream ---------------------
  * The paper's conclusion names computing several histograms from the same
  * data, and its kernels being small and launch-bound, as the next step.  A

@@ -114,6 +114,8 @@ def load(path: str | None = None):
             "hist_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_uint32, _P]),
             "hist_batch_fill": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
             "hist_batch_tune": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
+            "hist_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+            "hist_kernel_time": (ctypes.c_int, [_P, _P, _P]),
             "hist_batch_configure": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                     ctypes.c_int32, _P]),
             "hist_batch_free": (None, [_P]),
@@ -314,6 +316,18 @@ def hist_batch_configure(b: int, strategy: int, smem_bytes: int, cost_cap_tenths
     _check(load().hist_batch_configure(b, int(strategy), int(smem_bytes), int(cost_cap_tenths), int(pace_tiles),
                                        ctypes.byref(r)), "hist_batch_configure")
     return {f: getattr(r, f) for f, _ in hist_batch_tuning_t._fields_}
+
+
+def hist_set_kernel_timing(h: int, on: bool) -> None:
+    _check(load().hist_set_kernel_timing(h, int(bool(on))), "hist_set_kernel_timing")
+
+
+def hist_kernel_time(h: int):
+    """(summed fill-kernel milliseconds, timed launches) since the last call."""
+    ms = ctypes.c_double()
+    k = ctypes.c_int64()
+    _check(load().hist_kernel_time(h, ctypes.byref(ms), ctypes.byref(k)), "hist_kernel_time")
+    return ms.value, k.value
 
 
 def hist_batch_free(b: int) -> None:

@@ -79,6 +79,10 @@ struct hist {
   // ordering of fills issued on different streams
   cudaEvent_t done = nullptr;
   bool have_done = false;
+  // optional timing of the fill kernel alone (pairs of events around it)
+  bool timing = false;
+  std::vector<cudaEvent_t> t_ev;
+  size_t t_used = 0;  // pairs recorded since the last hist_kernel_time
 };
 
 namespace {
@@ -96,6 +100,7 @@ int dalloc(T** p, size_t bytes) {
 
 void free_state(hist* h) {
   if (h->done) cudaEventDestroy(h->done);
+  for (cudaEvent_t e : h->t_ev) cudaEventDestroy(e);
   cudaFree(h->d_T);
   cudaFree(h->g_lo);
   cudaFree(h->g_hi);
@@ -205,7 +210,22 @@ int fill_impl(hist* h, const double* values, const double* weights, int64_t n, c
   if (rc != HIST_OK) return rc;
   p.part_bins = h->part_bins;
   p.part_stats = h->part_stats;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (h->timing) {
+    while (h->t_ev.size() < 2 * (h->t_used + 1)) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return HIST_ERR_CUDA;
+      h->t_ev.push_back(e);
+    }
+    t0 = h->t_ev[2 * h->t_used];
+    t1 = h->t_ev[2 * h->t_used + 1];
+    if (cudaEventRecord(t0, stream) != cudaSuccess) return HIST_ERR_CUDA;
+  }
   if (launch_fill(p, acc, shape, stream) != 0) return HIST_ERR_CUDA;
+  if (h->timing) {
+    if (cudaEventRecord(t1, stream) != cudaSuccess) return HIST_ERR_CUDA;
+    ++h->t_used;
+  }
   ReduceParams r;
   std::memset(&r, 0, sizeof(r));
   r.part_bins = p.smem_bins ? h->part_bins : nullptr;
@@ -241,6 +261,29 @@ int fill_impl(hist* h, const double* values, const double* weights, int64_t n, c
 extern "C" {
 
 const char* hist_version(void) { return "gb300-hist 0.1 (sm_103a)"; }
+
+int hist_set_kernel_timing(hist_t* h, int on) {
+  if (h == nullptr) return HIST_ERR_ARG;
+  h->timing = on != 0;
+  h->t_used = 0;
+  return HIST_OK;
+}
+
+int hist_kernel_time(hist_t* h, double* ms, int64_t* launches) {
+  if (h == nullptr || ms == nullptr || launches == nullptr) return HIST_ERR_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return HIST_ERR_CUDA;
+  double total = 0.0;
+  for (size_t i = 0; i < h->t_used; ++i) {
+    if (cudaEventSynchronize(h->t_ev[2 * i + 1]) != cudaSuccess) return HIST_ERR_CUDA;
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, h->t_ev[2 * i], h->t_ev[2 * i + 1]) != cudaSuccess) return HIST_ERR_CUDA;
+    total += t;
+  }
+  *ms = total;
+  *launches = (int64_t)h->t_used;
+  h->t_used = 0;
+  return HIST_OK;
+}
 
 const char* hist_strerror(int code) {
   switch (code) {
