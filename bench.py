@@ -52,8 +52,8 @@ WORKLOAD = ("1d_weighted_1e8x2: (a) 1000 fixed bins [-5,5) x~N(0,1); "
 # DRAM bytes per event that ncu counted for the fill kernel of each fill
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 2e7
 # events), valid for the kernel sources with this digest only.
-TRAFFIC = {"digest": "f0b43c3bca99017a", "a_fixed1000": (320045824 + 6800128) / 2e7,
-           "b_var500": (320037632 + 4615680) / 2e7}
+TRAFFIC = {"digest": "3c569a729cbcc1ac", "a_fixed1000": (320046336 + 6584832) / 2e7,
+           "b_var500": (320056320 + 4606208) / 2e7}
 KERNEL_SOURCES = ["fill_kernels.cu", "device_common.cuh", "learned_eval.cuh"]
 
 
@@ -209,12 +209,22 @@ def measure_forms(B, W, hbm: float, args) -> dict:
     lw = W.cfg5(n=n5, device="cuda")
     col = lw.columns[0].contiguous()
     del lw.columns
+    res = {"events": n5, "histograms": len(lw.axes)}
+    # the default locator (bucket map where the axis has one)
     hists = [B.Hist([ax]) for ax in lw.axes]
+    res["default_locators"] = [B.hist_locator_mode(h.h, 0) for h in hists]
 
     def plain5():
         for h in hists:
             h.fill(col, None)
-    res = {"events": n5, "histograms": len(hists)}
+    res["plain_default_ms"] = _timed(plain5, 2)
+    batch = B.Batch(hists, lw.col_of_hist, B.HIST_BATCH_GRAPH | B.HIST_BATCH_WIDE)
+    res["fused_default_ms"] = _timed(lambda: batch.fill([col], None), 2)
+    batch.close()
+    for h in hists:
+        h.close()
+    # binary search over the edges, then the learned locator on the same axes
+    hists = [B.Hist([ax], B.HIST_LOCATOR_BSEARCH) for ax in lw.axes]
     res["plain_bsearch_ms"] = _timed(plain5, 2)
     batch = B.Batch(hists, lw.col_of_hist, B.HIST_BATCH_GRAPH | B.HIST_BATCH_WIDE)
     res["fused_bsearch_ms"] = _timed(lambda: batch.fill([col], None), 2)
@@ -233,9 +243,13 @@ def measure_forms(B, W, hbm: float, args) -> dict:
     torch.cuda.empty_cache()
     res["learned_vs_bsearch_plain"] = res["plain_bsearch_ms"] / res["plain_learned_ms"]
     res["learned_vs_bsearch_fused"] = res["fused_bsearch_ms"] / res["fused_learned_ms"]
-    best = min(res["fused_learned_ms"], res["plain_learned_ms"])
-    res["best_learned_gfills_per_s"] = n5 * len(hists) / (best * 1e-3) / 1e9
-    res["best_learned_hbm_frac"] = 8 * n5 / (res["fused_learned_ms"] * 1e-3) / 1e9 / hbm
+    res["default_vs_bsearch_plain"] = res["plain_bsearch_ms"] / res["plain_default_ms"]
+    nh5 = len(lw.axes)
+    for k in ("plain_bsearch", "plain_learned", "plain_default"):
+        res[k + "_gfills_per_s"] = n5 * nh5 / (res[k + "_ms"] * 1e-3) / 1e9
+    for k in ("fused_bsearch", "fused_learned", "fused_default"):
+        res[k + "_gfills_per_s"] = n5 * nh5 / (res[k + "_ms"] * 1e-3) / 1e9
+        res[k + "_hbm_frac"] = 8 * n5 / (res[k + "_ms"] * 1e-3) / 1e9 / hbm
     out["learned8"] = res
     return out
 
@@ -361,6 +375,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic,
                 "kernel": f"k_fill (1D, fixed-point bins in shared memory) on {dom}",
+                "locators": {"a_fixed1000": B.hist_locator_mode(ha.h, 0), "b_var500": B.hist_locator_mode(hb.h, 0)},
                 "peak_source": f"{peak_src} (HBM copy, burst)",
                 "algorithmic_bytes_per_launch": BYTES_PER_EVENT * n,
                 "kernel_ms": {"a_fixed1000": kern_a, "b_var500": kern_b},

@@ -87,10 +87,18 @@ typedef struct {
 #define HIST_PREC_FP32C (1u << 4)
 #define HIST_PREC_F64ATOMIC (2u << 4)
 #define HIST_PREC_MASK (3u << 4)
-/* Variable-axis locator (bits 8-9): binary search (default) or a trained
- * index model with an exact window correction (needs hist_train_locator). */
-#define HIST_LOCATOR_BSEARCH (0u << 8)
+/* Variable-axis locator (bits 8-9), all exact (the same bins):
+ *   HIST_LOCATOR_AUTO     (default) a bucket map when the axis has one: the
+ *                         coordinate's bucket under a monotone linear or
+ *                         logarithmic map, then that bucket's few thresholds;
+ *                         else the binary search over the edges (Sec. 3.1);
+ *   HIST_LOCATOR_LEARNED  as AUTO until hist_train_locator installs the
+ *                         trained index model (windowed search, full
+ *                         binary search on a miss);
+ *   HIST_LOCATOR_BSEARCH  always the binary search over the edges. */
+#define HIST_LOCATOR_AUTO (0u << 8)
 #define HIST_LOCATOR_LEARNED (1u << 8)
+#define HIST_LOCATOR_BSEARCH (2u << 8)
 #define HIST_LOCATOR_MASK (3u << 8)
 
 typedef struct hist hist_t; /* opaque; owns its device bins, statistics and axis tables */
@@ -134,6 +142,11 @@ int hist_counts(hist_t *h, uint64_t *counts);
  * values as in hist_fill_bulk; out: device int64 [n].  Asynchronous on
  * `stream`.  Does not change the histogram. */
 int hist_locate(hist_t *h, const double *values, int64_t n, int64_t *out, hist_stream_t stream);
+
+/* How the fills find the bin on axis `axis`: 0 the fixed-width estimate with
+ * its exact correction, 1 binary search over the thresholds, 2 the trained
+ * index model, 3 the bucket map.  Returns the mode, or HIST_ERR_ARG. */
+int hist_locator_mode(const hist_t *h, int axis);
 
 /* Kernel timing (measurement aid; the paper has no counterpart): while on,
  * every hist_fill_bulk records a pair of CUDA events on its stream around

@@ -39,8 +39,9 @@ HIST_STAT_OVERFLOWS = 1 << 1
 HIST_PREC_FP64 = 0 << 4
 HIST_PREC_FP32C = 1 << 4
 HIST_PREC_F64ATOMIC = 2 << 4
-HIST_LOCATOR_BSEARCH = 0 << 8
+HIST_LOCATOR_AUTO = 0 << 8
 HIST_LOCATOR_LEARNED = 1 << 8
+HIST_LOCATOR_BSEARCH = 2 << 8
 
 
 class HistError(RuntimeError):
@@ -115,6 +116,7 @@ def load(path: str | None = None):
             "hist_batch_fill": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
             "hist_batch_tune": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
             "hist_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+            "hist_locator_mode": (ctypes.c_int, [_P, ctypes.c_int]),
             "hist_kernel_time": (ctypes.c_int, [_P, _P, _P]),
             "hist_batch_configure": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                     ctypes.c_int32, _P]),
@@ -316,6 +318,16 @@ def hist_batch_configure(b: int, strategy: int, smem_bytes: int, cost_cap_tenths
     _check(load().hist_batch_configure(b, int(strategy), int(smem_bytes), int(cost_cap_tenths), int(pace_tiles),
                                        ctypes.byref(r)), "hist_batch_configure")
     return {f: getattr(r, f) for f, _ in hist_batch_tuning_t._fields_}
+
+
+LOCATOR_MODES = {0: "affine", 1: "bsearch", 2: "learned", 3: "bucket"}
+
+
+def hist_locator_mode(h: int, axis: int = 0) -> str:
+    m = load().hist_locator_mode(h, int(axis))
+    if m < 0:
+        raise HistError(m, "hist_locator_mode")
+    return LOCATOR_MODES[m]
 
 
 def hist_set_kernel_timing(h: int, on: bool) -> None:

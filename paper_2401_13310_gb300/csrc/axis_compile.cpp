@@ -184,3 +184,99 @@ bool affine_estimate(int32_t nbins, double xmin, double xmax, float* scale, floa
 }
 
 }  // namespace hgb
+
+namespace hgb {
+
+float host_est_float(double x) {
+  uint64_t b;
+  std::memcpy(&b, &x, 8);
+  const uint32_t hi = (uint32_t)(b >> 32);
+  const uint32_t sgn = hi & 0x80000000u;
+  const uint32_t e = (hi >> 20) & 0x7FFu;
+  uint32_t f = ((uint32_t)(b >> 29) - 0xC0000000u) & 0x7FFFFFFFu;
+  f = (e < 897u) ? 0u : f;
+  f = (e > 1150u) ? 0x7F000000u : f;
+  f |= sgn;
+  float r;
+  std::memcpy(&r, &f, 4);
+  return r;
+}
+
+// The device evaluates the same expressions: __fmaf_rn and a round-down
+// conversion (linear), or the float's bits (logarithmic); both clamp.
+int bucket_of(const BucketMap& m, float xf) {
+  int b;
+  if (m.log_map) {
+    uint32_t u;
+    std::memcpy(&u, &xf, 4);
+    b = (int)(u >> m.shift) - m.base;
+    if ((int32_t)u < 0) b = 0;
+  } else {
+    float t = std::fmaf(xf, m.scale, m.offset);
+    t = std::fmin(std::fmax(t, -1.0f), (float)m.nbk);
+    b = (int)std::floor(t);
+  }
+  return b < 0 ? 0 : (b > m.nbk - 1 ? m.nbk - 1 : b);
+}
+
+namespace {
+
+// Bucket of every threshold T[1..nbins+1] under map m; the most in one.
+int bucket_histogram(const BucketMap& m, int32_t nbins, const int64_t* T, std::vector<int32_t>* count) {
+  count->assign((size_t)m.nbk, 0);
+  int most = 0;
+  for (int32_t k = 1; k <= nbins + 1; ++k) {
+    const int b = bucket_of(m, host_est_float(host_double_of_key(T[k])));
+    const int c = ++(*count)[(size_t)b];
+    if (c > most) most = c;
+  }
+  return most;
+}
+
+}  // namespace
+
+int build_bucket_map(int32_t nbins, const int64_t* T, int32_t nbk, BucketMap* map, std::vector<int32_t>* cnt) {
+  const float x0 = host_est_float(host_double_of_key(T[1]));
+  const float x1 = host_est_float(host_double_of_key(T[nbins + 1]));
+  if (!(std::isfinite(x0) && std::isfinite(x1)) || !(x1 > x0)) return -1;
+  std::vector<int32_t> count, best_count;
+  int best = -1;
+  BucketMap lin;
+  std::memset(&lin, 0, sizeof(lin));
+  lin.nbk = nbk;
+  lin.log_map = 0;
+  lin.scale = (float)((double)nbk / ((double)x1 - (double)x0));
+  lin.offset = (float)(-(double)x0 * (double)lin.scale);
+  if (std::isfinite(lin.scale) && lin.scale > 0.0f && std::isfinite(lin.offset)) {
+    best = bucket_histogram(lin, nbins, T, &best_count);
+    *map = lin;
+  }
+  if (x0 > 0.0f) {  // logarithmic map: positive range only
+    uint32_t u0, u1;
+    std::memcpy(&u0, &x0, 4);
+    std::memcpy(&u1, &x1, 4);
+    int shift = 0;
+    while (shift < 31 && (int64_t)(u1 >> shift) - (int64_t)(u0 >> shift) >= nbk) ++shift;
+    BucketMap lg;
+    std::memset(&lg, 0, sizeof(lg));
+    lg.nbk = nbk;
+    lg.log_map = 1;
+    lg.shift = shift;
+    lg.base = (int32_t)(u0 >> shift);
+    const int most = bucket_histogram(lg, nbins, T, &count);
+    if (best < 0 || most < best) {
+      best = most;
+      best_count.swap(count);
+      *map = lg;
+    }
+  }
+  if (best < 0) return -1;
+  cnt->assign((size_t)nbk + 1, 0);
+  for (int32_t b = 0; b < nbk; ++b) (*cnt)[(size_t)b + 1] = (*cnt)[(size_t)b] + best_count[(size_t)b];
+  int top = 0;
+  while (best > 0 && (top == 0 || top * 2 <= best)) top = top ? top * 2 : 1;
+  map->top = top;
+  return best;
+}
+
+}  // namespace hgb

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 
 namespace hgb {
 
@@ -24,5 +25,20 @@ void build_variable_thresholds(int32_t nbins, const double* edges, int64_t* T);
 // the fixed-width formula) with a proven bound eps on |v - (1 + q)|; returns
 // false when the axis is outside the range where such a bound stays < 1/4.
 bool affine_estimate(int32_t nbins, double xmin, double xmax, float* scale, float* offset, float* eps);
+
+// FP32 value of a binary64 with its significand truncated to 24 bits,
+// saturating (|x| < 2^-126 -> +-0, |x| >= 2^128 -> +-2^127), from the bits
+// exactly as the device computes it.
+float host_est_float(double x);
+
+// The bucket map and counts of a variable axis (T: its nbins + 3 keys) for
+// the LOC_BUCKET locate; cnt receives nbk + 1 counts.  Returns the most
+// thresholds that share one bucket, or -1 when no map applies.
+struct BucketMap {
+  int32_t nbk, log_map, shift, base, top;
+  float scale, offset;
+};
+int build_bucket_map(int32_t nbins, const int64_t* T, int32_t nbk, BucketMap* map, std::vector<int32_t>* cnt);
+int bucket_of(const BucketMap& m, float xf);
 
 }  // namespace hgb

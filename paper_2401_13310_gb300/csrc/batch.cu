@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_fill(const __grid_constant__ B
 #pragma unroll
         for (int e = 0; e < kEv; ++e) {
           if (!valid[e]) continue;
-          const int k = locate_axis(d.ax, T, Thi, xb[e], xf[e], f32ok[e]);
+          const int k = locate_axis(d.ax, T, Thi, d.ax.bk.cnt, xb[e], xf[e], f32ok[e]);
           if (in_smem)
             batch_add<UNIT, true>(d, sbins, k, V[e], wok[e], wb[e]);
           else

@@ -133,7 +133,7 @@ __device__ __forceinline__ void fill_frags(const SliceFragDev* sfr, int f0, int 
       int k;
       if (koff < 0) {
         const unsigned long long b = ev.xb[e];
-        k = locate_mode<LOC_AFFINE>(d.ax, d.ax.T, nullptr, b, hi24(b), in_f32(exp_field(b)));
+        k = locate_mode<LOC_AFFINE>(d.ax, d.ax.T, nullptr, nullptr, b, hi24(b), in_f32(exp_field(b)));
       } else {
         k = d.a + count_le(skeys + koff, d.b - d.a - 1, d.top, key);
       }

@@ -110,9 +110,37 @@ __device__ __noinline__ int locate_exact(const long long* T, int nbins, int k, u
   return k;
 }
 
+// LOC_BUCKET: range tests on the key, the coordinate's bucket, then the
+// bucket's own thresholds (at most a few) by binary lifting.  Exact: the map
+// is monotone and the host placed every threshold with the same arithmetic.
+__device__ __forceinline__ int locate_bucket(const AxisDev& a, const long long* T, const int* cnt,
+                                             unsigned long long b, long long key) {
+  if (key < T[1]) return 0;
+  if (key >= T[a.nbins + 1]) return a.nbins + 1;
+  const float xf = est_float(b);
+  int bk;
+  if (a.bk.log_map) {
+    const unsigned u = __float_as_uint(xf);
+    bk = (int)(u >> a.bk.shift) - a.bk.base;
+    bk = ((int)u < 0) ? 0 : bk;
+  } else {
+    const float t = fminf(fmaxf(__fmaf_rn(xf, a.bk.scale, a.bk.offset), -1.0f), (float)a.bk.nbk);
+    bk = __float2int_rd(t);
+  }
+  bk = min(max(bk, 0), a.bk.nbk - 1);
+  const int k = cnt[bk];
+  const int n_in = cnt[bk + 1] - k;
+  int pos = 0;
+  for (int step = a.bk.top; step > 0; step >>= 1) {
+    const int q = pos + step;
+    if (q <= n_in && T[k + q] <= key) pos = q;
+  }
+  return k + pos;
+}
+
 // Bin of one coordinate on one axis (Sec. 3.1 step 1), exact.
 // xf: the coordinate as FP32 (hi24), valid when in_f32 of its exponent field.
-__device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T, const int* Thi,
+__device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T, const int* Thi, const int* cnt,
                                            unsigned long long b, float xf, bool f32ok) {
   if (a.mode == LOC_AFFINE) {
     // v estimates 1 + q; t = floor(v) + 1.5*2^23 exactly while |v| < 2^22.
@@ -128,6 +156,7 @@ __device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T,
     return locate_exact(T, a.nbins, k, b);
   }
   const long long key = key_of(b);
+  if (a.mode == LOC_BUCKET) return locate_bucket(a, T, cnt, b, key);
   if (a.mode == LOC_LEARNED) {
     // the trained index model, then an exact search of the certified window;
     // a window that does not bracket the key falls back to the full search
@@ -145,9 +174,9 @@ __device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T,
 // kernels are specialised per mode so each keeps only its own path), or
 // chosen at run time (LOC < 0).
 template <int LOC>
-__device__ __forceinline__ int locate_mode(const AxisDev& a, const long long* T, const int* Thi,
+__device__ __forceinline__ int locate_mode(const AxisDev& a, const long long* T, const int* Thi, const int* cnt,
                                            unsigned long long b, float xf, bool f32ok) {
-  if (LOC < 0) return locate_axis(a, T, Thi, b, xf, f32ok);
+  if (LOC < 0) return locate_axis(a, T, Thi, cnt, b, xf, f32ok);
   if (LOC == LOC_AFFINE) {  // as in locate_axis
     const float v = __fmaf_rn(xf, a.scale, a.offset);
     const float t = __fadd_rd(v, kMagic);
@@ -159,6 +188,7 @@ __device__ __forceinline__ int locate_mode(const AxisDev& a, const long long* T,
     return locate_exact(T, a.nbins, k, b);
   }
   const long long key = key_of(b);
+  if (LOC == LOC_BUCKET) return locate_bucket(a, T, cnt, b, key);
   if (LOC == LOC_LEARNED) {
     const float kh = lm_eval(a.lm, est_float(b));
     const int k0 = (int)floorf(__fadd_rn(kh, 0.5f));

@@ -208,6 +208,7 @@ struct Filler {
   static constexpr int NS = NStats<NDIM>::NS;
   const FillParams& p;
   const long long* Tax[NDIM];
+  const int* BKx[NDIM];  // bucket counts (LOC_BUCKET), shared or global
   const int* Thi[NDIM];  // high words of the shared-memory thresholds (nullptr: global table)
   unsigned* sbins;
   double* sbins_f64;
@@ -227,7 +228,7 @@ struct Filler {
     for (int d = 0; d < NDIM; ++d) {
       ef[d] = exp_field(cb[d]);
       xf[d] = hi24(cb[d]);
-      const int k = locate_mode<LOC>(p.ax[d], Tax[d], Thi[d], cb[d], xf[d], in_f32(ef[d]));
+      const int k = locate_mode<LOC>(p.ax[d], Tax[d], Thi[d], BKx[d], cb[d], xf[d], in_f32(ef[d]));
       inr = inr && ((unsigned)(k - 1) < (unsigned)p.ax[d].nbins);
       g += (long long)k * (d == 0 ? 1 : (d == 1 ? stride1 : stride2));
     }
@@ -380,7 +381,9 @@ __global__ void __launch_bounds__(256, NDIM == 1 ? HGB_MIN_BLOCKS_1D : HGB_MIN_B
   const int nkeys = p.table_keys;
   long long* skeys = reinterpret_cast<long long*>(smem_raw);
   int* shi = reinterpret_cast<int*>(smem_raw + (size_t)nkeys * 8);
-  unsigned char* after_keys = smem_raw + (((size_t)nkeys * 12 + 15) & ~(size_t)15);
+  int* sbk = reinterpret_cast<int*>(smem_raw + (((size_t)nkeys * 12 + 15) & ~(size_t)15));
+  unsigned char* after_keys =
+      smem_raw + (((size_t)nkeys * 12 + 15) & ~(size_t)15) + (((size_t)p.table_bk * 4 + 15) & ~(size_t)15);
   __shared__ double sred[8 * kMaxStats];
 
   Filler<NDIM, ACC, SMEM, LOC> f(p);
@@ -391,11 +394,13 @@ __global__ void __launch_bounds__(256, NDIM == 1 ? HGB_MIN_BLOCKS_1D : HGB_MIN_B
     skeys[i] = t;
     shi[i] = (int)(t >> 32);
   }
+  for (int i = threadIdx.x; i < p.table_bk; i += blockDim.x) sbk[i] = p.BK_concat[i];
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
     const bool staged = p.ax[d].smem_off >= 0;
     f.Tax[d] = staged ? skeys + p.ax[d].smem_off : p.ax[d].T;
     f.Thi[d] = staged ? shi + p.ax[d].smem_off : nullptr;
+    f.BKx[d] = p.ax[d].bk.smem_off >= 0 ? sbk + p.ax[d].bk.smem_off : p.ax[d].bk.cnt;
   }
   const int nb = (int)p.nbins_total;
   if (SMEM) {
@@ -528,7 +533,7 @@ __global__ void __launch_bounds__(256) k_locate(const FillParams p, long long* _
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
       const unsigned long long b = dbits(__ldcs(p.col[d] + i));
-      const int k = locate_axis(p.ax[d], p.ax[d].T, nullptr, b, hi24(b), in_f32(exp_field(b)));
+      const int k = locate_axis(p.ax[d], p.ax[d].T, nullptr, p.ax[d].bk.cnt, b, hi24(b), in_f32(exp_field(b)));
       g += (long long)k * (d == 0 ? 1 : (d == 1 ? stride1 : stride2));
     }
     out[i] = g;
@@ -542,6 +547,7 @@ const void* fill_fn(int loc) {
   } else {
     if (loc == LOC_AFFINE) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_AFFINE>);
     if (loc == LOC_LEARNED) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_LEARNED>);
+    if (loc == LOC_BUCKET) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_BUCKET>);
     return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_BSEARCH>);
   }
 }
@@ -577,7 +583,7 @@ int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shap
   const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0, p.ax[0].mode);
   if (fn == nullptr) return -1;
   const int block = 256;
-  size_t smem = (((size_t)p.table_keys * 12 + 15) & ~(size_t)15);
+  size_t smem = (((size_t)p.table_keys * 12 + 15) & ~(size_t)15) + (((size_t)p.table_bk * 4 + 15) & ~(size_t)15);
   if (p.smem_bins) smem += (size_t)p.nbins_total * smem_bin_bytes(acc_mode, p.track_counts);
   if (smem > 48 * 1024) {
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;

@@ -30,6 +30,9 @@ namespace {
 
 constexpr int kDefaultFxElo = 1015;             // |w| in [2^-8, 2^8) summed exactly
 constexpr size_t kSmemTableBudget = 64 * 1024;  // threshold keys staged per block
+constexpr size_t kSmemBucketBudget = 32 * 1024; // bucket counts staged per block
+constexpr int kBucketMax = 1 << 22;             // buckets of one axis at most
+constexpr int kBucketMaxRun = 16;               // most thresholds in one bucket for LOC_BUCKET
 #ifndef HGB_SMEM_BINS_BUDGET
 #define HGB_SMEM_BINS_BUDGET (96 * 1024)
 #endif
@@ -55,6 +58,11 @@ struct hist {
   int32_t loc_mode[kMaxDim] = {0, 0, 0};
   float scale[kMaxDim] = {0, 0, 0}, offset[kMaxDim] = {0, 0, 0}, eps[kMaxDim] = {1, 1, 1};
   std::vector<int64_t> T_host[kMaxDim];  // host copy of the thresholds
+  // bucket maps of the LOC_BUCKET axes
+  int* d_BK = nullptr;       // concatenated bucket counts
+  int32_t bk_off[kMaxDim] = {-1, -1, -1};
+  int32_t smem_bk = 0;       // how many bucket counts are staged into shared memory
+  BucketDev bk[kMaxDim] = {};
   int2* lm_knots[kMaxDim] = {nullptr, nullptr, nullptr};
   LearnedDev lm[kMaxDim] = {};
   int config_version = 0;    // bumped when a locator is installed (batches rebuild descriptors)
@@ -102,6 +110,7 @@ void free_state(hist* h) {
   if (h->done) cudaEventDestroy(h->done);
   for (cudaEvent_t e : h->t_ev) cudaEventDestroy(e);
   cudaFree(h->d_T);
+  cudaFree(h->d_BK);
   cudaFree(h->g_lo);
   cudaFree(h->g_hi);
   cudaFree(h->g_count);
@@ -142,6 +151,8 @@ FillParams make_params(const hist* h, const double* values, const double* weight
     a.offset = h->offset[d];
     a.eps = h->eps[d];
     a.lm = h->lm[d];
+    a.bk = h->bk[d];
+    if (h->bk_off[d] >= 0) a.bk.smem_off = (h->bk_off[d] + h->bk[d].nbk + 1 <= h->smem_bk) ? h->bk_off[d] : -1;
     p.col[d] = values + (size_t)d * (size_t)n;
   }
   p.w = weights;
@@ -154,6 +165,8 @@ FillParams make_params(const hist* h, const double* values, const double* weight
   p.track_counts = (h->flags & HIST_TRACK_COUNTS) ? 1 : 0;
   p.fx_elo = h->fx_elo;
   p.table_keys = h->smem_keys;
+  p.BK_concat = h->d_BK;
+  p.table_bk = h->smem_bk;
   bool al = weights == nullptr || aligned16(weights);
   for (int d = 0; d < h->ndim; ++d) al = al && aligned16(p.col[d]);
   p.aligned = al ? 1 : 0;
@@ -262,6 +275,11 @@ extern "C" {
 
 const char* hist_version(void) { return "gb300-hist 0.1 (sm_103a)"; }
 
+int hist_locator_mode(const hist_t* h, int axis) {
+  if (h == nullptr || axis < 0 || axis >= h->ndim) return HIST_ERR_ARG;
+  return h->loc_mode[axis];
+}
+
 int hist_set_kernel_timing(hist_t* h, int on) {
   if (h == nullptr) return HIST_ERR_ARG;
   h->timing = on != 0;
@@ -320,7 +338,7 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
   const uint32_t known = HIST_TRACK_COUNTS | HIST_STAT_OVERFLOWS | HIST_PREC_MASK | HIST_LOCATOR_MASK;
   if (flags & ~known) return HIST_ERR_ARG;
   if ((flags & HIST_PREC_MASK) == (3u << 4)) return HIST_ERR_ARG;
-  if ((flags & HIST_LOCATOR_MASK) > HIST_LOCATOR_LEARNED) return HIST_ERR_ARG;
+  if ((flags & HIST_LOCATOR_MASK) > HIST_LOCATOR_BSEARCH) return HIST_ERR_ARG;
   int64_t total = 1;
   for (int d = 0; d < ndim; ++d) {
     const hist_axis_t& a = axes[d];
@@ -345,6 +363,7 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
     h->flags = flags;
     h->nbins_total = total;
     std::vector<int64_t> T;
+    std::vector<int32_t> BK;
     for (int d = 0; d < ndim; ++d) {
       const hist_axis_t& a = axes[d];
       h->kind[d] = a.kind;
@@ -360,6 +379,28 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
       } else {
         build_variable_thresholds(a.nbins, a.edges, Td);
         h->loc_mode[d] = LOC_BSEARCH;
+        if ((flags & HIST_LOCATOR_MASK) != HIST_LOCATOR_BSEARCH) {
+          // a bucket map when one keeps every bucket's thresholds few
+          int nbk = 64;
+          while (nbk < 2 * (a.nbins + 1) && nbk < kBucketMax) nbk *= 2;
+          BucketMap m;
+          std::vector<int32_t> cnt;
+          const int most = build_bucket_map(a.nbins, Td, nbk, &m, &cnt);
+          if (most >= 0 && most <= kBucketMaxRun) {
+            h->loc_mode[d] = LOC_BUCKET;
+            h->bk_off[d] = (int32_t)BK.size();
+            BK.insert(BK.end(), cnt.begin(), cnt.end());
+            BucketDev& bd = h->bk[d];
+            bd.nbk = m.nbk;
+            bd.log_map = m.log_map;
+            bd.scale = m.scale;
+            bd.offset = m.offset;
+            bd.shift = m.shift;
+            bd.base = m.base;
+            bd.top = m.top;
+            bd.smem_off = -1;
+          }
+        }
       }
       h->T_host[d].assign(Td, Td + a.nbins + 3);
     }
@@ -369,6 +410,20 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
     for (int d = 0; d < ndim; ++d) {
       const int32_t end = h->t_off[d] + h->nbins[d] + 3;
       if ((size_t)end * 8 <= kSmemTableBudget) h->smem_keys = end;
+    }
+    // and a prefix of the bucket counts
+    h->smem_bk = 0;
+    for (int d = 0; d < ndim; ++d)
+      if (h->bk_off[d] >= 0 && (size_t)(h->bk_off[d] + h->bk[d].nbk + 1) * 4 <= kSmemBucketBudget)
+        h->smem_bk = h->bk_off[d] + h->bk[d].nbk + 1;
+    if (!BK.empty()) {
+      if ((rc = dalloc(&h->d_BK, BK.size() * sizeof(int32_t))) != HIST_OK) break;
+      if (cudaMemcpy(h->d_BK, BK.data(), BK.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        rc = HIST_ERR_CUDA;
+        break;
+      }
+      for (int d = 0; d < ndim; ++d)
+        if (h->bk_off[d] >= 0) h->bk[d].cnt = h->d_BK + h->bk_off[d];
     }
     rc = dalloc(&h->d_T, T.size() * sizeof(int64_t));
     if (rc != HIST_OK) break;
@@ -867,6 +922,8 @@ int batch_upload(hist_batch* b) {
     d.ax.offset = h->offset[0];
     d.ax.eps = h->eps[0];
     d.ax.lm = h->lm[0];
+    d.ax.bk = h->bk[0];
+    d.ax.bk.smem_off = -1;
     d.col = b->col[i];
     d.group = b->group[i];
     d.sbin_off = b->sbin_off[i];
@@ -918,6 +975,8 @@ SliceFragDev slice_frag(const hist* h, long long a, long long m) {
   d.ax.offset = h->offset[0];
   d.ax.eps = h->eps[0];
   d.ax.lm = h->lm[0];
+  d.ax.bk = h->bk[0];
+  d.ax.bk.smem_off = -1;
   d.a = (int)a;
   d.b = (int)(a + m);
   d.Ta = h->T_host[0][a];

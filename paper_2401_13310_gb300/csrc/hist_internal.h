@@ -26,6 +26,24 @@ enum LocMode : int32_t {
   LOC_AFFINE = 0,   // FP32 affine estimate from the coordinate, then <= 1 step correction
   LOC_BSEARCH = 1,  // branchless binary search over the thresholds
   LOC_LEARNED = 2,  // trained piecewise-linear index model + windowed search
+  LOC_BUCKET = 3,   // monotone bucket map of the coordinate + the bucket's few thresholds
+};
+
+// LOC_BUCKET: a monotone map m of the in-range coordinate onto nbk buckets
+// (linear: floor(xf * scale + offset); logarithmic, for positive ranges:
+// (bits(xf) >> shift) - base), and cnt[b] = number of thresholds T[1..nbins+1]
+// whose own coordinate maps below bucket b.  Every threshold below bucket b
+// is <= any key in it and every one above is greater, so the bin of an
+// in-range key in bucket b is cnt[b] plus the number of the bucket's own
+// thresholds T[cnt[b]+1 .. cnt[b+1]] that are <= the key.
+struct BucketDev {
+  const int* cnt;       // [nbk + 1] (global; the fill kernels may stage it)
+  int32_t nbk;          // number of buckets
+  int32_t log_map;      // 0: linear map, 1: logarithmic map
+  float scale, offset;  // linear map
+  int32_t shift, base;  // logarithmic map
+  int32_t top;          // largest power of two <= the most thresholds in one bucket (0: none)
+  int32_t smem_off;     // offset of cnt in the shared copy (ints), -1: global
 };
 
 // How weights reach the bins.
@@ -51,6 +69,7 @@ struct AxisDev {
   float scale, offset; // LOC_AFFINE: v = xf * scale + offset estimates 1 + q of the formula
   float eps;           // proven bound on |v - (1 + q)|; floor(v) is exact when frac(v) is farther than eps from an integer
   LearnedDev lm;
+  BucketDev bk;
 };
 
 struct FillParams {
@@ -58,6 +77,8 @@ struct FillParams {
   const double* col[kMaxDim];
   const double* w;              // nullptr = unit weights
   const long long* T_concat;    // all axes' keys back to back (shared-memory staging source)
+  const int* BK_concat;         // all bucket-mapped axes' bucket counts back to back
+  int32_t table_bk;             // bucket counts staged into shared memory
   long long n;
   long long nbins_total;
   int32_t ndim;

@@ -66,9 +66,9 @@ def test_learned_locate_bit_exact(B, nedges):
     print(f"nedges={nedges}: {rep}")
 
 
-def _time_fill(B, axis, x, learned, reps=5):
+def _time_fill(B, axis, x, learned, reps=5, flags=None):
     import torch
-    h = B.Hist([axis])
+    h = B.Hist([axis], B.HIST_LOCATOR_BSEARCH if flags is None else flags)
     try:
         if learned:
             h.train_locator(0)
@@ -94,8 +94,11 @@ def test_learned_locator_gain_over_binary_search(B, nedges):
     x = W.mixture_values(20_000_000, device="cuda", seed=13)
     t_bs, c_bs = _time_fill(B, axis, x, learned=False)
     t_lm, c_lm = _time_fill(B, axis, x, learned=True)
+    t_bk, c_bk = _time_fill(B, axis, x, learned=False, flags=B.HIST_LOCATOR_AUTO)
     assert np.array_equal(c_bs, c_lm)
-    print(f"nedges={nedges}: binary search {t_bs:.3f} ms, learned {t_lm:.3f} ms, gain {t_bs / t_lm:.2f}x")
+    assert np.array_equal(c_bs, c_bk)
+    print(f"nedges={nedges}: binary search {t_bs:.3f} ms, learned {t_lm:.3f} ms, gain {t_bs / t_lm:.2f}x; "
+          f"default locator {t_bk:.3f} ms")
     assert t_lm < t_bs
 
 
