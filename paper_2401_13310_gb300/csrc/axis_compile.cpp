@@ -202,21 +202,19 @@ float host_est_float(double x) {
   return r;
 }
 
-// The device evaluates the same expressions: __fmaf_rn and a round-down
-// conversion (linear), or the float's bits (logarithmic); both clamp.
-int bucket_of(const BucketMap& m, float xf) {
-  int b;
-  if (m.log_map) {
-    uint32_t u;
-    std::memcpy(&u, &xf, 4);
-    b = (int)(u >> m.shift) - m.base;
-    if ((int32_t)u < 0) b = 0;
+// The device evaluates the same expressions: a shift of the key (key map),
+// or __fmaf_rn on the truncated coordinate and a round-down conversion
+// (linear map); both clamp.  Each is monotone in the key.
+int bucket_of(const BucketMap& m, int64_t key) {
+  int64_t b;
+  if (m.key_map) {
+    b = (key >> m.shift) - m.kbase;
   } else {
-    float t = std::fmaf(xf, m.scale, m.offset);
+    float t = std::fmaf(host_est_float(host_double_of_key(key)), m.scale, m.offset);
     t = std::fmin(std::fmax(t, -1.0f), (float)m.nbk);
-    b = (int)std::floor(t);
+    b = (int64_t)std::floor(t);
   }
-  return b < 0 ? 0 : (b > m.nbk - 1 ? m.nbk - 1 : b);
+  return b < 0 ? 0 : (b > m.nbk - 1 ? m.nbk - 1 : (int)b);
 }
 
 namespace {
@@ -226,8 +224,7 @@ int bucket_histogram(const BucketMap& m, int32_t nbins, const int64_t* T, std::v
   count->assign((size_t)m.nbk, 0);
   int most = 0;
   for (int32_t k = 1; k <= nbins + 1; ++k) {
-    const int b = bucket_of(m, host_est_float(host_double_of_key(T[k])));
-    const int c = ++(*count)[(size_t)b];
+    const int c = ++(*count)[(size_t)bucket_of(m, T[k])];
     if (c > most) most = c;
   }
   return most;
@@ -236,41 +233,38 @@ int bucket_histogram(const BucketMap& m, int32_t nbins, const int64_t* T, std::v
 }  // namespace
 
 int build_bucket_map(int32_t nbins, const int64_t* T, int32_t nbk, BucketMap* map, std::vector<int32_t>* cnt) {
-  const float x0 = host_est_float(host_double_of_key(T[1]));
-  const float x1 = host_est_float(host_double_of_key(T[nbins + 1]));
-  if (!(std::isfinite(x0) && std::isfinite(x1)) || !(x1 > x0)) return -1;
+  const int64_t k0 = T[1], k1 = T[nbins + 1];
+  if (!(k1 > k0)) return -1;
   std::vector<int32_t> count, best_count;
-  int best = -1;
-  BucketMap lin;
-  std::memset(&lin, 0, sizeof(lin));
-  lin.nbk = nbk;
-  lin.log_map = 0;
-  lin.scale = (float)((double)nbk / ((double)x1 - (double)x0));
-  lin.offset = (float)(-(double)x0 * (double)lin.scale);
-  if (std::isfinite(lin.scale) && lin.scale > 0.0f && std::isfinite(lin.offset)) {
-    best = bucket_histogram(lin, nbins, T, &best_count);
-    *map = lin;
-  }
-  if (x0 > 0.0f) {  // logarithmic map: positive range only
-    uint32_t u0, u1;
-    std::memcpy(&u0, &x0, 4);
-    std::memcpy(&u1, &x1, 4);
-    int shift = 0;
-    while (shift < 31 && (int64_t)(u1 >> shift) - (int64_t)(u0 >> shift) >= nbk) ++shift;
-    BucketMap lg;
-    std::memset(&lg, 0, sizeof(lg));
-    lg.nbk = nbk;
-    lg.log_map = 1;
-    lg.shift = shift;
-    lg.base = (int32_t)(u0 >> shift);
-    const int most = bucket_histogram(lg, nbins, T, &count);
-    if (best < 0 || most < best) {
-      best = most;
-      best_count.swap(count);
-      *map = lg;
+  // key map: the smallest shift that spreads [k0, k1] over at most nbk buckets
+  BucketMap km;
+  std::memset(&km, 0, sizeof(km));
+  km.nbk = nbk;
+  km.key_map = 1;
+  // (the difference in unsigned arithmetic: k1 - k0 can exceed INT64_MAX)
+  while (km.shift < 63 && (uint64_t)(k1 >> km.shift) - (uint64_t)(k0 >> km.shift) >= (uint64_t)nbk) ++km.shift;
+  km.kbase = k0 >> km.shift;
+  int best = bucket_histogram(km, nbins, T, &best_count);
+  *map = km;
+  // linear map of the truncated coordinate, when the range is finite in FP32
+  const float x0 = host_est_float(host_double_of_key(k0));
+  const float x1 = host_est_float(host_double_of_key(k1));
+  if (std::isfinite(x0) && std::isfinite(x1) && x1 > x0) {
+    BucketMap lin;
+    std::memset(&lin, 0, sizeof(lin));
+    lin.nbk = nbk;
+    lin.key_map = 0;
+    lin.scale = (float)((double)nbk / ((double)x1 - (double)x0));
+    lin.offset = (float)(-(double)x0 * (double)lin.scale);
+    if (std::isfinite(lin.scale) && lin.scale > 0.0f && std::isfinite(lin.offset)) {
+      const int most = bucket_histogram(lin, nbins, T, &count);
+      if (most < best) {
+        best = most;
+        best_count.swap(count);
+        *map = lin;
+      }
     }
   }
-  if (best < 0) return -1;
   cnt->assign((size_t)nbk + 1, 0);
   for (int32_t b = 0; b < nbk; ++b) (*cnt)[(size_t)b + 1] = (*cnt)[(size_t)b] + best_count[(size_t)b];
   int top = 0;

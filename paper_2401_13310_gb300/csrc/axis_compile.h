@@ -35,10 +35,11 @@ float host_est_float(double x);
 // the LOC_BUCKET locate; cnt receives nbk + 1 counts.  Returns the most
 // thresholds that share one bucket, or -1 when no map applies.
 struct BucketMap {
-  int32_t nbk, log_map, shift, base, top;
+  int32_t nbk, key_map, shift, top;
+  int64_t kbase;
   float scale, offset;
 };
 int build_bucket_map(int32_t nbins, const int64_t* T, int32_t nbk, BucketMap* map, std::vector<int32_t>* cnt);
-int bucket_of(const BucketMap& m, float xf);
+int bucket_of(const BucketMap& m, int64_t key);
 
 }  // namespace hgb

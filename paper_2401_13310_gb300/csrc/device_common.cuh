@@ -115,19 +115,20 @@ __device__ __noinline__ int locate_exact(const long long* T, int nbins, int k, u
 // is monotone and the host placed every threshold with the same arithmetic.
 __device__ __forceinline__ int locate_bucket(const AxisDev& a, const long long* T, const int* cnt,
                                              unsigned long long b, long long key) {
-  if (key < T[1]) return 0;
-  if (key >= T[a.nbins + 1]) return a.nbins + 1;
-  const float xf = est_float(b);
+  if (key < a.bk.lo_key) return 0;
+  if (key >= a.bk.hi_key) return a.nbins + 1;
   int bk;
-  if (a.bk.log_map) {
-    const unsigned u = __float_as_uint(xf);
-    bk = (int)(u >> a.bk.shift) - a.bk.base;
-    bk = ((int)u < 0) ? 0 : bk;
+  if (a.bk.key_map) {
+    bk = (int)((key >> a.bk.shift) - a.bk.kbase);
   } else {
-    const float t = fminf(fmaxf(__fmaf_rn(xf, a.bk.scale, a.bk.offset), -1.0f), (float)a.bk.nbk);
+    const float t = fminf(fmaxf(__fmaf_rn(est_float(b), a.bk.scale, a.bk.offset), -1.0f), (float)a.bk.nbk);
     bk = __float2int_rd(t);
   }
   bk = min(max(bk, 0), a.bk.nbk - 1);
+  if (a.bk.single) {
+    const longlong2 e = reinterpret_cast<const longlong2*>(cnt)[bk];
+    return (int)e.y + (key >= e.x ? 1 : 0);
+  }
   const int k = cnt[bk];
   const int n_in = cnt[bk + 1] - k;
   int pos = 0;

@@ -95,6 +95,9 @@ struct hist {
 
 namespace {
 
+// Ints of an axis' bucket table.
+int bucket_ints(const BucketDev& b) { return b.single ? 4 * b.nbk : b.nbk + 1; }
+
 template <class T>
 int dalloc(T** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -152,7 +155,7 @@ FillParams make_params(const hist* h, const double* values, const double* weight
     a.eps = h->eps[d];
     a.lm = h->lm[d];
     a.bk = h->bk[d];
-    if (h->bk_off[d] >= 0) a.bk.smem_off = (h->bk_off[d] + h->bk[d].nbk + 1 <= h->smem_bk) ? h->bk_off[d] : -1;
+    if (h->bk_off[d] >= 0) a.bk.smem_off = (h->bk_off[d] + bucket_ints(h->bk[d]) <= h->smem_bk) ? h->bk_off[d] : -1;
     p.col[d] = values + (size_t)d * (size_t)n;
   }
   p.w = weights;
@@ -382,21 +385,38 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
         if ((flags & HIST_LOCATOR_MASK) != HIST_LOCATOR_BSEARCH) {
           // a bucket map when one keeps every bucket's thresholds few
           int nbk = 64;
-          while (nbk < 2 * (a.nbins + 1) && nbk < kBucketMax) nbk *= 2;
+          while (nbk < 4 * (a.nbins + 1) && nbk < kBucketMax) nbk *= 2;
           BucketMap m;
           std::vector<int32_t> cnt;
           const int most = build_bucket_map(a.nbins, Td, nbk, &m, &cnt);
           if (most >= 0 && most <= kBucketMaxRun) {
             h->loc_mode[d] = LOC_BUCKET;
+            while (BK.size() % 4) BK.push_back(0);  // 16-byte aligned tables
             h->bk_off[d] = (int32_t)BK.size();
-            BK.insert(BK.end(), cnt.begin(), cnt.end());
+            if (most <= 1) {
+              // (threshold, cnt) pairs: the bucket's one threshold, or INT64_MAX
+              for (int b = 0; b < nbk; ++b) {
+                const int64_t thr = cnt[(size_t)b + 1] > cnt[(size_t)b] ? Td[cnt[(size_t)b] + 1]
+                                                                       : std::numeric_limits<int64_t>::max();
+                const int64_t kk = cnt[(size_t)b];
+                int32_t w[4];
+                std::memcpy(w, &thr, 8);
+                std::memcpy(w + 2, &kk, 8);
+                BK.insert(BK.end(), w, w + 4);
+              }
+            } else {
+              BK.insert(BK.end(), cnt.begin(), cnt.end());
+            }
             BucketDev& bd = h->bk[d];
+            bd.single = most <= 1 ? 1 : 0;
+            bd.lo_key = Td[1];
+            bd.hi_key = Td[a.nbins + 1];
             bd.nbk = m.nbk;
-            bd.log_map = m.log_map;
+            bd.key_map = m.key_map;
             bd.scale = m.scale;
             bd.offset = m.offset;
             bd.shift = m.shift;
-            bd.base = m.base;
+            bd.kbase = m.kbase;
             bd.top = m.top;
             bd.smem_off = -1;
           }
@@ -414,8 +434,8 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
     // and a prefix of the bucket counts
     h->smem_bk = 0;
     for (int d = 0; d < ndim; ++d)
-      if (h->bk_off[d] >= 0 && (size_t)(h->bk_off[d] + h->bk[d].nbk + 1) * 4 <= kSmemBucketBudget)
-        h->smem_bk = h->bk_off[d] + h->bk[d].nbk + 1;
+      if (h->bk_off[d] >= 0 && (size_t)(h->bk_off[d] + bucket_ints(h->bk[d])) * 4 <= kSmemBucketBudget)
+        h->smem_bk = h->bk_off[d] + bucket_ints(h->bk[d]);
     if (!BK.empty()) {
       if ((rc = dalloc(&h->d_BK, BK.size() * sizeof(int32_t))) != HIST_OK) break;
       if (cudaMemcpy(h->d_BK, BK.data(), BK.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {

@@ -29,21 +29,31 @@ enum LocMode : int32_t {
   LOC_BUCKET = 3,   // monotone bucket map of the coordinate + the bucket's few thresholds
 };
 
-// LOC_BUCKET: a monotone map m of the in-range coordinate onto nbk buckets
-// (linear: floor(xf * scale + offset); logarithmic, for positive ranges:
-// (bits(xf) >> shift) - base), and cnt[b] = number of thresholds T[1..nbins+1]
-// whose own coordinate maps below bucket b.  Every threshold below bucket b
-// is <= any key in it and every one above is greater, so the bin of an
-// in-range key in bucket b is cnt[b] plus the number of the bucket's own
-// thresholds T[cnt[b]+1 .. cnt[b+1]] that are <= the key.
+// LOC_BUCKET: a monotone map m of the in-range key onto nbk buckets
+// (linear in the coordinate: floor(xf * scale + offset), xf the coordinate
+// truncated to FP32; or a shift of the key itself: (key >> shift) - kbase,
+// which is logarithmic in the coordinate), and cnt[b] = the number of
+// thresholds T[1..nbins+1] whose own key maps below bucket b.  Every
+// threshold below bucket b is <= any key in it and every one above is
+// greater, so the bin of an in-range key in bucket b is cnt[b] plus the
+// number of the bucket's own thresholds T[cnt[b]+1 .. cnt[b+1]] that are <=
+// the key.
+// When no bucket holds more than one threshold the table is stored as
+// (threshold, cnt) pairs instead, one 16-byte load per locate: the bin is
+// cnt[b] + (key >= the bucket's threshold), INT64_MAX standing for none.
 struct BucketDev {
-  const int* cnt;       // [nbk + 1] (global; the fill kernels may stage it)
-  int32_t nbk;          // number of buckets
-  int32_t log_map;      // 0: linear map, 1: logarithmic map
-  float scale, offset;  // linear map
-  int32_t shift, base;  // logarithmic map
-  int32_t top;          // largest power of two <= the most thresholds in one bucket (0: none)
-  int32_t smem_off;     // offset of cnt in the shared copy (ints), -1: global
+  const int* cnt;          // [nbk + 1] counts, or [nbk] (threshold, cnt) int64 pairs when `single`
+                           // (global; the fill kernels may stage it)
+  long long lo_key;        // T[1]: keys below are underflow
+  long long hi_key;        // T[nbins + 1]: keys from here on are overflow
+  long long kbase;         // key map: bucket = (key >> shift) - kbase
+  int32_t nbk;             // number of buckets
+  int32_t key_map;         // 1: key map, 0: linear map
+  float scale, offset;     // linear map
+  int32_t shift;           // key map
+  int32_t top;             // largest power of two <= the most thresholds in one bucket (0: none)
+  int32_t smem_off;        // offset of the table in the shared copy (ints), -1: global
+  int32_t single;          // 1: the pair table
 };
 
 // How weights reach the bins.
