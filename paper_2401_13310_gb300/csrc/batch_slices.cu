@@ -122,22 +122,32 @@ __device__ __forceinline__ void fill_frags(const SliceFragDev* sfr, int f0, int 
                                            const unsigned long long (&wb)[kSliceEv]) {
   for (int f = f0; f < f1; ++f) {
     const SliceFragDev& d = sfr[f];
-    const long long Ta = d.Ta, Tb = d.Tb;
-    const bool whole = d.whole != 0;
     const int koff = d.key_off;
+    if (koff < 0) {
+      // the histogram's own locator (affine estimate, bucket map, learned
+      // model) over its global tables, for every event alike -- no
+      // divergence -- then the fragment test on the bin
+      const AxisDev ax = d.ax;
+      const int a = d.a, b = d.b;
 #pragma unroll
-    for (int e = 0; e < kSliceEv; ++e) {
-      if (!valid[e]) continue;
-      const long long key = ev.key[e];
-      if (!whole && (key < Ta || key >= Tb)) continue;
-      int k;
-      if (koff < 0) {
-        const unsigned long long b = ev.xb[e];
-        k = locate_mode<LOC_AFFINE>(d.ax, d.ax.T, nullptr, nullptr, b, hi24(b), in_f32(exp_field(b)));
-      } else {
-        k = d.a + count_le(skeys + koff, d.b - d.a - 1, d.top, key);
+      for (int e = 0; e < kSliceEv; ++e) {
+        if (!valid[e]) continue;
+        const unsigned long long xb = ev.xb[e];
+        const int k = locate_axis(ax, ax.T, nullptr, ax.bk.cnt, xb, hi24(xb), in_f32(exp_field(xb)));
+        if (k >= a && k < b) slice_add<UNIT>(d, sbins, k, V[e], wok[e], wb[e]);
       }
-      slice_add<UNIT>(d, sbins, k, V[e], wok[e], wb[e]);
+    } else {
+      // binary search over the fragment's own thresholds in shared memory
+      const long long Ta = d.Ta, Tb = d.Tb;
+      const bool whole = d.whole != 0;
+#pragma unroll
+      for (int e = 0; e < kSliceEv; ++e) {
+        if (!valid[e]) continue;
+        const long long key = ev.key[e];
+        if (!whole && (key < Ta || key >= Tb)) continue;
+        const int k = d.a + count_le(skeys + koff, d.b - d.a - 1, d.top, key);
+        slice_add<UNIT>(d, sbins, k, V[e], wok[e], wb[e]);
+      }
     }
   }
 }

@@ -384,8 +384,13 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
         h->loc_mode[d] = LOC_BSEARCH;
         if ((flags & HIST_LOCATOR_MASK) != HIST_LOCATOR_BSEARCH) {
           // a bucket map when one keeps every bucket's thresholds few
+          // small axes: 4 buckets per bin and, when no bucket holds two
+          // thresholds, the 16-byte pair table (staged in shared memory);
+          // large axes: 2 buckets per bin and the 4-byte counts, so that the
+          // tables of a batch of large axes stay within L2
           int nbk = 64;
-          while (nbk < 4 * (a.nbins + 1) && nbk < kBucketMax) nbk *= 2;
+          const bool small = 16LL * 4 * (a.nbins + 1) <= (long long)kSmemBucketBudget;
+          while (nbk < (small ? 4 : 2) * (a.nbins + 1) && nbk < kBucketMax) nbk *= 2;
           BucketMap m;
           std::vector<int32_t> cnt;
           const int most = build_bucket_map(a.nbins, Td, nbk, &m, &cnt);
@@ -393,7 +398,7 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
             h->loc_mode[d] = LOC_BUCKET;
             while (BK.size() % 4) BK.push_back(0);  // 16-byte aligned tables
             h->bk_off[d] = (int32_t)BK.size();
-            if (most <= 1) {
+            if (most <= 1 && 16LL * nbk <= (long long)kSmemBucketBudget) {
               // (threshold, cnt) pairs: the bucket's one threshold, or INT64_MAX
               for (int b = 0; b < nbk; ++b) {
                 const int64_t thr = cnt[(size_t)b + 1] > cnt[(size_t)b] ? Td[cnt[(size_t)b] + 1]
@@ -408,7 +413,7 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
               BK.insert(BK.end(), cnt.begin(), cnt.end());
             }
             BucketDev& bd = h->bk[d];
-            bd.single = most <= 1 ? 1 : 0;
+            bd.single = (most <= 1 && 16LL * nbk <= (long long)kSmemBucketBudget) ? 1 : 0;
             bd.lo_key = Td[1];
             bd.hi_key = Td[a.nbins + 1];
             bd.nbk = m.nbk;
@@ -1006,10 +1011,12 @@ SliceFragDev slice_frag(const hist* h, long long a, long long m) {
 }
 
 // Stage the fragment's keys (non-affine axes) and reserve its bins.
+bool slice_own_locator(const hist* h) { return h->loc_mode[0] != LOC_BSEARCH; }
+
 void slice_place(const hist* h, SliceFragDev& d, std::vector<int64_t>& keys, int* nkeys, int* nwords) {
   d.bin_off = *nwords;
   *nwords += 2 * (d.b - d.a);
-  if (h->loc_mode[0] == LOC_AFFINE) {
+  if (slice_own_locator(h)) {  // the histogram's own locator; no staged keys
     d.key_off = -1;
     d.top = 0;
     return;
@@ -1037,7 +1044,7 @@ void slice_plan(hist_batch* b, int budget, double cap) {
   const int nh = (int)b->hs.size();
   auto bytes_of = [&](int i) {
     const hist* h = b->hs[i];
-    return (long long)(h->nbins[0] + 2) * (h->loc_mode[0] == LOC_AFFINE ? 8 : 16) + desc;
+    return (long long)(h->nbins[0] + 2) * (slice_own_locator(h) ? 8 : 16) + desc;
   };
   // shared members: smallest first, up to half the budget
   std::vector<int> order(nh);
@@ -1094,7 +1101,7 @@ void slice_plan(hist_batch* b, int budget, double cap) {
     for (int i : mem) {
       const hist* h = b->hs[i];
       const long long nbt = h->nbins[0] + 2;
-      const long long per_bin = h->loc_mode[0] == LOC_AFFINE ? 8 : 16;
+      const long long per_bin = slice_own_locator(h) ? 8 : 16;
       long long a = 0;
       while (a < nbt) {
         if (!open) open_slice();
