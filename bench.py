@@ -218,7 +218,9 @@ def measure_forms(B, W, hbm: float, args) -> dict:
         for h in hists:
             h.fill(col, None)
     res["plain_default_ms"] = _timed(plain5, 2)
-    batch = B.Batch(hists, lw.col_of_hist, B.HIST_BATCH_GRAPH | B.HIST_BATCH_WIDE)
+    sample = [col[:8_000_000]]
+    batch = B.Batch(hists, lw.col_of_hist, B.HIST_BATCH_GRAPH)
+    res["fused_default_tuning"] = batch.tune(sample, None)
     res["fused_default_ms"] = _timed(lambda: batch.fill([col], None), 2)
     batch.close()
     for h in hists:
@@ -226,7 +228,8 @@ def measure_forms(B, W, hbm: float, args) -> dict:
     # binary search over the edges, then the learned locator on the same axes
     hists = [B.Hist([ax], B.HIST_LOCATOR_BSEARCH) for ax in lw.axes]
     res["plain_bsearch_ms"] = _timed(plain5, 2)
-    batch = B.Batch(hists, lw.col_of_hist, B.HIST_BATCH_GRAPH | B.HIST_BATCH_WIDE)
+    batch = B.Batch(hists, lw.col_of_hist, B.HIST_BATCH_GRAPH)
+    batch.tune(sample, None)
     res["fused_bsearch_ms"] = _timed(lambda: batch.fill([col], None), 2)
     batch.close()
     t0 = time.perf_counter()
@@ -234,7 +237,8 @@ def measure_forms(B, W, hbm: float, args) -> dict:
     res["train_s"] = time.perf_counter() - t0
     res["windows"] = [r["window"] for r in reports]
     res["plain_learned_ms"] = _timed(plain5, 2)
-    batch = B.Batch(hists, lw.col_of_hist, B.HIST_BATCH_GRAPH | B.HIST_BATCH_WIDE)
+    batch = B.Batch(hists, lw.col_of_hist, B.HIST_BATCH_GRAPH)
+    res["fused_learned_tuning"] = batch.tune(sample, None)
     res["fused_learned_ms"] = _timed(lambda: batch.fill([col], None), 2)
     batch.close()
     for h in hists:

@@ -208,27 +208,30 @@ typedef struct {
   int32_t slices;          /* sliced: slices of the chosen plan (0 for wide) */
   int32_t replicas;        /* sliced: blocks per slice */
   int32_t cost_cap_tenths; /* sliced: work cap per slice of the chosen plan, tenths of one histogram */
+  int32_t events_per_thread; /* events each thread holds per pass over the histograms */
 } hist_batch_tuning_t;
 
 /* Autotune the batch: time the candidate strategies, shared-memory budgets
- * (which histograms keep shared-memory bins; the slice size) and work caps
- * per slice, each with the occupancy it allows, on the given sample of
- * events, writing into scratch accumulators (the member histograms are not
+ * (which histograms keep shared-memory bins; the slice size), blocks per SM,
+ * events per thread and work caps per slice on the given sample of events, writing into scratch accumulators (the member histograms are not
  * changed), and keep the fastest for later fills.  Synchronous.  report may
  * be NULL.  Errors: as hist_batch_fill. */
 int hist_batch_tune(hist_batch_t *b, const double *const *cols, int ncols, const double *weights, int64_t n,
                     hist_batch_tuning_t *report);
 
 /* Pin the batch's configuration instead of tuning it: strategy 0 (wide) or
- * 1 (sliced), the shared-memory budget per block in bytes, and for the
- * sliced strategy the work cap per slice in tenths of one histogram's
+ * 1 (sliced), the shared-memory budget per block in bytes; for the sliced
+ * strategy the work cap per slice in tenths of one histogram's
  * locate-and-add and the pacing window in tiles of 2048 events (-1 the
- * default, 0 no pacing).  info (may be NULL) receives the resulting plan
- * (with best_ms = worst_ms = 0).  Waits for the batch's earlier fills.
- * Errors: HIST_ERR_ARG, HIST_ERR_UNSUPPORTED (the plan does not fit one
- * block's shared memory), HIST_ERR_OOM, HIST_ERR_CUDA. */
+ * default, 0 no pacing); for the wide strategy the blocks per SM the kernel
+ * is compiled for (2 or 4: its register budget) and the events each thread
+ * holds (2 or 4).  info (may be NULL) receives the resulting plan (with
+ * best_ms = worst_ms = 0).  Waits for the batch's earlier fills.  Errors:
+ * HIST_ERR_ARG, HIST_ERR_UNSUPPORTED (the plan does not fit one block's
+ * shared memory), HIST_ERR_OOM, HIST_ERR_CUDA. */
 int hist_batch_configure(hist_batch_t *b, int32_t strategy, int32_t smem_bytes, int32_t cost_cap_tenths,
-                         int32_t pace_tiles, hist_batch_tuning_t *info);
+                         int32_t pace_tiles, int32_t blocks_per_sm, int32_t events_per_thread,
+                         hist_batch_tuning_t *info);
 
 /* Release the batch (not its histograms).  NULL is a no-op. */
 void hist_batch_free(hist_batch_t *b);

@@ -67,7 +67,8 @@ class hist_batch_tuning_t(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("smem_hists", ctypes.c_int32),
                 ("best_ms", ctypes.c_double), ("worst_ms", ctypes.c_double),
                 ("strategy", ctypes.c_int32), ("slices", ctypes.c_int32),
-                ("replicas", ctypes.c_int32), ("cost_cap_tenths", ctypes.c_int32)]
+                ("replicas", ctypes.c_int32), ("cost_cap_tenths", ctypes.c_int32),
+                ("events_per_thread", ctypes.c_int32)]
 
 
 HIST_BATCH_GRAPH = 1 << 0
@@ -119,7 +120,7 @@ def load(path: str | None = None):
             "hist_locator_mode": (ctypes.c_int, [_P, ctypes.c_int]),
             "hist_kernel_time": (ctypes.c_int, [_P, _P, _P]),
             "hist_batch_configure": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                                    ctypes.c_int32, _P]),
+                                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]),
             "hist_batch_free": (None, [_P]),
             "hist_locator_loss_grad": (ctypes.c_int, [ctypes.c_int, ctypes.c_float, ctypes.c_float, _P, _P, _P,
                                                       _P, ctypes.c_int64, _P, _P]),
@@ -313,10 +314,11 @@ def hist_batch_tune(b: int, cols, weights, n: int) -> dict:
 
 
 def hist_batch_configure(b: int, strategy: int, smem_bytes: int, cost_cap_tenths: int = 30,
-                         pace_tiles: int = -1) -> dict:
+                         pace_tiles: int = -1, blocks_per_sm: int = 2, events_per_thread: int = 4) -> dict:
     r = hist_batch_tuning_t()
     _check(load().hist_batch_configure(b, int(strategy), int(smem_bytes), int(cost_cap_tenths), int(pace_tiles),
-                                       ctypes.byref(r)), "hist_batch_configure")
+                                       int(blocks_per_sm), int(events_per_thread), ctypes.byref(r)),
+           "hist_batch_configure")
     return {f: getattr(r, f) for f, _ in hist_batch_tuning_t._fields_}
 
 
@@ -360,8 +362,10 @@ class Batch:
     def tune(self, cols, weights=None) -> dict:
         return hist_batch_tune(self.b, list(cols), weights, int(cols[0].shape[-1]))
 
-    def configure(self, strategy: int, smem_bytes: int, cost_cap_tenths: int = 30, pace_tiles: int = -1) -> dict:
-        return hist_batch_configure(self.b, strategy, smem_bytes, cost_cap_tenths, pace_tiles)
+    def configure(self, strategy: int, smem_bytes: int, cost_cap_tenths: int = 30, pace_tiles: int = -1,
+                  blocks_per_sm: int = 2, events_per_thread: int = 4) -> dict:
+        return hist_batch_configure(self.b, strategy, smem_bytes, cost_cap_tenths, pace_tiles, blocks_per_sm,
+                                    events_per_thread)
 
     def close(self) -> None:
         if self.b:

@@ -7,8 +7,9 @@
 //  * histograms are sorted by column; the per-column work (the FP32 view of
 //    the coordinate, its range flags) and the per-event weight work (the
 //    exact fixed-point value) happen once per event, not once per histogram;
-//  * each thread holds kEv events in registers and walks the histograms
-//    outermost, so a histogram's descriptor is read once per kEv events;
+//  * each thread holds KEV events in registers and walks the histograms
+//    outermost, so a histogram's descriptor is read once per KEV events
+//    (KEV and the blocks per SM the launch is compiled for are tuned);
 //  * small histograms keep block-private bins in shared memory: the low 64
 //    bits of the exact fixed-point sum as two u32 words updated by
 //    carry-propagating atomics, the rare carry out of bit 63 going straight
@@ -33,7 +34,6 @@
 namespace hgb {
 namespace {
 
-constexpr int kEv = 4;  // events per thread per iteration
 
 template <bool UNIT, bool SMEM>
 __device__ __forceinline__ void batch_add(const BatchHistDev& d, unsigned* sbins, int k, long long V, bool wok,
@@ -71,8 +71,9 @@ __device__ __forceinline__ void batch_add(const BatchHistDev& d, unsigned* sbins
   }
 }
 
-template <bool UNIT>
-__global__ void __launch_bounds__(256, 2) k_batch_fill(const __grid_constant__ BatchParams p) {
+template <bool UNIT, int MINB, int KEV>
+__global__ void __launch_bounds__(256, MINB) k_batch_fill(const __grid_constant__ BatchParams p) {
+  constexpr int kEv = KEV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nkeys = p.table_keys;
   long long* skeys = reinterpret_cast<long long*>(smem_raw);
@@ -200,10 +201,28 @@ __global__ void k_batch_reduce(const BatchReduceParams r) {
 
 }  // namespace
 
-int batch_max_blocks_per_sm(int block, size_t smem, int* per_sm) {
-  const void* fn = reinterpret_cast<const void*>(&k_batch_fill<false>);
-  const void* fu = reinterpret_cast<const void*>(&k_batch_fill<true>);
-  if (smem > 48 * 1024) {
+// The compiled variants: blocks per SM the registers allow (2 or 4) times
+// events per thread (2 or 4).
+const void* batch_fn(bool unit, int minb, int kev) {
+#define HGB_BATCH(U, M, K) \
+  if (unit == U && minb == M && kev == K) return reinterpret_cast<const void*>(&k_batch_fill<U, M, K>);
+  HGB_BATCH(false, 2, 4)
+  HGB_BATCH(false, 2, 2)
+  HGB_BATCH(false, 4, 4)
+  HGB_BATCH(false, 4, 2)
+  HGB_BATCH(true, 2, 4)
+  HGB_BATCH(true, 2, 2)
+  HGB_BATCH(true, 4, 4)
+  HGB_BATCH(true, 4, 2)
+#undef HGB_BATCH
+  return nullptr;
+}
+
+int batch_max_blocks_per_sm(int block, size_t smem, int minb, int kev, int* per_sm) {
+  const void* fn = batch_fn(false, minb, kev);
+  const void* fu = batch_fn(true, minb, kev);
+  if (fn == nullptr || fu == nullptr) return -1;
+  {  // always: it also loads the kernel before the occupancy query
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;
     if (cudaFuncSetAttribute(fu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;
   }
@@ -214,10 +233,10 @@ int batch_max_blocks_per_sm(int block, size_t smem, int* per_sm) {
   return 0;
 }
 
-int launch_batch_fill(const BatchParams& p, int block, int grid, size_t smem, void* stream) {
-  const void* fn = (p.w == nullptr) ? reinterpret_cast<const void*>(&k_batch_fill<true>)
-                                    : reinterpret_cast<const void*>(&k_batch_fill<false>);
-  if (smem > 48 * 1024) {
+int launch_batch_fill(const BatchParams& p, int block, int grid, size_t smem, int minb, int kev, void* stream) {
+  const void* fn = batch_fn(p.w == nullptr, minb, kev);
+  if (fn == nullptr) return -1;
+  {  // always: it also loads the kernel before the occupancy query
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;
   }
   void* args[] = {const_cast<BatchParams*>(&p)};

@@ -291,7 +291,7 @@ int slice_max_blocks_per_sm(int block, size_t smem, int* per_sm) {
   const void* fn = reinterpret_cast<const void*>(&k_slice_fill<false>);
   const void* fu = reinterpret_cast<const void*>(&k_slice_fill<true>);
   if (block != kSliceThreads) return -1;
-  if (smem > 48 * 1024) {
+  {  // always: it also loads the kernel before the occupancy query
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;
     if (cudaFuncSetAttribute(fu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;
   }
@@ -306,7 +306,7 @@ int launch_slice_fill(const SliceParams& p, int block, int grid, size_t smem, vo
   if (block != kSliceThreads || p.tile != kSliceThreads * kSliceEv) return -1;
   const void* fn = (p.w == nullptr) ? reinterpret_cast<const void*>(&k_slice_fill<true>)
                                     : reinterpret_cast<const void*>(&k_slice_fill<false>);
-  if (smem > 48 * 1024) {
+  {  // always: it also loads the kernel before the occupancy query
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;
   }
   void* args[] = {const_cast<SliceParams*>(&p)};

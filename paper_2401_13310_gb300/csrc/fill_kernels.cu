@@ -585,7 +585,7 @@ int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shap
   const int block = 256;
   size_t smem = (((size_t)p.table_keys * 12 + 15) & ~(size_t)15) + (((size_t)p.table_bk * 4 + 15) & ~(size_t)15);
   if (p.smem_bins) smem += (size_t)p.nbins_total * smem_bin_bytes(acc_mode, p.track_counts);
-  if (smem > 48 * 1024) {
+  {  // always: it also loads the kernel before the occupancy query
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;
   }
   int per_sm = 0;

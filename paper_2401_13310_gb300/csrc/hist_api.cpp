@@ -863,6 +863,7 @@ struct hist_batch {
   int shared_col_begin[kBatchMaxCols + 1] = {};
   int slice_replicas = 1, slice_window = 0;
   int pace_tiles = -1;                    // pacing window in tiles: -1 default, 0 off
+  int wide_minb = 2, wide_kev = 4;        // wide: blocks per SM compiled for, events per thread
   double slice_cap = 0.0;
   SliceDev* d_slices = nullptr;
   SliceFragDev* d_frags = nullptr;
@@ -1266,7 +1267,8 @@ int batch_configure(hist_batch* b, int budget) {
   batch_place(b, budget);
   b->smem = batch_smem_bytes(b);
   int per_sm = 0;
-  if (batch_max_blocks_per_sm(256, b->smem, &per_sm) != 0 || per_sm < 1) return HIST_ERR_CUDA;
+  if (batch_max_blocks_per_sm(256, b->smem, b->wide_minb, b->wide_kev, &per_sm) != 0 || per_sm < 1)
+    return HIST_ERR_CUDA;
   b->grid = per_sm * b->sm_count;
   b->strategy = 0;
   int rc = batch_part_stats(b);
@@ -1357,7 +1359,7 @@ int batch_launch(const hist_batch* b, const double* const* cols, const double* w
     if (launch_slice_fill(p, kSliceBlock, b->grid, b->smem, s) != 0) return HIST_ERR_CUDA;
   } else {
     const BatchParams p = batch_params(b, cols, weights, n, tune);
-    if (launch_batch_fill(p, 256, b->grid, b->smem, s) != 0) return HIST_ERR_CUDA;
+    if (launch_batch_fill(p, 256, b->grid, b->smem, b->wide_minb, b->wide_kev, s) != 0) return HIST_ERR_CUDA;
   }
   BatchReduceParams r;
   std::memset(&r, 0, sizeof(r));
@@ -1597,7 +1599,7 @@ void batch_report(const hist_batch* b, hist_batch_tuning_t* r) {
   r->smem_bytes = b->smem_budget;
   int per_sm = 0;
   if (b->strategy == 0)
-    batch_max_blocks_per_sm(256, b->smem, &per_sm);
+    batch_max_blocks_per_sm(256, b->smem, b->wide_minb, b->wide_kev, &per_sm);
   else
     slice_max_blocks_per_sm(kSliceBlock, b->smem, &per_sm);
   r->blocks_per_sm = per_sm;
@@ -1611,6 +1613,7 @@ void batch_report(const hist_batch* b, hist_batch_tuning_t* r) {
   r->slices = b->strategy == 1 ? (int)b->slices.size() : 0;
   r->replicas = b->strategy == 1 ? b->slice_replicas : 0;
   r->cost_cap_tenths = b->strategy == 1 ? (int)(10.0 * b->slice_cap + 0.5) : 0;
+  r->events_per_thread = b->strategy == 0 ? b->wide_kev : 4;
 }
 }  // namespace
 
@@ -1628,28 +1631,35 @@ extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int n
   struct Cand {
     int strategy, budget;
     double cap;
+    int minb, kev;
   };
   std::vector<Cand> cands;
   if (!(b->flags & HIST_BATCH_SLICED))
-    for (int kb : {16, 48, 96, 144, 200}) cands.push_back({0, kb * 1024, 0.0});
+    for (int kb : {16, 48, 96, 144, 200})
+      for (int minb : {2, 4})
+        for (int kev : {4, 2}) cands.push_back({0, kb * 1024, 0.0, minb, kev});
   if (!(b->flags & HIST_BATCH_WIDE))
-    for (int kb : {48, 96, 200})
-      for (double cap : {1.5, 3.0, 6.0}) cands.push_back({1, kb * 1024, cap});
+    for (int kb : {96, 200})
+      for (double cap : {3.0, 12.0}) cands.push_back({1, kb * 1024, cap, 2, 4});
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HIST_ERR_CUDA;
   double best = 1e300, worst = 0.0;
   Cand best_c = cands.front();
-  int tried = 0, last_wide = -1;
+  int tried = 0;
+  std::vector<long long> seen;
   for (const Cand& c : cands) {
+    b->wide_minb = c.minb;
+    b->wide_kev = c.kev;
     rc = c.strategy == 0 ? batch_configure(b, c.budget) : slice_configure(b, c.budget, c.cap);
     if (rc == HIST_ERR_UNSUPPORTED) {
       rc = HIST_OK;
       continue;
     }
     if (rc != HIST_OK) break;
-    if (c.strategy == 0) {  // budgets clamp to the same placement: time it once
-      if (b->smem_budget == last_wide) continue;
-      last_wide = b->smem_budget;
+    if (c.strategy == 0) {  // budgets clamp to the same placement: time each variant once
+      const long long sig = ((long long)b->smem_budget << 8) | (c.minb << 4) | c.kev;
+      if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+      seen.push_back(sig);
     }
     if ((rc = batch_reserve(b, n)) != HIST_OK) break;
     if ((rc = batch_launch(b, cols, weights, n, true, nullptr)) != HIST_OK) break;  // warm-up
@@ -1675,6 +1685,8 @@ extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int n
   cudaEventDestroy(e1);
   if (cudaDeviceSynchronize() != cudaSuccess) return HIST_ERR_CUDA;
   if (rc != HIST_OK) return rc;
+  b->wide_minb = best_c.minb;
+  b->wide_kev = best_c.kev;
   rc = best_c.strategy == 0 ? batch_configure(b, best_c.budget) : slice_configure(b, best_c.budget, best_c.cap);
   if (rc != HIST_OK) return rc;
   if (report) {
@@ -1687,11 +1699,15 @@ extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int n
 }
 
 extern "C" int hist_batch_configure(hist_batch_t* b, int32_t strategy, int32_t smem_bytes, int32_t cost_cap_tenths,
-                                    int32_t pace_tiles, hist_batch_tuning_t* info) {
+                                    int32_t pace_tiles, int32_t blocks_per_sm, int32_t events_per_thread,
+                                    hist_batch_tuning_t* info) {
   if (b == nullptr || (strategy != 0 && strategy != 1) || smem_bytes < 1024 ||
-      (strategy == 1 && cost_cap_tenths < 10) || pace_tiles < -1)
+      (strategy == 1 && cost_cap_tenths < 10) || pace_tiles < -1 || (blocks_per_sm != 2 && blocks_per_sm != 4) ||
+      (events_per_thread != 2 && events_per_thread != 4))
     return HIST_ERR_ARG;
   b->pace_tiles = pace_tiles;
+  b->wide_minb = blocks_per_sm;
+  b->wide_kev = events_per_thread;
   if (cudaSetDevice(b->device) != cudaSuccess) return HIST_ERR_CUDA;
   if (b->have_done && cudaEventSynchronize(b->done) != cudaSuccess) return HIST_ERR_CUDA;
   const int rc = strategy == 0 ? batch_configure(b, smem_bytes) : slice_configure(b, smem_bytes, 0.1 * cost_cap_tenths);

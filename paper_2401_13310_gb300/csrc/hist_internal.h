@@ -236,8 +236,8 @@ int launch_slice_fill(const SliceParams& p, int block, int grid, size_t smem, vo
 int slice_max_blocks_per_sm(int block, size_t smem, int* per_sm);
 size_t slice_smem_bytes(int keys, int words, int frags);
 
-int launch_batch_fill(const BatchParams& p, int block, int grid, size_t smem, void* stream);
-int batch_max_blocks_per_sm(int block, size_t smem, int* per_sm);
+int launch_batch_fill(const BatchParams& p, int block, int grid, size_t smem, int minb, int kev, void* stream);
+int batch_max_blocks_per_sm(int block, size_t smem, int minb, int kev, int* per_sm);
 int launch_batch_reduce(const BatchReduceParams& r, void* stream);
 
 // Launchers (fill_kernels.cu).

@@ -164,3 +164,34 @@ def test_batch_unit_weights_many_edges_tuned(B):
             batch.close()
         for h in hists:
             h.close()
+
+
+def test_batch_configurations_agree_exactly(B):
+    """Pinned configurations (wide at two register budgets and events per
+    thread, sliced at two slice sizes): the exact fixed-point bins are
+    bit-identical whatever the configuration; statistics within tolerance."""
+    bw = W.cfg4(n=150_001)
+    cols = [to_device(np.ascontiguousarray(bw.columns[c])) for c in range(3)]
+    w = to_device(bw.weights)
+    configs = [(0, 48 << 10, 30, -1, 2, 4), (0, 96 << 10, 30, -1, 4, 2), (1, 96 << 10, 30, -1, 2, 4),
+               (1, 200 << 10, 120, 0, 2, 4)]
+    results = []
+    for cfg in configs:
+        hists = [B.Hist([ax]) for ax in bw.axes]
+        batch = None
+        try:
+            batch = B.Batch(hists, bw.col_of_hist)
+            info = batch.configure(*cfg)
+            assert info["strategy"] == cfg[0]
+            batch.fill(cols, w)
+            results.append([h.result() for h in hists])
+        finally:
+            if batch is not None:
+                batch.close()
+            for h in hists:
+                h.close()
+    for r in results[1:]:
+        for i, ((b0, s0), (b1, s1)) in enumerate(zip(results[0], r)):
+            assert np.array_equal(b0, b1), f"hist {i} bins differ between configurations"
+            ref = oracle.fill([bw.axes[i]], bw.columns[bw.col_of_hist[i]].reshape(1, -1), bw.weights)
+            assert_sums_close(s1[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, f"hist {i} stats")
