@@ -168,10 +168,38 @@ def _timed(fn, reps: int) -> float:
     return e0.elapsed_time(e1) / reps
 
 
+def measure_precisions(B, W, hbm: float, n: int) -> dict:
+    """The bench workload's two fills in each precision mode (fill kernel
+    alone, library event pairs), same GPU."""
+    import torch
+    out = {}
+    wa = W.cfg2a(n=n, device="cuda")
+    wb = W.cfg2b(n=n, device="cuda")
+    for name, flag in (("fixed_point", B.HIST_PREC_FP64), ("fp32_compensated", B.HIST_PREC_FP32C),
+                       ("f64_atomic", B.HIST_PREC_F64ATOMIC)):
+        res = {}
+        for tag, wl in (("a_fixed1000", wa), ("b_var500", wb)):
+            h = B.Hist(wl.axes, flag)
+            for _ in range(3):
+                h.fill(wl.values, wl.weights)
+            torch.cuda.synchronize()
+            B.hist_set_kernel_timing(h.h, True)
+            for _ in range(20):
+                h.fill(wl.values, wl.weights)
+            ms, k = B.hist_kernel_time(h.h)
+            h.close()
+            res[tag + "_ms"] = ms / k
+            res[tag + "_hbm_frac"] = BYTES_PER_EVENT * n / (ms / k * 1e-3) / 1e9 / hbm
+        out[name] = res
+    del wa, wb
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_forms(B, W, hbm: float, args) -> dict:
     """The batched and learned forms beside the plain one, same GPU."""
     import torch
-    out = {}
+    out = {"precision": measure_precisions(B, W, hbm, args.events)}
     # batched: 64 histograms (10 .. 1e5 bins, fixed and variable) on the
     # columns pT, phi, eta with binary64 weights
     n4 = args.batch_events

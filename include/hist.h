@@ -80,8 +80,18 @@ typedef struct {
  *                    weight with |w| in [2^-8, 2^8); other weights are added
  *                    in binary64); per-bin error <= 2.3e-13 * sum |w|;
  *                    bit-reproducible for in-window weights.
- *   HIST_PREC_FP32C  FP32 compensated (hi, lo) partials per block, flushed
- *                    to binary64; per-bin error bound stated in the docs.
+ *   HIST_PREC_FP32C  FP32 compensated partials: each weight split into FP32
+ *                    hi + lo (|w - hi - lo| <= 2^-48 |w|); hi added to the
+ *                    block's FP32 bin by an atomic whose rounding error is
+ *                    recovered exactly (TwoSum on the returned old value) and
+ *                    added with lo to an FP32 compensation word; blocks
+ *                    flushed and summed in binary64.  Per bin, with m_b the
+ *                    bin's entries in block b and A = sum |w|:
+ *                      |err| <= 2^-48 ((max_b m_b + 1)^2 + 1) A + B 2^-53 A
+ *                    (B blocks); the compensation words' rounding errors
+ *                    are random in sign, so measured errors stay far below.
+ *                    Weights outside [2^-40, 2^40), and histograms whose bins
+ *                    outgrow shared memory, use binary64 atomics.
  *   HIST_PREC_F64ATOMIC  binary64 atomic adds (order-dependent rounding). */
 #define HIST_PREC_FP64 (0u << 4)
 #define HIST_PREC_FP32C (1u << 4)

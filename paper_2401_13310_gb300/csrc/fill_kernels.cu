@@ -274,6 +274,29 @@ struct Filler {
         else
           atomicAdd(&p.g_count[g], 1ull);
       }
+    } else if (ACC == ACC_F32C) {
+      // FP32 compensated partials: the weight as hi + lo (FP32 double-word);
+      // hi goes to the block's FP32 bin by an atomic that returns the old
+      // value, so the rounding error of that addition is recovered exactly
+      // (TwoSum) and added, with lo, to the bin's FP32 compensation word
+      w_ok = in_ff(exp_field(wb));
+      if (!w_ok || !SMEM) {
+        slow_bin(p.g_f64, g, wb);  // outside the double-word range, or bins in global memory
+      } else {
+        const FF W = ff_split(wb, hi24(wb));
+        float* a = reinterpret_cast<float*>(&sbins[2 * g]);
+        const float old = atomicAdd(a, W.hi);
+        const float sum = __fadd_rn(old, W.hi);
+        const float bv = __fsub_rn(sum, old);
+        const float err = __fadd_rn(__fsub_rn(old, __fsub_rn(sum, bv)), __fsub_rn(W.hi, bv));
+        atomicAdd(a + 1, __fadd_rn(err, W.lo));
+      }
+      if (p.track_counts) {
+        if (SMEM)
+          atomicAdd(&sbins[2 * (int)p.nbins_total + g], 1u);
+        else
+          atomicAdd(&p.g_count[g], 1ull);
+      }
     } else {  // ACC_F64: the paper's binary64 atomics
       if (SMEM) {
         f64_bin(sbins_f64, 2 * g, wb);
@@ -404,7 +427,7 @@ __global__ void __launch_bounds__(256, NDIM == 1 ? HGB_MIN_BLOCKS_1D : HGB_MIN_B
   }
   const int nb = (int)p.nbins_total;
   if (SMEM) {
-    const int words = (UNIT ? 1 : (ACC == ACC_FX ? (p.track_counts ? 3 : 2) : 4)) * nb;
+    const int words = (UNIT ? 1 : ((ACC == ACC_FX || ACC == ACC_F32C) ? (p.track_counts ? 3 : 2) : 4)) * nb;
     for (int i = threadIdx.x; i < words; i += blockDim.x) f.sbins[i] = 0u;
   }
   f.stride1 = p.ax[0].nbins + 2;
@@ -446,6 +469,13 @@ __global__ void __launch_bounds__(256, NDIM == 1 ? HGB_MIN_BLOCKS_1D : HGB_MIN_B
         // {low word, next word, top word (kept in global), entries}
         for (int i = threadIdx.x; i < nb; i += blockDim.x)
           out[i] = make_uint4(f.sbins[2 * i], f.sbins[2 * i + 1], 0u, p.track_counts ? f.sbins[2 * nb + i] : 0u);
+      } else if (ACC == ACC_F32C) {
+        // {hi + lo in binary64, entries}: the reduction sums blocks in binary64
+        double2* out2 = reinterpret_cast<double2*>(p.part_bins) + (size_t)blockIdx.x * nb;
+        const float* sf = reinterpret_cast<const float*>(f.sbins);
+        for (int i = threadIdx.x; i < nb; i += blockDim.x)
+          out2[i] = make_double2(__dadd_rn((double)sf[2 * i], (double)sf[2 * i + 1]),
+                                 p.track_counts ? (double)f.sbins[2 * nb + i] : 0.0);
       } else {
         const uint4* sb4 = reinterpret_cast<const uint4*>(f.sbins);
         for (int i = threadIdx.x; i < nb; i += blockDim.x) out[i] = sb4[i];
@@ -559,12 +589,15 @@ const void* pick_fill(int ndim, int acc, bool smem, int loc) {
   HGB_PICK(1, ACC_UNIT)
   HGB_PICK(1, ACC_FX)
   HGB_PICK(1, ACC_F64)
+  HGB_PICK(1, ACC_F32C)
   HGB_PICK(2, ACC_UNIT)
   HGB_PICK(2, ACC_FX)
   HGB_PICK(2, ACC_F64)
+  HGB_PICK(2, ACC_F32C)
   HGB_PICK(3, ACC_UNIT)
   HGB_PICK(3, ACC_FX)
   HGB_PICK(3, ACC_F64)
+  HGB_PICK(3, ACC_F32C)
 #undef HGB_PICK
   return nullptr;
 }
@@ -575,7 +608,7 @@ size_t part_bin_bytes(int acc_mode, int /*track_counts*/) { return acc_mode == A
 
 size_t smem_bin_bytes(int acc_mode, int track_counts) {
   if (acc_mode == ACC_UNIT) return 4;
-  if (acc_mode == ACC_FX) return track_counts ? 12 : 8;
+  if (acc_mode == ACC_FX || acc_mode == ACC_F32C) return track_counts ? 12 : 8;
   return 16;
 }
 

@@ -215,7 +215,6 @@ int order_after_previous(hist* h, cudaStream_t s) {
 
 int fill_impl(hist* h, const double* values, const double* weights, int64_t n, cudaStream_t stream) {
   const int acc = (weights == nullptr) ? ACC_UNIT : acc_mode_of(h->flags, false);
-  if (acc == ACC_F32C) return HIST_ERR_UNSUPPORTED;
   if (cudaSetDevice(h->device) != cudaSuccess) return HIST_ERR_CUDA;
   int rc = order_after_previous(h, stream);
   if (rc != HIST_OK) return rc;

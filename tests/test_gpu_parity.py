@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from paper_2401_13310_gb300 import workloads as W
-from tests.helpers import check_against_oracle, edge_probe_values, gpu_fill, to_device
+from tests.helpers import assert_sums_close, check_against_oracle, edge_probe_values, gpu_fill, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -262,3 +262,27 @@ def test_zero_and_tiny_coordinates(B, weighted):
     ref = oracle.fill(axes, x.reshape(1, -1), w)
     bins, stats, counts = gpu_fill(axes, x, w, flags=B.HIST_TRACK_COUNTS)
     check_against_oracle(axes, x, w, bins, stats, counts, ref, RTOL, RTOL, what=f"zeros weighted={weighted}")
+
+
+@pytest.mark.parametrize("name,n", [("2a", 2_000_003), ("2b", 2_000_003), ("3b", 1_000_001), ("1", 1 << 20)])
+def test_fp32c_within_stated_bound(B, name, n):
+    """HIST_PREC_FP32C (FP32 compensated shared-memory partials): counts
+    exact, every bin within the stated bound
+        |err| <= 2^-48 ((m + 1)^2 + 1) A + B 2^-53 A
+    (m <= the bin's entries, A = sum |w| of the bin, B <= 1216 blocks), the
+    statistics (double-word path) within 1e-12 of sum |term|."""
+    wl = W.CONFIGS[name](n=n)
+    w = wl.weights if wl.weights is not None else np.random.default_rng(3).uniform(0.5, 1.5, n)
+    flags = B.HIST_TRACK_COUNTS | B.HIST_PREC_FP32C
+    ref = oracle.fill(wl.axes, wl.values, w, threads=4)
+    bins, stats, counts = gpu_fill(wl.axes, wl.values, w, flags=flags)
+    assert np.array_equal(counts, ref.counts)
+    m = ref.counts.astype(np.float64)
+    A = ref.bins_abs
+    bound = 2.0 ** -48 * ((m + 1.0) ** 2 + 1.0) * A + 1216 * 2.0 ** -53 * A
+    err = np.abs(bins - ref.bins_acc)
+    assert np.all(err <= bound), f"cfg{name}: worst bin error / bound {np.max(err / np.maximum(bound, 1e-300)):.3g}"
+    rel = np.max(err / np.maximum(A, 1e-300))
+    print(f"cfg{name} FP32C: max |err| / sum|w| per bin = {rel:.3g}")
+    assert stats[0] == ref.stats_acc[0]
+    assert_sums_close(stats[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, f"cfg{name} FP32C stats")
