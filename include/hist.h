@@ -148,6 +148,20 @@ int hist_result(hist_t *h, double *bins, double *stats);
  * HIST_ERR_STATE). */
 int hist_counts(hist_t *h, uint64_t *counts);
 
+/* Fill from HOST memory, pipelined (Sec. 3.2 transfers bulks of events to
+ * the GPU; Sec. 6 names pipelining the bulks as future work): values host
+ * column-major [ndim][n], weights host [n] or NULL.  The events are cut into
+ * bulks of `bulk` events (0: 2^22); bulk i is copied into one of two
+ * library-owned device slots on one of the histogram's two copy streams while the
+ * fill of bulk i-1 runs on `stream`, and filled from the slot on `stream`.
+ * Pinned host memory makes the copies asynchronous (pageable memory works,
+ * with the driver's staging).  Asynchronous: the caller keeps the host
+ * buffers alive and unmodified until `stream` has passed the call.  Results
+ * are those of hist_fill_bulk over the same events.  Errors: HIST_ERR_ARG,
+ * HIST_ERR_OOM, HIST_ERR_CUDA. */
+int hist_fill_host(hist_t *h, const double *values, const double *weights, int64_t n, int64_t bulk,
+                   hist_stream_t stream);
+
 /* Per-event linear bin index of a bulk (step 1 of Sec. 3.1 alone).
  * values as in hist_fill_bulk; out: device int64 [n].  Asynchronous on
  * `stream`.  Does not change the histogram. */

@@ -117,6 +117,7 @@ def load(path: str | None = None):
             "hist_batch_fill": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
             "hist_batch_tune": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
             "hist_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+            "hist_fill_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P]),
             "hist_locator_mode": (ctypes.c_int, [_P, ctypes.c_int]),
             "hist_kernel_time": (ctypes.c_int, [_P, _P, _P]),
             "hist_batch_configure": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -332,6 +333,23 @@ def hist_locator_mode(h: int, axis: int = 0) -> str:
     return LOCATOR_MODES[m]
 
 
+def hist_fill_host(h: int, values, weights, n: int, bulk: int = 0, stream=None) -> None:
+    """Pipelined fill from host memory: ``values`` and ``weights`` are CPU
+    tensors (pinned for asynchronous copies) or numpy arrays, float64,
+    contiguous; the caller keeps them alive until the stream passes."""
+    def host_ptr(a):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            assert not a.is_cuda and a.is_contiguous()
+            return a.data_ptr()
+        import numpy as np
+        assert isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"] and a.dtype == np.float64
+        return a.ctypes.data
+    _check(load().hist_fill_host(h, host_ptr(values), host_ptr(weights), int(n), int(bulk), _stream_ptr(stream)),
+           "hist_fill_host")
+
+
 def hist_set_kernel_timing(h: int, on: bool) -> None:
     _check(load().hist_set_kernel_timing(h, int(bool(on))), "hist_set_kernel_timing")
 
@@ -401,6 +419,10 @@ class Hist:
         if weights is not None:
             assert weights.shape == (n,) and weights.is_contiguous()
         hist_fill_bulk(self.h, values, weights, n, stream)
+
+    def fill_host(self, values, weights=None, bulk: int = 0, stream=None) -> None:
+        n = int(values.shape[-1])
+        hist_fill_host(self.h, values, weights, n, bulk, stream)
 
     def locate(self, values, out=None, stream=None):
         import torch

@@ -31,6 +31,9 @@ namespace {
 constexpr int kDefaultFxElo = 1015;             // |w| in [2^-8, 2^8) summed exactly
 constexpr size_t kSmemTableBudget = 64 * 1024;  // threshold keys staged per block
 constexpr size_t kSmemBucketBudget = 32 * 1024; // bucket counts staged per block
+constexpr int64_t kDefaultHostBulk = 1 << 22;    // events per staged bulk of hist_fill_host
+constexpr int64_t kHostGraphBulk = 1 << 20;      // bulks up to this size replay as one graph
+constexpr int64_t kHostGraphBulks = 4096;        // ... when there are at most this many
 constexpr int kBucketMax = 1 << 22;             // buckets of one axis at most
 constexpr int kBucketMaxRun = 16;               // most thresholds in one bucket for LOC_BUCKET
 #ifndef HGB_SMEM_BINS_BUDGET
@@ -87,6 +90,21 @@ struct hist {
   // ordering of fills issued on different streams
   cudaEvent_t done = nullptr;
   bool have_done = false;
+  // host-bulk pipeline (hist_fill_host): two device staging slots
+  double* d_stage[2] = {nullptr, nullptr};
+  int64_t stage_events = 0;  // events per slot
+  cudaStream_t copy_stream[2] = {nullptr, nullptr};  // one per slot: two copies in flight
+  cudaEvent_t copied[2] = {nullptr, nullptr};
+  cudaEvent_t consumed[2] = {nullptr, nullptr};
+  bool slot_used[2] = {false, false};
+  cudaEvent_t fork_ev = nullptr;
+  bool capturing = false;   // inside a graph capture: no waits on events recorded outside it
+  // graph of a whole pipelined fill, replayed while its arguments repeat
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t host_exec = nullptr;
+  const double* g_values = nullptr;
+  const double* g_weights = nullptr;
+  int64_t g_n = -1, g_bulk = -1;
   // optional timing of the fill kernel alone (pairs of events around it)
   bool timing = false;
   std::vector<cudaEvent_t> t_ev;
@@ -110,6 +128,19 @@ int dalloc(T** p, size_t bytes) {
 }
 
 void free_state(hist* h) {
+  for (int i = 0; i < 2; ++i)
+    if (h->copy_stream[i]) cudaStreamSynchronize(h->copy_stream[i]);
+  for (int i = 0; i < 2; ++i) {
+    if (h->consumed[i]) cudaEventSynchronize(h->consumed[i]);
+    if (h->copied[i]) cudaEventDestroy(h->copied[i]);
+    if (h->consumed[i]) cudaEventDestroy(h->consumed[i]);
+    cudaFree(h->d_stage[i]);
+  }
+  for (int i = 0; i < 2; ++i)
+    if (h->copy_stream[i]) cudaStreamDestroy(h->copy_stream[i]);
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+  if (h->host_exec) cudaGraphExecDestroy(h->host_exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->done) cudaEventDestroy(h->done);
   for (cudaEvent_t e : h->t_ev) cudaEventDestroy(e);
   cudaFree(h->d_T);
@@ -207,7 +238,7 @@ int ensure_scratch(hist* h, int grid, int acc, bool smem_bins) {
 
 // Order this call after the previous fill when it used another stream.
 int order_after_previous(hist* h, cudaStream_t s) {
-  if (h->have_done) {
+  if (h->have_done && !h->capturing) {
     if (cudaStreamWaitEvent(s, h->done, 0) != cudaSuccess) return HIST_ERR_CUDA;
   }
   return HIST_OK;
@@ -226,7 +257,7 @@ int fill_impl(hist* h, const double* values, const double* weights, int64_t n, c
   p.part_bins = h->part_bins;
   p.part_stats = h->part_stats;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
-  if (h->timing) {
+  if (h->timing && !h->capturing) {
     while (h->t_ev.size() < 2 * (h->t_used + 1)) {
       cudaEvent_t e;
       if (cudaEventCreate(&e) != cudaSuccess) return HIST_ERR_CUDA;
@@ -237,7 +268,7 @@ int fill_impl(hist* h, const double* values, const double* weights, int64_t n, c
     if (cudaEventRecord(t0, stream) != cudaSuccess) return HIST_ERR_CUDA;
   }
   if (launch_fill(p, acc, shape, stream) != 0) return HIST_ERR_CUDA;
-  if (h->timing) {
+  if (h->timing && !h->capturing) {
     if (cudaEventRecord(t1, stream) != cudaSuccess) return HIST_ERR_CUDA;
     ++h->t_used;
   }
@@ -264,10 +295,92 @@ int fill_impl(hist* h, const double* values, const double* weights, int64_t n, c
       h->fx_global_since_norm = 0;
     }
   }
-  if (cudaEventRecord(h->done, stream) != cudaSuccess) return HIST_ERR_CUDA;
+  // (inside a capture the graph's launch records completion instead)
+  if (!h->capturing && cudaEventRecord(h->done, stream) != cudaSuccess) return HIST_ERR_CUDA;
   h->have_done = true;
   h->n_entries += n;
   if (acc != ACC_UNIT && !(h->flags & HIST_TRACK_COUNTS)) h->counts_complete = false;
+  return HIST_OK;
+}
+
+// Staging slots, streams and events of the host pipeline, and the fill
+// scratch for its bulk sizes (nothing is allocated while it is enqueued,
+// which may be inside a graph capture).
+int pipeline_prepare(hist* h, int64_t n, int64_t bulk, bool weighted) {
+  if (h->copy_stream[0] == nullptr) {
+    for (int i = 0; i < 2; ++i)
+      if (cudaStreamCreateWithFlags(&h->copy_stream[i], cudaStreamNonBlocking) != cudaSuccess) return HIST_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess) return HIST_ERR_CUDA;
+    for (int i = 0; i < 2; ++i)
+      if (cudaEventCreateWithFlags(&h->copied[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->consumed[i], cudaEventDisableTiming) != cudaSuccess)
+        return HIST_ERR_CUDA;
+  }
+  if (bulk > h->stage_events) {  // grow the slots (after their last use)
+    if (h->have_done && cudaEventSynchronize(h->done) != cudaSuccess) return HIST_ERR_CUDA;
+    for (int i = 0; i < 2; ++i)
+      if (cudaStreamSynchronize(h->copy_stream[i]) != cudaSuccess) return HIST_ERR_CUDA;
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(h->d_stage[i]);
+      h->d_stage[i] = nullptr;
+      h->slot_used[i] = false;
+    }
+    h->stage_events = 0;
+    if (h->host_exec) {
+      cudaGraphExecDestroy(h->host_exec);
+      h->host_exec = nullptr;
+    }
+    for (int i = 0; i < 2; ++i) {
+      const int rc = dalloc(&h->d_stage[i], (size_t)bulk * (size_t)(h->ndim + 1) * sizeof(double));
+      if (rc != HIST_OK) return rc;
+    }
+    h->stage_events = bulk;
+  }
+  const int acc = weighted ? h->acc_mode : ACC_UNIT;
+  for (int64_t m : {bulk, n % bulk}) {
+    if (m == 0) continue;
+    FillParams p = make_params(h, h->d_stage[0], weighted ? h->d_stage[0] : nullptr, m, acc);
+    LaunchShape shape;
+    if (plan_fill(p, acc, h->sm_count, &shape) != 0) return HIST_ERR_CUDA;
+    const int rc = ensure_scratch(h, shape.grid, acc, p.smem_bins != 0);
+    if (rc != HIST_OK) return rc;
+  }
+  return HIST_OK;
+}
+
+// Bulk i: copied into slot i % 2 on the copy stream once the fill that last
+// read the slot is done, then filled from it on stream s.
+int pipeline_enqueue(hist* h, const double* values, const double* weights, int64_t n, int64_t bulk,
+                     cudaStream_t s) {
+  if (cudaEventRecord(h->fork_ev, s) != cudaSuccess) return HIST_ERR_CUDA;  // after s's earlier work
+  for (int i = 0; i < 2; ++i)
+    if (cudaStreamWaitEvent(h->copy_stream[i], h->fork_ev, 0) != cudaSuccess) return HIST_ERR_CUDA;
+  for (int64_t off = 0, i = 0; off < n; off += bulk, ++i) {
+    const int slot = (int)(i & 1);
+    const int64_t m = std::min<int64_t>(bulk, n - off);
+    double* dst = h->d_stage[slot];
+    cudaStream_t cs = h->copy_stream[slot];
+    if (i >= 2 && cudaStreamWaitEvent(cs, h->consumed[slot], 0) != cudaSuccess) return HIST_ERR_CUDA;
+    for (int d = 0; d < h->ndim; ++d)
+      if (cudaMemcpyAsync(dst + (size_t)d * m, values + (size_t)d * n + off, (size_t)m * sizeof(double),
+                          cudaMemcpyHostToDevice, cs) != cudaSuccess)
+        return HIST_ERR_CUDA;
+    if (weights != nullptr &&
+        cudaMemcpyAsync(dst + (size_t)h->ndim * m, weights + off, (size_t)m * sizeof(double), cudaMemcpyHostToDevice,
+                        cs) != cudaSuccess)
+      return HIST_ERR_CUDA;
+    if (cudaEventRecord(h->copied[slot], cs) != cudaSuccess) return HIST_ERR_CUDA;
+    if (cudaStreamWaitEvent(s, h->copied[slot], 0) != cudaSuccess) return HIST_ERR_CUDA;
+    const int rc = fill_impl(h, dst, weights != nullptr ? dst + (size_t)h->ndim * m : nullptr, m, s);
+    if (rc != HIST_OK) return rc;
+    if (cudaEventRecord(h->consumed[slot], s) != cudaSuccess) return HIST_ERR_CUDA;
+    h->slot_used[slot] = true;
+  }
+  // join both copy streams back into s (a capture must end joined)
+  for (int i = 0; i < 2; ++i)
+    if (cudaEventRecord(h->copied[i], h->copy_stream[i]) != cudaSuccess ||
+        cudaStreamWaitEvent(s, h->copied[i], 0) != cudaSuccess)
+      return HIST_ERR_CUDA;
   return HIST_OK;
 }
 
@@ -527,6 +640,72 @@ int hist_fill_bulk(hist_t* h, const double* values, const double* weights, int64
   if (values == nullptr) return HIST_ERR_ARG;
   if (!aligned8(values) || (weights != nullptr && !aligned8(weights))) return HIST_ERR_ALIGN;
   return fill_impl(h, values, weights, n, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int hist_fill_host(hist_t* h, const double* values, const double* weights, int64_t n, int64_t bulk,
+                   hist_stream_t stream) {
+  if (h == nullptr || n < 0 || bulk < 0) return HIST_ERR_ARG;
+  if (n == 0) return HIST_OK;
+  if (values == nullptr) return HIST_ERR_ARG;
+  if (bulk == 0) bulk = kDefaultHostBulk;
+  if (bulk > n) bulk = n;
+  if (cudaSetDevice(h->device) != cudaSuccess) return HIST_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc = pipeline_prepare(h, n, bulk, weights != nullptr);
+  if (rc != HIST_OK) return rc;
+  const int acc = weights == nullptr ? ACC_UNIT : h->acc_mode;
+  const bool smem = acc == ACC_UNIT ? h->smem_unit : h->smem_weighted;
+  // small bulks are launch-bound: replay the whole pipelined fill as one
+  // CUDA graph (exact integer bins in shared memory only: the global
+  // fixed-point path needs host-side overflow bookkeeping per fill)
+  const bool graph = bulk <= kHostGraphBulk && smem && (n + bulk - 1) / bulk <= kHostGraphBulks;
+  if (!graph) return pipeline_enqueue(h, values, weights, n, bulk, s);
+  if (h->host_exec == nullptr || h->g_values != values || h->g_weights != weights || h->g_n != n ||
+      h->g_bulk != bulk) {
+    if (h->host_exec) {
+      cudaGraphExecDestroy(h->host_exec);
+      h->host_exec = nullptr;
+    }
+    if (h->cap_stream == nullptr && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return HIST_ERR_CUDA;
+    const int64_t entries = h->n_entries;
+    const bool complete = h->counts_complete, had_done = h->have_done;
+    if (h->have_done && cudaEventSynchronize(h->done) != cudaSuccess) return HIST_ERR_CUDA;
+    h->capturing = true;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      h->capturing = false;
+      return HIST_ERR_CUDA;
+    }
+    rc = pipeline_enqueue(h, values, weights, n, bulk, h->cap_stream);
+    const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &g);
+    h->capturing = false;
+    h->n_entries = entries;
+    h->counts_complete = complete;
+    h->have_done = had_done;
+    if (rc != HIST_OK || ec != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return rc != HIST_OK ? rc : HIST_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&h->host_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      h->host_exec = nullptr;
+      return HIST_ERR_CUDA;
+    }
+    h->g_values = values;
+    h->g_weights = weights;
+    h->g_n = n;
+    h->g_bulk = bulk;
+  }
+  if ((rc = order_after_previous(h, s)) != HIST_OK) return rc;
+  if (cudaGraphLaunch(h->host_exec, s) != cudaSuccess) return HIST_ERR_CUDA;
+  if (cudaEventRecord(h->done, s) != cudaSuccess) return HIST_ERR_CUDA;
+  h->have_done = true;
+  h->n_entries += n;
+  if (acc != ACC_UNIT && !(h->flags & HIST_TRACK_COUNTS)) h->counts_complete = false;
+  for (int i = 0; i < 2; ++i) h->slot_used[i] = false;  // the graph orders its own slot reuse
+  return HIST_OK;
 }
 
 int hist_locate(hist_t* h, const double* values, int64_t n, int64_t* out, hist_stream_t stream) {
