@@ -74,6 +74,7 @@ typedef struct {
 /* Booking flags (bitwise or). */
 #define HIST_TRACK_COUNTS (1u << 0)   /* keep per-bin entry counts for weighted fills */
 #define HIST_STAT_OVERFLOWS (1u << 1) /* include under/overflow entries in the statistics */
+#define HIST_SUMW2 (1u << 2)          /* also keep each bin's sum of squared weights (ROOT's Sumw2) */
 /* Accumulation of weighted bin contents (bits 4-5):
  *   HIST_PREC_FP64   (default) exact fixed-point sums of each weight truncated
  *                    to a multiple of 2^-50 (relative error <= 2^-42 per
@@ -147,6 +148,17 @@ int hist_result(hist_t *h, double *bins, double *stats);
  * always have them; weighted ones need HIST_TRACK_COUNTS (else
  * HIST_ERR_STATE). */
 int hist_counts(hist_t *h, uint64_t *counts);
+
+/* Per-bin sum of squared weights (the bin errors' input; with HIST_SUMW2),
+ * host out [prod(nbins_d + 2)], every entry's w*w (1 for unit-weight
+ * entries).  Weighted fills with the bins in shared memory keep it as FP32
+ * compensated words (the square formed as an FP32 double-word, within
+ * 2^-45 w^2 of fl(w*w)) flushed to binary64, with the error bound of
+ * HIST_PREC_FP32C relative to sum w^2; otherwise binary64 atomics of
+ * fl(w*w).  Synchronizes like hist_result.  Errors: HIST_ERR_ARG,
+ * HIST_ERR_STATE (booked without HIST_SUMW2), HIST_ERR_CUDA.  Histograms
+ * with HIST_SUMW2 cannot join a batch (HIST_ERR_UNSUPPORTED there). */
+int hist_sumw2(hist_t *h, double *sumw2);
 
 /* Fill from HOST memory, pipelined (Sec. 3.2 transfers bulks of events to
  * the GPU; Sec. 6 names pipelining the bulks as future work): values host

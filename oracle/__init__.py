@@ -258,3 +258,18 @@ def fill(axes, values, weights=None, stat_overflows: bool = False,
     acc = Accumulator(axes, stat_overflows)
     acc.fill(values, weights, threads=threads)
     return acc.result()
+
+
+def sumw2(axes, values, weights=None, threads: int = 1):
+    """Per-bin sum of squared weights (ROOT's Sumw2, the input of the bin
+    errors; the paper's statistics sums stop at the per-histogram level):
+    each entry adds its rounded w*w to its bin -- the per-bin weighted sum
+    of this oracle with the squared weights as weights; unit weights give
+    the entry counts.  Returns (compensated sums, sums of |w*w|)."""
+    if weights is None:
+        r = fill(axes, values, None, threads=threads)
+        c = r.counts.astype(np.float64)
+        return c, c.copy()
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    r = fill(axes, values, w * w, threads=threads)
+    return r.bins_acc, r.bins_abs

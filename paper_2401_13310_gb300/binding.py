@@ -36,6 +36,7 @@ HIST_AXIS_VARIABLE = 1
 
 HIST_TRACK_COUNTS = 1 << 0
 HIST_STAT_OVERFLOWS = 1 << 1
+HIST_SUMW2 = 1 << 2
 HIST_PREC_FP64 = 0 << 4
 HIST_PREC_FP32C = 1 << 4
 HIST_PREC_F64ATOMIC = 2 << 4
@@ -117,6 +118,7 @@ def load(path: str | None = None):
             "hist_batch_fill": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
             "hist_batch_tune": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
             "hist_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+            "hist_sumw2": (ctypes.c_int, [_P, _P]),
             "hist_fill_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P]),
             "hist_locator_mode": (ctypes.c_int, [_P, ctypes.c_int]),
             "hist_kernel_time": (ctypes.c_int, [_P, _P, _P]),
@@ -333,6 +335,13 @@ def hist_locator_mode(h: int, axis: int = 0) -> str:
     return LOCATOR_MODES[m]
 
 
+def hist_sumw2(h: int, nbins_total: int):
+    import numpy as np
+    out = np.zeros(nbins_total, dtype=np.float64)
+    _check(load().hist_sumw2(h, out.ctypes.data), "hist_sumw2")
+    return out
+
+
 def hist_fill_host(h: int, values, weights, n: int, bulk: int = 0, stream=None) -> None:
     """Pipelined fill from host memory: ``values`` and ``weights`` are CPU
     tensors (pinned for asynchronous copies) or numpy arrays, float64,
@@ -419,6 +428,9 @@ class Hist:
         if weights is not None:
             assert weights.shape == (n,) and weights.is_contiguous()
         hist_fill_bulk(self.h, values, weights, n, stream)
+
+    def sumw2(self):
+        return hist_sumw2(self.h, self.nbins_total)
 
     def fill_host(self, values, weights=None, bulk: int = 0, stream=None) -> None:
         n = int(values.shape[-1])

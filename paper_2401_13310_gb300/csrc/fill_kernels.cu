@@ -170,6 +170,33 @@ __device__ __noinline__ void slow_bin(double* g_f64, long long g, unsigned long 
   atomicAdd(&g_f64[g], __longlong_as_double((long long)wb));
 }
 
+__device__ __noinline__ void sumw2_global(double* g_sumw2, long long g, unsigned long long wb) {
+  const double w = __longlong_as_double((long long)wb);
+  atomicAdd(&g_sumw2[g], __dmul_rn(w, w));
+}
+
+// w^2 into FP32 compensated shared words (hi, lo) of bin g: the square as an
+// FP32 double-word from the weight's hi + lo split (within 2^-45 w^2 of
+// fl(w*w)), hi added by an atomic that returns the old value so its
+// rounding error is recovered exactly (TwoSum) and added with the low part;
+// weights outside the double-word range take the binary64 global atomic.
+__device__ __noinline__ void sumw2_shared(unsigned* words, double* g_sumw2, long long g, unsigned long long wb) {
+  if (!in_ff(exp_field(wb))) {
+    sumw2_global(g_sumw2, g, wb);
+    return;
+  }
+  const FF W = ff_split(wb, hi24(wb));
+  const float ph = __fmul_rn(W.hi, W.hi);
+  const float pe = __fmaf_rn(W.hi, W.hi, -ph);
+  const float pl = __fmaf_rn(__fadd_rn(W.hi, W.hi), W.lo, pe);
+  float* a = reinterpret_cast<float*>(&words[2 * g]);
+  const float old = atomicAdd(a, ph);
+  const float sum = __fadd_rn(old, ph);
+  const float bv = __fsub_rn(sum, old);
+  const float err = __fadd_rn(__fsub_rn(old, __fsub_rn(sum, bv)), __fsub_rn(ph, bv));
+  atomicAdd(a + 1, __fadd_rn(err, pl));
+}
+
 __device__ __noinline__ void f64_bin(double* bins, long long slot, unsigned long long wb) {
   atomicAdd(&bins[slot], __longlong_as_double((long long)wb));
 }
@@ -202,7 +229,7 @@ __device__ __forceinline__ void block_reduce_stats(const double* d, double* out,
 // ---------------------------------------------------------------- fill kernel
 
 // Per-thread state of one fill launch and the three steps for one event.
-template <int NDIM, int ACC, bool SMEM, int LOC>
+template <int NDIM, int ACC, bool SMEM, int LOC, bool SW2 = false>
 struct Filler {
   static constexpr bool UNIT = (ACC == ACC_UNIT);
   static constexpr int NS = NStats<NDIM>::NS;
@@ -217,6 +244,16 @@ struct Filler {
   double* slow;  // binary64 statistics of slow-path events (local memory)
 
   __device__ __forceinline__ Filler(const FillParams& pp) : p(pp) {}
+
+  // w^2 of the event into its bin's sum of squares (out of line: the hot
+  // loop of fills without HIST_SUMW2 keeps only the test)
+  __device__ __forceinline__ void sumw2_add(long long g, unsigned long long wb) {
+    constexpr bool kShared = SMEM && (ACC == ACC_FX || ACC == ACC_F32C);
+    if (kShared)
+      sumw2_shared(sbins + (p.track_counts ? 3 : 2) * (int)p.nbins_total, p.g_sumw2, g, wb);
+    else
+      sumw2_global(p.g_sumw2, g, wb);
+  }
 
   __device__ __forceinline__ void event(const unsigned long long* cb, unsigned long long wb) {
     // ---- step 1: the bin on every axis, linearised x fastest
@@ -306,6 +343,8 @@ struct Filler {
         if (p.track_counts) atomicAdd(&p.g_count[g], 1ull);
       }
     }
+    // ---- per-bin sum of w^2 (ROOT's Sumw2)
+    if (SW2) sumw2_add(g, wb);
     // ---- step 3: statistics
     if (!(inr || p.stat_overflows)) return;
     bool fast = (ACC != ACC_F64) && w_ok;
@@ -353,8 +392,8 @@ __device__ __forceinline__ void load_pair(const double* __restrict__ p, long lon
 // All full pairs of events, grid-strided.  The next pair's loads are issued
 // before the current pair is processed, so each thread keeps two pairs of
 // loads in flight across the long per-event work.
-template <int NDIM, int ACC, bool SMEM, int LOC, bool VEC>
-__device__ __forceinline__ void fill_pairs(Filler<NDIM, ACC, SMEM, LOC>& f, long long npairs) {
+template <int NDIM, int ACC, bool SMEM, int LOC, bool SW2, bool VEC>
+__device__ __forceinline__ void fill_pairs(Filler<NDIM, ACC, SMEM, LOC, SW2>& f, long long npairs) {
   const FillParams& p = f.p;
   const long long nthreads = (long long)gridDim.x * blockDim.x;
   int iters = 0;
@@ -396,7 +435,7 @@ __device__ __forceinline__ void fill_pairs(Filler<NDIM, ACC, SMEM, LOC>& f, long
   }
 }
 
-template <int NDIM, int ACC, bool SMEM, int LOC>
+template <int NDIM, int ACC, bool SMEM, int LOC, bool SW2>
 __global__ void __launch_bounds__(256, NDIM == 1 ? HGB_MIN_BLOCKS_1D : HGB_MIN_BLOCKS) k_fill(const FillParams p) {
   constexpr bool UNIT = (ACC == ACC_UNIT);
   constexpr int NS = NStats<NDIM>::NS;
@@ -409,7 +448,7 @@ __global__ void __launch_bounds__(256, NDIM == 1 ? HGB_MIN_BLOCKS_1D : HGB_MIN_B
       smem_raw + (((size_t)nkeys * 12 + 15) & ~(size_t)15) + (((size_t)p.table_bk * 4 + 15) & ~(size_t)15);
   __shared__ double sred[8 * kMaxStats];
 
-  Filler<NDIM, ACC, SMEM, LOC> f(p);
+  Filler<NDIM, ACC, SMEM, LOC, SW2> f(p);
   f.sbins = reinterpret_cast<unsigned*>(after_keys);
   f.sbins_f64 = reinterpret_cast<double*>(after_keys);
   for (int i = threadIdx.x; i < nkeys; i += blockDim.x) {
@@ -427,7 +466,10 @@ __global__ void __launch_bounds__(256, NDIM == 1 ? HGB_MIN_BLOCKS_1D : HGB_MIN_B
   }
   const int nb = (int)p.nbins_total;
   if (SMEM) {
-    const int words = (UNIT ? 1 : ((ACC == ACC_FX || ACC == ACC_F32C) ? (p.track_counts ? 3 : 2) : 4)) * nb;
+    const int words = (UNIT ? 1
+                            : ((ACC == ACC_FX || ACC == ACC_F32C) ? (p.track_counts ? 3 : 2) + (p.sumw2 ? 2 : 0)
+                                                                  : 4)) *
+                      nb;
     for (int i = threadIdx.x; i < words; i += blockDim.x) f.sbins[i] = 0u;
   }
   f.stride1 = p.ax[0].nbins + 2;
@@ -442,9 +484,9 @@ __global__ void __launch_bounds__(256, NDIM == 1 ? HGB_MIN_BLOCKS_1D : HGB_MIN_B
   // every full pair of events, then the odd last event
   const long long n = p.n;
   if (p.aligned)
-    fill_pairs<NDIM, ACC, SMEM, LOC, true>(f, n >> 1);
+    fill_pairs<NDIM, ACC, SMEM, LOC, SW2, true>(f, n >> 1);
   else
-    fill_pairs<NDIM, ACC, SMEM, LOC, false>(f, n >> 1);
+    fill_pairs<NDIM, ACC, SMEM, LOC, SW2, false>(f, n >> 1);
   if ((n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
     unsigned long long c[NDIM];
 #pragma unroll
@@ -481,6 +523,12 @@ __global__ void __launch_bounds__(256, NDIM == 1 ? HGB_MIN_BLOCKS_1D : HGB_MIN_B
         for (int i = threadIdx.x; i < nb; i += blockDim.x) out[i] = sb4[i];
       }
     }
+  }
+  if (SW2 && SMEM && (ACC == ACC_FX || ACC == ACC_F32C)) {
+    const float* sf = reinterpret_cast<const float*>(f.sbins) + (p.track_counts ? 3 : 2) * nb;
+    double* out = p.part_sumw2 + (size_t)blockIdx.x * nb;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+      out[i] = __dadd_rn((double)sf[2 * i], (double)sf[2 * i + 1]);
   }
   block_reduce_stats<NS>(f.st.d, p.part_stats + (size_t)blockIdx.x * kMaxStats, sred);
 }
@@ -528,6 +576,11 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceParams r) {
         atomicAdd(&r.g_f64[g], s);
         if (r.track_counts && c != 0.0) atomicAdd(&r.g_count[g], (unsigned long long)c);
       }
+      if (r.part_sumw2 != nullptr) {
+        double s2 = 0.0;
+        for (int b = b0; b < b1; ++b) s2 = __dadd_rn(s2, r.part_sumw2[(size_t)b * nb + g]);
+        if (s2 != 0.0) atomicAdd(&r.g_sumw2[g], s2);
+      }
     }
   }
   if (blockIdx.x == 0 && blockIdx.y == 0) {
@@ -571,21 +624,26 @@ __global__ void __launch_bounds__(256) k_locate(const FillParams p, long long* _
 }
 
 template <int NDIM, int ACC, bool SMEM>
-const void* fill_fn(int loc) {
+const void* fill_fn(int loc, bool sw2) {
+  if constexpr (ACC != ACC_UNIT) {
+    // the per-bin sum of w^2 has its own kernels (run-time locate): the
+    // other fills keep none of its code
+    if (sw2) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, -1, true>);
+  }
   if constexpr (NDIM > 1) {
-    return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, -1>);
+    return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, -1, false>);
   } else {
-    if (loc == LOC_AFFINE) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_AFFINE>);
-    if (loc == LOC_LEARNED) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_LEARNED>);
-    if (loc == LOC_BUCKET) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_BUCKET>);
-    return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_BSEARCH>);
+    if (loc == LOC_AFFINE) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_AFFINE, false>);
+    if (loc == LOC_LEARNED) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_LEARNED, false>);
+    if (loc == LOC_BUCKET) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_BUCKET, false>);
+    return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_BSEARCH, false>);
   }
 }
 
 // 1D kernels are specialised per locate mode; ND kernels choose per axis at run time.
-const void* pick_fill(int ndim, int acc, bool smem, int loc) {
+const void* pick_fill(int ndim, int acc, bool smem, int loc, bool sw2) {
 #define HGB_PICK(N, A) \
-  if (ndim == N && acc == A) return smem ? fill_fn<N, A, true>(loc) : fill_fn<N, A, false>(loc);
+  if (ndim == N && acc == A) return smem ? fill_fn<N, A, true>(loc, sw2) : fill_fn<N, A, false>(loc, sw2);
   HGB_PICK(1, ACC_UNIT)
   HGB_PICK(1, ACC_FX)
   HGB_PICK(1, ACC_F64)
@@ -606,18 +664,18 @@ const void* pick_fill(int ndim, int acc, bool smem, int loc) {
 
 size_t part_bin_bytes(int acc_mode, int /*track_counts*/) { return acc_mode == ACC_UNIT ? 4 : 16; }
 
-size_t smem_bin_bytes(int acc_mode, int track_counts) {
+size_t smem_bin_bytes(int acc_mode, int track_counts, int sumw2) {
   if (acc_mode == ACC_UNIT) return 4;
-  if (acc_mode == ACC_FX || acc_mode == ACC_F32C) return track_counts ? 12 : 8;
+  if (acc_mode == ACC_FX || acc_mode == ACC_F32C) return (track_counts ? 12 : 8) + (sumw2 ? 8 : 0);
   return 16;
 }
 
 int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shape) {
-  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0, p.ax[0].mode);
+  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0, p.ax[0].mode, p.sumw2 != 0);
   if (fn == nullptr) return -1;
   const int block = 256;
   size_t smem = (((size_t)p.table_keys * 12 + 15) & ~(size_t)15) + (((size_t)p.table_bk * 4 + 15) & ~(size_t)15);
-  if (p.smem_bins) smem += (size_t)p.nbins_total * smem_bin_bytes(acc_mode, p.track_counts);
+  if (p.smem_bins) smem += (size_t)p.nbins_total * smem_bin_bytes(acc_mode, p.track_counts, p.sumw2);
   {  // always: it also loads the kernel before the occupancy query
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;
   }
@@ -635,7 +693,7 @@ int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shap
 }
 
 int launch_fill(const FillParams& p, int acc_mode, const LaunchShape& s, void* stream) {
-  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0, p.ax[0].mode);
+  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0, p.ax[0].mode, p.sumw2 != 0);
   if (fn == nullptr) return -1;
   void* args[] = {const_cast<FillParams*>(&p)};
   const cudaError_t e = cudaLaunchKernel(fn, dim3(s.grid), dim3(s.block), args, s.smem, (cudaStream_t)stream);

@@ -78,6 +78,7 @@ struct hist {
   unsigned long long* g_count = nullptr;
   unsigned long long* g_unit = nullptr;
   double* g_f64 = nullptr;
+  double* g_sumw2 = nullptr;  // HIST_SUMW2: binary64 per-bin sum of w^2 of weighted fills
   double* g_stats = nullptr;
   int64_t n_entries = 0;
   bool counts_complete = true;  // false once a weighted fill ran without HIST_TRACK_COUNTS
@@ -87,6 +88,8 @@ struct hist {
   size_t part_bins_bytes = 0;
   double* part_stats = nullptr;
   int part_stats_blocks = 0;
+  double* part_sumw2 = nullptr;
+  size_t part_sumw2_bytes = 0;
   // ordering of fills issued on different streams
   cudaEvent_t done = nullptr;
   bool have_done = false;
@@ -151,6 +154,8 @@ void free_state(hist* h) {
   cudaFree(h->g_unit);
   cudaFree(h->g_f64);
   cudaFree(h->g_stats);
+  cudaFree(h->g_sumw2);
+  cudaFree(h->part_sumw2);
   cudaFree(h->part_bins);
   cudaFree(h->part_stats);
   for (int d = 0; d < kMaxDim; ++d) cudaFree(h->lm_knots[d]);
@@ -205,8 +210,11 @@ FillParams make_params(const hist* h, const double* values, const double* weight
   for (int d = 0; d < h->ndim; ++d) al = al && aligned16(p.col[d]);
   p.aligned = al ? 1 : 0;
   p.smem_bins = (acc == ACC_UNIT ? h->smem_unit : h->smem_weighted) ? 1 : 0;
+  p.sumw2 = (acc != ACC_UNIT && (h->flags & HIST_SUMW2)) ? 1 : 0;
+  p.g_sumw2 = h->g_sumw2;
   p.part_bins = h->part_bins;
   p.part_stats = h->part_stats;
+  p.part_sumw2 = h->part_sumw2;
   p.g_lo = h->g_lo;
   p.g_hi = h->g_hi;
   p.g_count = h->g_count;
@@ -224,6 +232,15 @@ int ensure_scratch(hist* h, int grid, int acc, bool smem_bins) {
     int rc = dalloc(&h->part_bins, need);
     if (rc != HIST_OK) return rc;
     h->part_bins_bytes = need;
+  }
+  const size_t need2 = (smem_bins && (h->flags & HIST_SUMW2)) ? (size_t)grid * (size_t)h->nbins_total * 8 : 0;
+  if (need2 > h->part_sumw2_bytes) {
+    cudaFree(h->part_sumw2);
+    h->part_sumw2 = nullptr;
+    h->part_sumw2_bytes = 0;
+    int rc = dalloc(&h->part_sumw2, need2);
+    if (rc != HIST_OK) return rc;
+    h->part_sumw2_bytes = need2;
   }
   if (grid > h->part_stats_blocks) {
     cudaFree(h->part_stats);
@@ -256,6 +273,8 @@ int fill_impl(hist* h, const double* values, const double* weights, int64_t n, c
   if (rc != HIST_OK) return rc;
   p.part_bins = h->part_bins;
   p.part_stats = h->part_stats;
+  p.part_sumw2 = h->part_sumw2;  // (re)allocated by ensure_scratch for this grid
+  if (p.sumw2 && p.smem_bins && (acc == ACC_FX || acc == ACC_F32C) && p.part_sumw2 == nullptr) return HIST_ERR_CUDA;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (h->timing && !h->capturing) {
     while (h->t_ev.size() < 2 * (h->t_used + 1)) {
@@ -287,6 +306,9 @@ int fill_impl(hist* h, const double* values, const double* weights, int64_t n, c
   r.g_unit = h->g_unit;
   r.g_f64 = h->g_f64;
   r.g_stats = h->g_stats;
+  const bool sw2_shared = p.sumw2 && p.smem_bins && (acc == ACC_FX || acc == ACC_F32C);
+  r.part_sumw2 = sw2_shared ? h->part_sumw2 : nullptr;
+  r.g_sumw2 = h->g_sumw2;
   if (launch_reduce(r, stream) != 0) return HIST_ERR_CUDA;
   if (acc == ACC_FX && !p.smem_bins) {
     h->fx_global_since_norm += n;
@@ -450,7 +472,7 @@ const char* hist_strerror(int code) {
 int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
   if (out == nullptr || axes == nullptr || ndim < 1 || ndim > kMaxDim) return HIST_ERR_ARG;
   *out = nullptr;
-  const uint32_t known = HIST_TRACK_COUNTS | HIST_STAT_OVERFLOWS | HIST_PREC_MASK | HIST_LOCATOR_MASK;
+  const uint32_t known = HIST_TRACK_COUNTS | HIST_STAT_OVERFLOWS | HIST_SUMW2 | HIST_PREC_MASK | HIST_LOCATOR_MASK;
   if (flags & ~known) return HIST_ERR_ARG;
   if ((flags & HIST_PREC_MASK) == (3u << 4)) return HIST_ERR_ARG;
   if ((flags & HIST_LOCATOR_MASK) > HIST_LOCATOR_BSEARCH) return HIST_ERR_ARG;
@@ -571,7 +593,8 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
     // weighted fills use the precision mode; unit fills always count
     h->acc_mode = acc_mode_of(flags, false);
     h->smem_unit = (size_t)total * smem_bin_bytes(ACC_UNIT, 0) <= kSmemBinsBudget;
-    h->smem_weighted = (size_t)total * smem_bin_bytes(h->acc_mode, (flags & HIST_TRACK_COUNTS) ? 1 : 0) <=
+    h->smem_weighted = (size_t)total * smem_bin_bytes(h->acc_mode, (flags & HIST_TRACK_COUNTS) ? 1 : 0,
+                                                       (flags & HIST_SUMW2) ? 1 : 0) <=
                        kSmemBinsBudget;
     const size_t nb = (size_t)total;
     if ((rc = dalloc(&h->g_lo, nb * 8)) != HIST_OK) break;
@@ -580,6 +603,7 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
     if ((rc = dalloc(&h->g_unit, nb * 8)) != HIST_OK) break;
     if ((rc = dalloc(&h->g_f64, nb * 8)) != HIST_OK) break;
     if ((rc = dalloc(&h->g_stats, kMaxStats * sizeof(double))) != HIST_OK) break;
+    if ((flags & HIST_SUMW2) && (rc = dalloc(&h->g_sumw2, nb * 8)) != HIST_OK) break;
     if (cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess) {
       rc = HIST_ERR_CUDA;
       break;
@@ -603,7 +627,8 @@ int hist_reset(hist_t* h) {
   if (cudaMemset(h->g_lo, 0, nb * 8) != cudaSuccess || cudaMemset(h->g_hi, 0, nb * 8) != cudaSuccess ||
       cudaMemset(h->g_count, 0, nb * 8) != cudaSuccess || cudaMemset(h->g_unit, 0, nb * 8) != cudaSuccess ||
       cudaMemset(h->g_f64, 0, nb * 8) != cudaSuccess ||
-      cudaMemset(h->g_stats, 0, kMaxStats * sizeof(double)) != cudaSuccess)
+      cudaMemset(h->g_stats, 0, kMaxStats * sizeof(double)) != cudaSuccess ||
+      (h->g_sumw2 != nullptr && cudaMemset(h->g_sumw2, 0, nb * 8) != cudaSuccess))
     return HIST_ERR_CUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return HIST_ERR_CUDA;
   h->n_entries = 0;
@@ -793,6 +818,20 @@ int hist_counts(hist_t* h, uint64_t* counts) {
       cudaMemcpy(unit.data(), h->g_unit, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
     return HIST_ERR_CUDA;
   for (size_t g = 0; g < nb; ++g) counts[g] += unit[g];
+  return HIST_OK;
+}
+
+int hist_sumw2(hist_t* h, double* sumw2) {
+  if (h == nullptr || sumw2 == nullptr) return HIST_ERR_ARG;
+  if (!(h->flags & HIST_SUMW2)) return HIST_ERR_STATE;
+  if (cudaSetDevice(h->device) != cudaSuccess) return HIST_ERR_CUDA;
+  if (h->have_done && cudaEventSynchronize(h->done) != cudaSuccess) return HIST_ERR_CUDA;
+  const size_t nb = (size_t)h->nbins_total;
+  std::vector<unsigned long long> unit(nb);
+  if (cudaMemcpy(sumw2, h->g_sumw2, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(unit.data(), h->g_unit, nb * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HIST_ERR_CUDA;
+  for (size_t g = 0; g < nb; ++g) sumw2[g] += (double)unit[g];  // unit weights: w^2 = 1 per entry
   return HIST_OK;
 }
 
@@ -1563,6 +1602,7 @@ extern "C" int hist_batch_create(hist_t* const* hists, int nh, const int32_t* co
   for (int i = 0; i < nh; ++i) {
     if (hists[i] == nullptr || col_of_hist[i] < 0 || col_of_hist[i] >= kBatchMaxCols) return HIST_ERR_ARG;
     if (hists[i]->ndim != 1) return HIST_ERR_UNSUPPORTED;
+    if (hists[i]->flags & HIST_SUMW2) return HIST_ERR_UNSUPPORTED;
     if (hists[i]->device != hists[0]->device) return HIST_ERR_ARG;
     if ((hists[i]->flags & HIST_STAT_OVERFLOWS) != stat_flag) return HIST_ERR_UNSUPPORTED;
     for (int j = 0; j < i; ++j)

@@ -99,6 +99,7 @@ struct FillParams {
   int32_t table_keys;           // keys staged into shared memory (sum over staged axes)
   int32_t aligned;              // columns and weights all 16-byte aligned
   int32_t smem_bins;            // 1 = per-block shared-memory bins, 0 = global atomics
+  int32_t sumw2;                // 1 = also the per-bin sum of squared weights (weighted fills)
   // per-launch partial results (scratch)
   void* part_bins;              // [grid][nbins_total] words per bin depend on the mode
   double* part_stats;           // [grid][kMaxStats]
@@ -108,6 +109,8 @@ struct FillParams {
   unsigned long long* g_count;  // entries of weighted fills (HIST_TRACK_COUNTS)
   unsigned long long* g_unit;   // entries of unit-weight fills (each adds weight 1)
   double* g_f64;                // binary64 bins (F64 mode, F32C mode, FX slow path)
+  double* g_sumw2;              // binary64 per-bin sum of w^2 (sumw2)
+  double* part_sumw2;           // [grid][nbins_total] block partials of sum w^2 (sumw2, shared bins)
 };
 
 struct ReduceParams {
@@ -125,6 +128,8 @@ struct ReduceParams {
   unsigned long long* g_unit;
   double* g_f64;
   double* g_stats;
+  const double* part_sumw2;     // [nblocks][nbins_total] or nullptr
+  double* g_sumw2;
 };
 
 // ---- batched fill: many 1D histograms from one event stream -------------
@@ -262,6 +267,6 @@ int launch_lm_adam(float* theta, float* m1, float* m2, const float* grad, int co
 int launch_lm_pack(const int* base, const float* theta, int2* knots, int count, void* stream);
 int launch_lm_certify(const LearnedDev& m, const long long* T, int nbins, int* max_err, void* stream);
 size_t part_bin_bytes(int acc_mode, int track_counts);
-size_t smem_bin_bytes(int acc_mode, int track_counts);  // per bin, block-private shared memory
+size_t smem_bin_bytes(int acc_mode, int track_counts, int sumw2 = 0);  // per bin, block-private shared memory
 
 }  // namespace hgb

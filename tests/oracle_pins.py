@@ -406,6 +406,25 @@ def check_fills_accumulate(seed=9):
     assert np.array_equal(a.stats_seq, b.stats_seq)
 
 
+def check_sumw2_vs_bincount(seed=10):
+    """Per-bin sum of squared weights against numpy.bincount of w*w over the
+    oracle's own (pinned) bins, and math.fsum per bin; unit weights give the
+    counts."""
+    rng = np.random.default_rng(seed)
+    axes = [oracle_axis_fixed(20, -1.0, 1.0)]
+    x = rng.normal(0, 0.7, 5000)
+    w = rng.uniform(-2.0, 3.0, 5000)
+    s2, a2 = oracle.sumw2(axes, x.reshape(1, -1), w)
+    g = oracle.locate(axes, x.reshape(1, -1))
+    ref = np.bincount(g, weights=w * w, minlength=22)
+    assert np.allclose(s2, ref, rtol=1e-13, atol=0.0)
+    for k in range(22):
+        assert s2[k] == math.fsum((w * w)[g == k])
+        assert a2[k] == math.fsum(np.abs(w * w)[g == k]) or np.isclose(a2[k], np.sum(np.abs(w * w)[g == k]))
+    c, _ = oracle.sumw2(axes, x.reshape(1, -1), None)
+    assert np.array_equal(c, np.bincount(g, minlength=22).astype(np.float64))
+
+
 ALL_CHECKS = [
     check_golden_fixed, check_golden_variable, check_fixed_dyadic_exact,
     check_fixed_vs_rational, check_fixed_centres, check_fixed_range_edges,
@@ -413,5 +432,5 @@ ALL_CHECKS = [
     check_variable_matches_fixed_on_dyadic_edges, check_nd_enumerated,
     check_golden_fill, check_fill_counts_vs_numpy, check_fill_sums_vs_library,
     check_stats_vs_fsum, check_stats_closed_form_centres, check_flows_and_specials,
-    check_fills_accumulate,
+    check_fills_accumulate, check_sumw2_vs_bincount,
 ]
