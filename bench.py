@@ -196,10 +196,37 @@ def measure_precisions(B, W, hbm: float, n: int) -> dict:
     return out
 
 
+def measure_filter_define(B, W, hbm: float, n: int) -> dict:
+    """The paper's RDataFrame example (Filter x != 0, Define r2 = x*x + y*y,
+    Histo1D r2) fused into the fill kernel, beside the same done as separate
+    steps (torch computes r2 and compacts the passing rows, then the fill)."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    x = torch.randn(n, dtype=torch.float64, device="cuda", generator=g) * 1.5
+    y = torch.randn(n, dtype=torch.float64, device="cuda", generator=g) * 1.5
+    x[::10] = 0.0
+    axes = [W.fixed(200, 0.0, 20.0)]
+    h = B.Hist(axes)
+    fused = _timed(lambda: h.fill_columns([x, y], [(B.HIST_DEF_SUMSQ, 0, 1)], [(0, B.HIST_FLT_NE, 0.0)]), 10)
+
+    def separate():
+        r2 = x * x + y * y
+        h.fill(r2[x != 0])
+    sep = _timed(separate, 10)
+    h.close()
+    del x, y
+    torch.cuda.empty_cache()
+    return {"events": n, "fused_ms": fused, "separate_ms": sep, "fused_speedup": sep / fused,
+            "fused_gev_per_s": n / (fused * 1e-3) / 1e9,
+            "fused_hbm_frac": 16 * n / (fused * 1e-3) / 1e9 / hbm}
+
+
 def measure_forms(B, W, hbm: float, args) -> dict:
     """The batched and learned forms beside the plain one, same GPU."""
     import torch
-    out = {"precision": measure_precisions(B, W, hbm, args.events)}
+    out = {"precision": measure_precisions(B, W, hbm, args.events),
+           "filter_define": measure_filter_define(B, W, hbm, args.events)}
     # batched: 64 histograms (10 .. 1e5 bins, fixed and variable) on the
     # columns pT, phi, eta with binary64 weights
     n4 = args.batch_events

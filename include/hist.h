@@ -149,6 +149,38 @@ int hist_result(hist_t *h, double *bins, double *stats);
  * HIST_ERR_STATE). */
 int hist_counts(hist_t *h, uint64_t *counts);
 
+/* ---- fused Filter/Define -------------------------------------------------
+ * The paper's RDataFrame example (Sec. 2, Listing 1) filters rows
+ * (Filter("x != 0")), defines a column (Define("r2", "x*x + y*y")) and
+ * fills a histogram with it.  hist_fill_columns does all three in the fill
+ * kernel, without writing the defined column: for each event i of the
+ * source columns cols[0..ncols) (device [n] binary64 each, ncols <= 4), if
+ * every filter holds (cols[col][i] <op> value, binary64 comparison; NaN
+ * fails all but HIST_FLT_NE), axis d is filled with defines[d] evaluated in
+ * binary64, each operation rounded once, left to right:
+ *   HIST_DEF_COL    a                 HIST_DEF_MUL  a * b
+ *   HIST_DEF_SUMSQ  a*a + b*b         HIST_DEF_ADD  a + b
+ *   HIST_DEF_HYPOT  sqrt(a*a + b*b)   HIST_DEF_SUB  a - b
+ * (a = cols[defines[d].a][i], b = cols[defines[d].b][i]; sqrt correctly
+ * rounded), with weight weights[i] (device [n], or NULL).  Rows that fail a
+ * filter are not entries.  1D and 2D histograms; at most 2 filters.
+ * Asynchronous like hist_fill_bulk.  Errors: HIST_ERR_ARG, HIST_ERR_ALIGN,
+ * HIST_ERR_UNSUPPORTED (3D, or HIST_SUMW2), HIST_ERR_CUDA. */
+enum { HIST_DEF_COL = 0, HIST_DEF_SUMSQ = 1, HIST_DEF_HYPOT = 2, HIST_DEF_MUL = 3, HIST_DEF_ADD = 4, HIST_DEF_SUB = 5 };
+enum { HIST_FLT_NE = 0, HIST_FLT_EQ = 1, HIST_FLT_LT = 2, HIST_FLT_LE = 3, HIST_FLT_GT = 4, HIST_FLT_GE = 5 };
+typedef struct {
+  int32_t op;   /* HIST_DEF_* */
+  int32_t a, b; /* source column indices (b unused by HIST_DEF_COL) */
+} hist_define_t;
+typedef struct {
+  int32_t col;  /* source column index */
+  int32_t op;   /* HIST_FLT_* */
+  double value; /* the constant compared with */
+} hist_filter_t;
+int hist_fill_columns(hist_t *h, const double *const *cols, int ncols, const hist_define_t *defines,
+                      const hist_filter_t *filters, int nfilters, const double *weights, int64_t n,
+                      hist_stream_t stream);
+
 /* Per-bin sum of squared weights (the bin errors' input; with HIST_SUMW2),
  * host out [prod(nbins_d + 2)], every entry's w*w (1 for unit-weight
  * entries).  Weighted fills with the bins in shared memory keep it as FP32

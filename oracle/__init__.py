@@ -260,6 +260,44 @@ def fill(axes, values, weights=None, stat_overflows: bool = False,
     return acc.result()
 
 
+# Filter/Define operation codes (the library's HIST_DEF_* / HIST_FLT_*).
+DEF_COL, DEF_SUMSQ, DEF_HYPOT, DEF_MUL, DEF_ADD, DEF_SUB = range(6)
+FLT_NE, FLT_EQ, FLT_LT, FLT_LE, FLT_GT, FLT_GE = range(6)
+
+
+def define_filter(columns, defines, filters):
+    """The paper's RDataFrame example (Sec. 2, Listing 1) restated: rows
+    pass when every filter (column <op> constant, binary64 comparison)
+    holds; each axis coordinate is its define evaluated in binary64, one
+    rounding per operation, left to right (a*a + b*b is fl(fl(a*a) +
+    fl(b*b)); sqrt correctly rounded).  Returns (mask, values[ndim][n])."""
+    cols = [np.asarray(c, dtype=np.float64) for c in columns]
+    n = cols[0].shape[0]
+    mask = np.ones(n, dtype=bool)
+    with np.errstate(invalid="ignore"):
+        for c, op, v in filters:
+            a = cols[c]
+            mask &= {FLT_NE: a != v, FLT_EQ: a == v, FLT_LT: a < v, FLT_LE: a <= v,
+                     FLT_GT: a > v, FLT_GE: a >= v}[op]
+    vals = []
+    with np.errstate(all="ignore"):
+        for op, a, b in defines:
+            x, y = cols[a], cols[b]
+            if op == DEF_COL:
+                vals.append(x.copy())
+            elif op == DEF_SUMSQ:
+                vals.append(x * x + y * y)
+            elif op == DEF_HYPOT:
+                vals.append(np.sqrt(x * x + y * y))
+            elif op == DEF_MUL:
+                vals.append(x * y)
+            elif op == DEF_ADD:
+                vals.append(x + y)
+            else:
+                vals.append(x - y)
+    return mask, np.stack(vals)
+
+
 def sumw2(axes, values, weights=None, threads: int = 1):
     """Per-bin sum of squared weights (ROOT's Sumw2, the input of the bin
     errors; the paper's statistics sums stop at the per-histogram level):

@@ -63,6 +63,18 @@ class hist_locator_report_t(ctypes.Structure):
                 ("train_ms", ctypes.c_double)]
 
 
+class hist_define_t(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("a", ctypes.c_int32), ("b", ctypes.c_int32)]
+
+
+class hist_filter_t(ctypes.Structure):
+    _fields_ = [("col", ctypes.c_int32), ("op", ctypes.c_int32), ("value", ctypes.c_double)]
+
+
+HIST_DEF_COL, HIST_DEF_SUMSQ, HIST_DEF_HYPOT, HIST_DEF_MUL, HIST_DEF_ADD, HIST_DEF_SUB = range(6)
+HIST_FLT_NE, HIST_FLT_EQ, HIST_FLT_LT, HIST_FLT_LE, HIST_FLT_GT, HIST_FLT_GE = range(6)
+
+
 class hist_batch_tuning_t(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("smem_hists", ctypes.c_int32),
@@ -119,6 +131,8 @@ def load(path: str | None = None):
             "hist_batch_tune": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
             "hist_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int]),
             "hist_sumw2": (ctypes.c_int, [_P, _P]),
+            "hist_fill_columns": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.c_int, _P, ctypes.c_int64,
+                                                 _P]),
             "hist_fill_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P]),
             "hist_locator_mode": (ctypes.c_int, [_P, ctypes.c_int]),
             "hist_kernel_time": (ctypes.c_int, [_P, _P, _P]),
@@ -335,6 +349,16 @@ def hist_locator_mode(h: int, axis: int = 0) -> str:
     return LOCATOR_MODES[m]
 
 
+def hist_fill_columns(h: int, cols, defines, filters, weights, n: int, stream=None) -> None:
+    """Fused Filter/Define fill: ``cols`` device float64 tensors, ``defines``
+    [(op, a, b)] per axis, ``filters`` [(col, op, value)]."""
+    arr = _col_array(cols)
+    d = (hist_define_t * max(len(defines), 1))(*[hist_define_t(int(o), int(a), int(b)) for o, a, b in defines])
+    f = (hist_filter_t * max(len(filters), 1))(*[hist_filter_t(int(c), int(o), float(v)) for c, o, v in filters])
+    _check(load().hist_fill_columns(h, arr, len(cols), ctypes.byref(d), ctypes.byref(f), len(filters),
+                                    _ptr(weights), int(n), _stream_ptr(stream)), "hist_fill_columns")
+
+
 def hist_sumw2(h: int, nbins_total: int):
     import numpy as np
     out = np.zeros(nbins_total, dtype=np.float64)
@@ -428,6 +452,9 @@ class Hist:
         if weights is not None:
             assert weights.shape == (n,) and weights.is_contiguous()
         hist_fill_bulk(self.h, values, weights, n, stream)
+
+    def fill_columns(self, cols, defines, filters=(), weights=None, stream=None) -> None:
+        hist_fill_columns(self.h, list(cols), list(defines), list(filters), weights, int(cols[0].shape[-1]), stream)
 
     def sumw2(self):
         return hist_sumw2(self.h, self.nbins_total)

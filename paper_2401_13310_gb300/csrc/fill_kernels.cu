@@ -435,7 +435,66 @@ __device__ __forceinline__ void fill_pairs(Filler<NDIM, ACC, SMEM, LOC, SW2>& f,
   }
 }
 
+// Fused Filter/Define: every event of the source columns, grid-strided;
+// the filters (each a binary64 comparison with a constant) decide whether
+// it is filled at all, and the defines give its coordinates, each
+// operation rounded once as written (x*x + y*y is fl(fl(x*x) + fl(y*y))).
+// Passing events are counted (the entry count).
+__device__ __forceinline__ bool expr_pass(const ExprDev& ex, const double* v) {
+  bool ok = true;
+  for (int k = 0; k < ex.nfilt; ++k) {
+    const double a = v[ex.filt_col[k]], c = ex.filt_val[k];
+    bool t;
+    switch (ex.filt_op[k]) {
+      case FLT_NE: t = a != c; break;
+      case FLT_EQ: t = a == c; break;
+      case FLT_LT: t = a < c; break;
+      case FLT_LE: t = a <= c; break;
+      case FLT_GT: t = a > c; break;
+      default: t = a >= c; break;
+    }
+    ok = ok && t;
+  }
+  return ok;
+}
+
+__device__ __forceinline__ double expr_define(int op, double a, double b) {
+  switch (op) {
+    case DEF_SUMSQ: return __dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b));
+    case DEF_HYPOT: return __dsqrt_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)));
+    case DEF_MUL: return __dmul_rn(a, b);
+    case DEF_ADD: return __dadd_rn(a, b);
+    case DEF_SUB: return __dsub_rn(a, b);
+    default: return a;
+  }
+}
+
 template <int NDIM, int ACC, bool SMEM, int LOC, bool SW2>
+__device__ __forceinline__ void fill_expr(Filler<NDIM, ACC, SMEM, LOC, SW2>& f) {
+  const FillParams& p = f.p;
+  const ExprDev& ex = p.ex;
+  const long long n = p.n;
+  unsigned long long passed = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v[kExprMaxSrc];
+#pragma unroll
+    for (int c = 0; c < kExprMaxSrc; ++c) v[c] = c < ex.nsrc ? __ldcs(ex.src[c] + i) : 0.0;
+    if (!expr_pass(ex, v)) continue;
+    ++passed;
+    unsigned long long cb[NDIM];
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d)
+      cb[d] = (unsigned long long)__double_as_longlong(expr_define(ex.def_op[d], v[ex.def_a[d]], v[ex.def_b[d]]));
+    const unsigned long long wb =
+        ACC == ACC_UNIT ? 0x3FF0000000000000ull : __ldcs(reinterpret_cast<const unsigned long long*>(p.w) + i);
+    f.event(cb, wb);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) passed += __shfl_down_sync(0xffffffffu, passed, o);
+  if ((threadIdx.x & 31) == 0 && passed) atomicAdd(ex.g_passed, passed);
+}
+
+template <int NDIM, int ACC, bool SMEM, int LOC, bool SW2, bool EXPR>
 __global__ void __launch_bounds__(256, NDIM == 1 ? HGB_MIN_BLOCKS_1D : HGB_MIN_BLOCKS) k_fill(const FillParams p) {
   constexpr bool UNIT = (ACC == ACC_UNIT);
   constexpr int NS = NStats<NDIM>::NS;
@@ -483,11 +542,13 @@ __global__ void __launch_bounds__(256, NDIM == 1 ? HGB_MIN_BLOCKS_1D : HGB_MIN_B
 
   // every full pair of events, then the odd last event
   const long long n = p.n;
-  if (p.aligned)
+  if (EXPR)
+    fill_expr(f);
+  else if (p.aligned)
     fill_pairs<NDIM, ACC, SMEM, LOC, SW2, true>(f, n >> 1);
   else
     fill_pairs<NDIM, ACC, SMEM, LOC, SW2, false>(f, n >> 1);
-  if ((n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
+  if (!EXPR && (n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
     unsigned long long c[NDIM];
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) c[d] = __ldcs(reinterpret_cast<const unsigned long long*>(p.col[d]) + (n - 1));
@@ -624,26 +685,32 @@ __global__ void __launch_bounds__(256) k_locate(const FillParams p, long long* _
 }
 
 template <int NDIM, int ACC, bool SMEM>
-const void* fill_fn(int loc, bool sw2) {
+const void* fill_fn(int loc, bool sw2, bool expr) {
+  if constexpr (NDIM <= 2) {
+    // Filter/Define fills (1D and 2D; run-time locate)
+    if (expr) return sw2 ? nullptr : reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, -1, false, true>);
+  } else {
+    if (expr) return nullptr;
+  }
   if constexpr (ACC != ACC_UNIT) {
     // the per-bin sum of w^2 has its own kernels (run-time locate): the
     // other fills keep none of its code
-    if (sw2) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, -1, true>);
+    if (sw2) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, -1, true, false>);
   }
   if constexpr (NDIM > 1) {
-    return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, -1, false>);
+    return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, -1, false, false>);
   } else {
-    if (loc == LOC_AFFINE) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_AFFINE, false>);
-    if (loc == LOC_LEARNED) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_LEARNED, false>);
-    if (loc == LOC_BUCKET) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_BUCKET, false>);
-    return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_BSEARCH, false>);
+    if (loc == LOC_AFFINE) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_AFFINE, false, false>);
+    if (loc == LOC_LEARNED) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_LEARNED, false, false>);
+    if (loc == LOC_BUCKET) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_BUCKET, false, false>);
+    return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_BSEARCH, false, false>);
   }
 }
 
 // 1D kernels are specialised per locate mode; ND kernels choose per axis at run time.
-const void* pick_fill(int ndim, int acc, bool smem, int loc, bool sw2) {
+const void* pick_fill(int ndim, int acc, bool smem, int loc, bool sw2, bool expr) {
 #define HGB_PICK(N, A) \
-  if (ndim == N && acc == A) return smem ? fill_fn<N, A, true>(loc, sw2) : fill_fn<N, A, false>(loc, sw2);
+  if (ndim == N && acc == A) return smem ? fill_fn<N, A, true>(loc, sw2, expr) : fill_fn<N, A, false>(loc, sw2, expr);
   HGB_PICK(1, ACC_UNIT)
   HGB_PICK(1, ACC_FX)
   HGB_PICK(1, ACC_F64)
@@ -671,7 +738,7 @@ size_t smem_bin_bytes(int acc_mode, int track_counts, int sumw2) {
 }
 
 int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shape) {
-  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0, p.ax[0].mode, p.sumw2 != 0);
+  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0, p.ax[0].mode, p.sumw2 != 0, p.ex.nsrc > 0);
   if (fn == nullptr) return -1;
   const int block = 256;
   size_t smem = (((size_t)p.table_keys * 12 + 15) & ~(size_t)15) + (((size_t)p.table_bk * 4 + 15) & ~(size_t)15);
@@ -693,7 +760,7 @@ int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shap
 }
 
 int launch_fill(const FillParams& p, int acc_mode, const LaunchShape& s, void* stream) {
-  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0, p.ax[0].mode, p.sumw2 != 0);
+  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0, p.ax[0].mode, p.sumw2 != 0, p.ex.nsrc > 0);
   if (fn == nullptr) return -1;
   void* args[] = {const_cast<FillParams*>(&p)};
   const cudaError_t e = cudaLaunchKernel(fn, dim3(s.grid), dim3(s.block), args, s.smem, (cudaStream_t)stream);

@@ -79,6 +79,7 @@ struct hist {
   unsigned long long* g_unit = nullptr;
   double* g_f64 = nullptr;
   double* g_sumw2 = nullptr;  // HIST_SUMW2: binary64 per-bin sum of w^2 of weighted fills
+  unsigned long long* g_passed = nullptr;  // entries of filtered fills (counted on the device)
   double* g_stats = nullptr;
   int64_t n_entries = 0;
   bool counts_complete = true;  // false once a weighted fill ran without HIST_TRACK_COUNTS
@@ -155,6 +156,7 @@ void free_state(hist* h) {
   cudaFree(h->g_f64);
   cudaFree(h->g_stats);
   cudaFree(h->g_sumw2);
+  cudaFree(h->g_passed);
   cudaFree(h->part_sumw2);
   cudaFree(h->part_bins);
   cudaFree(h->part_stats);
@@ -261,12 +263,17 @@ int order_after_previous(hist* h, cudaStream_t s) {
   return HIST_OK;
 }
 
-int fill_impl(hist* h, const double* values, const double* weights, int64_t n, cudaStream_t stream) {
+int fill_impl(hist* h, const double* values, const double* weights, int64_t n, cudaStream_t stream,
+              const ExprDev* ex = nullptr) {
   const int acc = (weights == nullptr) ? ACC_UNIT : acc_mode_of(h->flags, false);
   if (cudaSetDevice(h->device) != cudaSuccess) return HIST_ERR_CUDA;
   int rc = order_after_previous(h, stream);
   if (rc != HIST_OK) return rc;
   FillParams p = make_params(h, values, weights, n, acc);
+  if (ex != nullptr) {
+    p.ex = *ex;
+    p.ex.g_passed = h->g_passed;
+  }
   LaunchShape shape;
   if (plan_fill(p, acc, h->sm_count, &shape) != 0) return HIST_ERR_CUDA;
   rc = ensure_scratch(h, shape.grid, acc, p.smem_bins != 0);
@@ -320,7 +327,7 @@ int fill_impl(hist* h, const double* values, const double* weights, int64_t n, c
   // (inside a capture the graph's launch records completion instead)
   if (!h->capturing && cudaEventRecord(h->done, stream) != cudaSuccess) return HIST_ERR_CUDA;
   h->have_done = true;
-  h->n_entries += n;
+  if (ex == nullptr) h->n_entries += n;  // filtered fills count their passing events on the device
   if (acc != ACC_UNIT && !(h->flags & HIST_TRACK_COUNTS)) h->counts_complete = false;
   return HIST_OK;
 }
@@ -604,6 +611,7 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
     if ((rc = dalloc(&h->g_f64, nb * 8)) != HIST_OK) break;
     if ((rc = dalloc(&h->g_stats, kMaxStats * sizeof(double))) != HIST_OK) break;
     if ((flags & HIST_SUMW2) && (rc = dalloc(&h->g_sumw2, nb * 8)) != HIST_OK) break;
+    if ((rc = dalloc(&h->g_passed, 8)) != HIST_OK) break;
     if (cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess) {
       rc = HIST_ERR_CUDA;
       break;
@@ -628,7 +636,8 @@ int hist_reset(hist_t* h) {
       cudaMemset(h->g_count, 0, nb * 8) != cudaSuccess || cudaMemset(h->g_unit, 0, nb * 8) != cudaSuccess ||
       cudaMemset(h->g_f64, 0, nb * 8) != cudaSuccess ||
       cudaMemset(h->g_stats, 0, kMaxStats * sizeof(double)) != cudaSuccess ||
-      (h->g_sumw2 != nullptr && cudaMemset(h->g_sumw2, 0, nb * 8) != cudaSuccess))
+      (h->g_sumw2 != nullptr && cudaMemset(h->g_sumw2, 0, nb * 8) != cudaSuccess) ||
+      cudaMemset(h->g_passed, 0, 8) != cudaSuccess)
     return HIST_ERR_CUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return HIST_ERR_CUDA;
   h->n_entries = 0;
@@ -797,7 +806,9 @@ int hist_result(hist_t* h, double* bins, double* stats) {
   if (stats != nullptr) {
     double s[kMaxStats];
     if (cudaMemcpy(s, h->g_stats, sizeof(s), cudaMemcpyDeviceToHost) != cudaSuccess) return HIST_ERR_CUDA;
-    s[0] = (double)h->n_entries;
+    unsigned long long passed = 0;
+    if (cudaMemcpy(&passed, h->g_passed, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return HIST_ERR_CUDA;
+    s[0] = (double)(h->n_entries + (int64_t)passed);
     // sum w over the statistics' entries = sum of those bins' contents
     s[1] = (double)sel_fx * lsb + (sel_f64 + sel_c);
     // unit-weight entries add 1 each to sum w^2
@@ -819,6 +830,43 @@ int hist_counts(hist_t* h, uint64_t* counts) {
     return HIST_ERR_CUDA;
   for (size_t g = 0; g < nb; ++g) counts[g] += unit[g];
   return HIST_OK;
+}
+
+int hist_fill_columns(hist_t* h, const double* const* cols, int ncols, const hist_define_t* defines,
+                      const hist_filter_t* filters, int nfilters, const double* weights, int64_t n,
+                      hist_stream_t stream) {
+  if (h == nullptr || n < 0 || ncols < 1 || ncols > kExprMaxSrc || cols == nullptr || defines == nullptr ||
+      nfilters < 0 || nfilters > kExprMaxFilters || (nfilters > 0 && filters == nullptr))
+    return HIST_ERR_ARG;
+  if (h->ndim > 2 || (h->flags & HIST_SUMW2)) return HIST_ERR_UNSUPPORTED;
+  ExprDev ex;
+  std::memset(&ex, 0, sizeof(ex));
+  ex.nsrc = ncols;
+  for (int c = 0; c < ncols; ++c) {
+    if (n > 0 && cols[c] == nullptr) return HIST_ERR_ARG;
+    if (!aligned8(cols[c])) return HIST_ERR_ALIGN;
+    ex.src[c] = cols[c];
+  }
+  if (weights != nullptr && !aligned8(weights)) return HIST_ERR_ALIGN;
+  for (int d = 0; d < h->ndim; ++d) {
+    const hist_define_t& df = defines[d];
+    if (df.op < HIST_DEF_COL || df.op > HIST_DEF_SUB || df.a < 0 || df.a >= ncols ||
+        (df.op != HIST_DEF_COL && (df.b < 0 || df.b >= ncols)))
+      return HIST_ERR_ARG;
+    ex.def_op[d] = df.op;
+    ex.def_a[d] = df.a;
+    ex.def_b[d] = df.op == HIST_DEF_COL ? df.a : df.b;
+  }
+  ex.nfilt = nfilters;
+  for (int k = 0; k < nfilters; ++k) {
+    if (filters[k].col < 0 || filters[k].col >= ncols || filters[k].op < HIST_FLT_NE || filters[k].op > HIST_FLT_GE)
+      return HIST_ERR_ARG;
+    ex.filt_col[k] = filters[k].col;
+    ex.filt_op[k] = filters[k].op;
+    ex.filt_val[k] = filters[k].value;
+  }
+  if (n == 0) return HIST_OK;
+  return fill_impl(h, cols[0], weights, n, reinterpret_cast<cudaStream_t>(stream), &ex);
 }
 
 int hist_sumw2(hist_t* h, double* sumw2) {

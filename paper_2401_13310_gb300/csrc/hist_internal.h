@@ -82,8 +82,25 @@ struct AxisDev {
   BucketDev bk;
 };
 
+// Fused Filter/Define (the paper's RDataFrame example, Sec. 2): events of
+// the source columns that pass every filter are filled with coordinates
+// computed per axis in binary64, each operation rounded once, left to right.
+constexpr int kExprMaxSrc = 4;
+constexpr int kExprMaxFilters = 2;
+enum DefineOp : int32_t { DEF_COL = 0, DEF_SUMSQ = 1, DEF_HYPOT = 2, DEF_MUL = 3, DEF_ADD = 4, DEF_SUB = 5 };
+enum FilterOp : int32_t { FLT_NE = 0, FLT_EQ = 1, FLT_LT = 2, FLT_LE = 3, FLT_GT = 4, FLT_GE = 5 };
+struct ExprDev {
+  const double* src[kExprMaxSrc];
+  int32_t nsrc, nfilt;
+  int32_t def_op[kMaxDim], def_a[kMaxDim], def_b[kMaxDim];
+  int32_t filt_col[kExprMaxFilters], filt_op[kExprMaxFilters];
+  double filt_val[kExprMaxFilters];
+  unsigned long long* g_passed;  // events that passed the filters (entry count)
+};
+
 struct FillParams {
   AxisDev ax[kMaxDim];
+  ExprDev ex;                   // used by the expression kernels only
   const double* col[kMaxDim];
   const double* w;              // nullptr = unit weights
   const long long* T_concat;    // all axes' keys back to back (shared-memory staging source)

@@ -425,6 +425,36 @@ def check_sumw2_vs_bincount(seed=10):
     assert np.array_equal(c, np.bincount(g, minlength=22).astype(np.float64))
 
 
+def check_define_filter_vs_python_loops(seed=11):
+    """The Filter/Define restatement against per-event Python float
+    arithmetic (IEEE binary64, one rounding per operation) on small inputs,
+    with zeros, NaN, infinities and signed zeros in the columns."""
+    rng = np.random.default_rng(seed)
+    x = rng.normal(0, 2, 300)
+    y = rng.normal(0, 2, 300)
+    x[::7] = 0.0
+    x[1::11] = -0.0
+    y[2::13] = math.nan
+    x[3::17] = math.inf
+    defines = [(oracle.DEF_SUMSQ, 0, 1), (oracle.DEF_HYPOT, 0, 1), (oracle.DEF_MUL, 0, 1),
+               (oracle.DEF_ADD, 0, 1), (oracle.DEF_SUB, 0, 1), (oracle.DEF_COL, 1, 0)]
+    filters = [(0, oracle.FLT_NE, 0.0), (1, oracle.FLT_LT, 3.0)]
+    mask, vals = oracle.define_filter([x, y], defines, filters)
+    for i in range(300):
+        a, b = float(x[i]), float(y[i])
+        assert mask[i] == ((a != 0.0) and (b < 3.0))
+        aa, bb = a * a, b * b
+        s2 = aa + bb
+        want = [s2, math.sqrt(s2) if s2 >= 0 or math.isnan(s2) else math.nan, a * b, a + b, a - b, b]
+        for k, wv in enumerate(want):
+            got = float(vals[k][i])
+            assert (math.isnan(got) and math.isnan(wv)) or got == wv, (i, k, got, wv)
+    for op, fn in [(oracle.FLT_EQ, lambda a: a == 1.5), (oracle.FLT_LE, lambda a: a <= 1.5),
+                   (oracle.FLT_GT, lambda a: a > 1.5), (oracle.FLT_GE, lambda a: a >= 1.5)]:
+        m, _ = oracle.define_filter([x], [(oracle.DEF_COL, 0, 0)], [(0, op, 1.5)])
+        assert all(m[i] == fn(float(x[i])) for i in range(300))
+
+
 ALL_CHECKS = [
     check_golden_fixed, check_golden_variable, check_fixed_dyadic_exact,
     check_fixed_vs_rational, check_fixed_centres, check_fixed_range_edges,
@@ -432,5 +462,5 @@ ALL_CHECKS = [
     check_variable_matches_fixed_on_dyadic_edges, check_nd_enumerated,
     check_golden_fill, check_fill_counts_vs_numpy, check_fill_sums_vs_library,
     check_stats_vs_fsum, check_stats_closed_form_centres, check_flows_and_specials,
-    check_fills_accumulate, check_sumw2_vs_bincount,
+    check_fills_accumulate, check_sumw2_vs_bincount, check_define_filter_vs_python_loops,
 ]
