@@ -176,7 +176,9 @@ def measure_precisions(B, W, hbm: float, n: int) -> dict:
     wa = W.cfg2a(n=n, device="cuda")
     wb = W.cfg2b(n=n, device="cuda")
     for name, flag in (("fixed_point", B.HIST_PREC_FP64), ("fp32_compensated", B.HIST_PREC_FP32C),
-                       ("f64_atomic", B.HIST_PREC_F64ATOMIC)):
+                       ("f64_atomic", B.HIST_PREC_F64ATOMIC),
+                       ("fixed_point_sumw2", B.HIST_PREC_FP64 | B.HIST_SUMW2),
+                       ("fixed_point_exact_stats", B.HIST_PREC_FP64 | B.HIST_STATS_EXACT)):
         res = {}
         for tag, wl in (("a_fixed1000", wa), ("b_var500", wb)):
             h = B.Hist(wl.axes, flag)
@@ -184,11 +186,11 @@ def measure_precisions(B, W, hbm: float, n: int) -> dict:
                 h.fill(wl.values, wl.weights)
             torch.cuda.synchronize()
             B.hist_set_kernel_timing(h.h, True)
-            for _ in range(20):
-                h.fill(wl.values, wl.weights)
+            call_ms = _timed(lambda: h.fill(wl.values, wl.weights), 20)
             ms, k = B.hist_kernel_time(h.h)
             h.close()
             res[tag + "_ms"] = ms / k
+            res[tag + "_call_ms"] = call_ms
             res[tag + "_hbm_frac"] = BYTES_PER_EVENT * n / (ms / k * 1e-3) / 1e9 / hbm
         out[name] = res
     del wa, wb

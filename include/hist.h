@@ -75,6 +75,15 @@ typedef struct {
 #define HIST_TRACK_COUNTS (1u << 0)   /* keep per-bin entry counts for weighted fills */
 #define HIST_STAT_OVERFLOWS (1u << 1) /* include under/overflow entries in the statistics */
 #define HIST_SUMW2 (1u << 2)          /* also keep each bin's sum of squared weights (ROOT's Sumw2) */
+/* HIST_STATS_EXACT (1D): the statistics sum w, w^2, w*x, w*x^2 become the
+ * exact sums of their rounded terms (w, fl(w*w), fl(w*x), fl(fl(w*x)*x)),
+ * rounded once to binary64 -- bit-reproducible whatever the launch shape,
+ * the order of atomics or the split into fills, and equal to a correctly
+ * rounded exact sum (math.fsum) of the same terms.  A second pass over
+ * each bulk accumulates them in integer limbs (see the design notes); it
+ * costs one more read of the bulk.  Not with hist_fill_columns or batches
+ * (HIST_ERR_UNSUPPORTED); ND histograms: HIST_ERR_UNSUPPORTED at booking. */
+#define HIST_STATS_EXACT (1u << 3)
 /* Accumulation of weighted bin contents (bits 4-5):
  *   HIST_PREC_FP64   (default) exact fixed-point sums of each weight truncated
  *                    to a multiple of 2^-50 (relative error <= 2^-42 per

@@ -26,6 +26,8 @@ import subprocess
 import threading
 from dataclasses import dataclass
 
+import math
+
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -258,6 +260,35 @@ def fill(axes, values, weights=None, stat_overflows: bool = False,
     acc = Accumulator(axes, stat_overflows)
     acc.fill(values, weights, threads=threads)
     return acc.result()
+
+
+def exact_stats(axes, values, weights=None, stat_overflows: bool = False):
+    """1D statistics as the exact sums of their rounded terms (R6: w, w*w,
+    w*x, (w*x)*x, binary64), each rounded once (math.fsum is the correctly
+    rounded sum of its inputs), over the in-range entries (R5).  Returns
+    [sum w, sum w^2, sum wx, sum wx^2]; NaN when a term is NaN or infinities
+    of both signs meet, +-inf for infinities of one sign."""
+    assert len(axes) == 1
+    x = np.asarray(values, dtype=np.float64).reshape(-1)
+    w = np.ones_like(x) if weights is None else np.asarray(weights, dtype=np.float64)
+    b = locate(axes, x.reshape(1, -1))
+    nb = nbins_total(axes)
+    m = np.ones(x.shape[0], dtype=bool) if stat_overflows else (b >= 1) & (b <= nb - 2)
+    x, w = x[m], w[m]
+    with np.errstate(all="ignore"):
+        wx = w * x
+        terms = [w, w * w, wx, wx * x]
+    out = []
+    for t in terms:
+        if np.isnan(t).any() or (np.isposinf(t).any() and np.isneginf(t).any()):
+            out.append(math.nan)
+        elif np.isposinf(t).any():
+            out.append(math.inf)
+        elif np.isneginf(t).any():
+            out.append(-math.inf)
+        else:
+            out.append(math.fsum(t.tolist()))
+    return out
 
 
 # Filter/Define operation codes (the library's HIST_DEF_* / HIST_FLT_*).

@@ -37,6 +37,7 @@ HIST_AXIS_VARIABLE = 1
 HIST_TRACK_COUNTS = 1 << 0
 HIST_STAT_OVERFLOWS = 1 << 1
 HIST_SUMW2 = 1 << 2
+HIST_STATS_EXACT = 1 << 3
 HIST_PREC_FP64 = 0 << 4
 HIST_PREC_FP32C = 1 << 4
 HIST_PREC_F64ATOMIC = 2 << 4

@@ -36,6 +36,7 @@ constexpr int64_t kHostGraphBulk = 1 << 20;      // bulks up to this size replay
 constexpr int64_t kHostGraphBulks = 4096;        // ... when there are at most this many
 constexpr int kBucketMax = 1 << 22;             // buckets of one axis at most
 constexpr int kBucketMaxRun = 16;               // most thresholds in one bucket for LOC_BUCKET
+constexpr size_t kExactBytes = (size_t)kExactStats * (kExactLimbs + kEscapeLimbs + 3) * 8;
 #ifndef HGB_SMEM_BINS_BUDGET
 #define HGB_SMEM_BINS_BUDGET (96 * 1024)
 #endif
@@ -80,6 +81,10 @@ struct hist {
   double* g_f64 = nullptr;
   double* g_sumw2 = nullptr;  // HIST_SUMW2: binary64 per-bin sum of w^2 of weighted fills
   unsigned long long* g_passed = nullptr;  // entries of filtered fills (counted on the device)
+  // HIST_STATS_EXACT: limbs, escape limbs and special-term counts of the 4 statistics
+  long long* d_exact = nullptr;
+  int32_t exact_grid[kExactStats] = {0, 0, 0, 0};
+  int64_t exact_launches = 0;
   double* g_stats = nullptr;
   int64_t n_entries = 0;
   bool counts_complete = true;  // false once a weighted fill ran without HIST_TRACK_COUNTS
@@ -157,6 +162,7 @@ void free_state(hist* h) {
   cudaFree(h->g_stats);
   cudaFree(h->g_sumw2);
   cudaFree(h->g_passed);
+  cudaFree(h->d_exact);
   cudaFree(h->part_sumw2);
   cudaFree(h->part_bins);
   cudaFree(h->part_stats);
@@ -317,6 +323,23 @@ int fill_impl(hist* h, const double* values, const double* weights, int64_t n, c
   r.part_sumw2 = sw2_shared ? h->part_sumw2 : nullptr;
   r.g_sumw2 = h->g_sumw2;
   if (launch_reduce(r, stream) != 0) return HIST_ERR_CUDA;
+  if (h->d_exact != nullptr) {
+    if (ex != nullptr) return HIST_ERR_UNSUPPORTED;
+    ExactParams e;
+    std::memset(&e, 0, sizeof(e));
+    e.x = values;
+    e.w = weights;
+    e.n = n;
+    e.lo_key = h->T_host[0][1];
+    e.hi_key = h->T_host[0][h->nbins[0] + 1];
+    e.stat_overflows = (h->flags & HIST_STAT_OVERFLOWS) ? 1 : 0;
+    for (int k = 0; k < kExactStats; ++k) e.grid[k] = h->exact_grid[k];
+    e.limbs = h->d_exact;
+    e.escape = h->d_exact + kExactStats * kExactLimbs;
+    e.special = reinterpret_cast<unsigned long long*>(h->d_exact + kExactStats * (kExactLimbs + kEscapeLimbs));
+    if (launch_stats_exact(e, weights == nullptr, h->sm_count, stream) != 0) return HIST_ERR_CUDA;
+    if (++h->exact_launches % 1024 == 0 && launch_exact_normalise(h->d_exact, stream) != 0) return HIST_ERR_CUDA;
+  }
   if (acc == ACC_FX && !p.smem_bins) {
     h->fx_global_since_norm += n;
     if (h->fx_global_since_norm > (int64_t)1 << 31) {
@@ -479,7 +502,8 @@ const char* hist_strerror(int code) {
 int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
   if (out == nullptr || axes == nullptr || ndim < 1 || ndim > kMaxDim) return HIST_ERR_ARG;
   *out = nullptr;
-  const uint32_t known = HIST_TRACK_COUNTS | HIST_STAT_OVERFLOWS | HIST_SUMW2 | HIST_PREC_MASK | HIST_LOCATOR_MASK;
+  const uint32_t known =
+      HIST_TRACK_COUNTS | HIST_STAT_OVERFLOWS | HIST_SUMW2 | HIST_STATS_EXACT | HIST_PREC_MASK | HIST_LOCATOR_MASK;
   if (flags & ~known) return HIST_ERR_ARG;
   if ((flags & HIST_PREC_MASK) == (3u << 4)) return HIST_ERR_ARG;
   if ((flags & HIST_LOCATOR_MASK) > HIST_LOCATOR_BSEARCH) return HIST_ERR_ARG;
@@ -612,6 +636,26 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
     if ((rc = dalloc(&h->g_stats, kMaxStats * sizeof(double))) != HIST_OK) break;
     if ((flags & HIST_SUMW2) && (rc = dalloc(&h->g_sumw2, nb * 8)) != HIST_OK) break;
     if ((rc = dalloc(&h->g_passed, 8)) != HIST_OK) break;
+    if (flags & HIST_STATS_EXACT) {
+      if (ndim != 1) {
+        rc = HIST_ERR_UNSUPPORTED;
+        break;
+      }
+      if ((rc = dalloc(&h->d_exact, kExactBytes)) != HIST_OK) break;
+      // grids: the statistic's largest expected term 2^T (|w| < 2^16, |x| < 2^X
+      // over the in-range coordinates) sets its 127-binade fast window
+      const double lo = axes[0].kind == HIST_AXIS_FIXED ? axes[0].xmin : axes[0].edges[0];
+      const double hi = axes[0].kind == HIST_AXIS_FIXED ? axes[0].xmax : axes[0].edges[axes[0].nbins];
+      int X = 64;
+      if (!(flags & HIST_STAT_OVERFLOWS)) {
+        int e = 0;
+        std::frexp(std::max(std::fabs(lo), std::fabs(hi)), &e);
+        X = e;  // |x| < 2^e
+      }
+      const int Wb = 16;
+      const int T[kExactStats] = {Wb, 2 * Wb, Wb + X, Wb + 2 * X};
+      for (int k = 0; k < kExactStats; ++k) h->exact_grid[k] = std::max(T[k] - 52 - kExactFastTop, -1074);
+    }
     if (cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess) {
       rc = HIST_ERR_CUDA;
       break;
@@ -637,7 +681,8 @@ int hist_reset(hist_t* h) {
       cudaMemset(h->g_f64, 0, nb * 8) != cudaSuccess ||
       cudaMemset(h->g_stats, 0, kMaxStats * sizeof(double)) != cudaSuccess ||
       (h->g_sumw2 != nullptr && cudaMemset(h->g_sumw2, 0, nb * 8) != cudaSuccess) ||
-      cudaMemset(h->g_passed, 0, 8) != cudaSuccess)
+      cudaMemset(h->g_passed, 0, 8) != cudaSuccess ||
+      (h->d_exact != nullptr && cudaMemset(h->d_exact, 0, kExactBytes) != cudaSuccess))
     return HIST_ERR_CUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return HIST_ERR_CUDA;
   h->n_entries = 0;
@@ -692,7 +737,8 @@ int hist_fill_host(hist_t* h, const double* values, const double* weights, int64
   // small bulks are launch-bound: replay the whole pipelined fill as one
   // CUDA graph (exact integer bins in shared memory only: the global
   // fixed-point path needs host-side overflow bookkeeping per fill)
-  const bool graph = bulk <= kHostGraphBulk && smem && (n + bulk - 1) / bulk <= kHostGraphBulks;
+  const bool graph = bulk <= kHostGraphBulk && smem && (n + bulk - 1) / bulk <= kHostGraphBulks &&
+                     h->d_exact == nullptr;  // exact statistics keep host-side launch counts
   if (!graph) return pipeline_enqueue(h, values, weights, n, bulk, s);
   if (h->host_exec == nullptr || h->g_values != values || h->g_weights != weights || h->g_n != n ||
       h->g_bulk != bulk) {
@@ -813,6 +859,16 @@ int hist_result(hist_t* h, double* bins, double* stats) {
     s[1] = (double)sel_fx * lsb + (sel_f64 + sel_c);
     // unit-weight entries add 1 each to sum w^2
     s[2] += (double)sel_unit;
+    if (h->d_exact != nullptr) {  // the exact sums of the rounded terms, rounded once
+      std::vector<long long> ex(kExactBytes / 8);
+      if (cudaMemcpy(ex.data(), h->d_exact, kExactBytes, cudaMemcpyDeviceToHost) != cudaSuccess) return HIST_ERR_CUDA;
+      const long long* limbs = ex.data();
+      const long long* esc = limbs + kExactStats * kExactLimbs;
+      const unsigned long long* sp =
+          reinterpret_cast<const unsigned long long*>(esc + kExactStats * kEscapeLimbs);
+      for (int k = 0; k < kExactStats; ++k)
+        s[1 + k] = exact_round(limbs + k * kExactLimbs, h->exact_grid[k], esc + k * kEscapeLimbs, sp + 3 * k);
+    }
     for (int k = 0; k < h->nstats; ++k) stats[k] = s[k];
   }
   return HIST_OK;
@@ -838,7 +894,7 @@ int hist_fill_columns(hist_t* h, const double* const* cols, int ncols, const his
   if (h == nullptr || n < 0 || ncols < 1 || ncols > kExprMaxSrc || cols == nullptr || defines == nullptr ||
       nfilters < 0 || nfilters > kExprMaxFilters || (nfilters > 0 && filters == nullptr))
     return HIST_ERR_ARG;
-  if (h->ndim > 2 || (h->flags & HIST_SUMW2)) return HIST_ERR_UNSUPPORTED;
+  if (h->ndim > 2 || (h->flags & (HIST_SUMW2 | HIST_STATS_EXACT))) return HIST_ERR_UNSUPPORTED;
   ExprDev ex;
   std::memset(&ex, 0, sizeof(ex));
   ex.nsrc = ncols;
@@ -1650,7 +1706,7 @@ extern "C" int hist_batch_create(hist_t* const* hists, int nh, const int32_t* co
   for (int i = 0; i < nh; ++i) {
     if (hists[i] == nullptr || col_of_hist[i] < 0 || col_of_hist[i] >= kBatchMaxCols) return HIST_ERR_ARG;
     if (hists[i]->ndim != 1) return HIST_ERR_UNSUPPORTED;
-    if (hists[i]->flags & HIST_SUMW2) return HIST_ERR_UNSUPPORTED;
+    if (hists[i]->flags & (HIST_SUMW2 | HIST_STATS_EXACT)) return HIST_ERR_UNSUPPORTED;
     if (hists[i]->device != hists[0]->device) return HIST_ERR_ARG;
     if ((hists[i]->flags & HIST_STAT_OVERFLOWS) != stat_flag) return HIST_ERR_UNSUPPORTED;
     for (int j = 0; j < i; ++j)

@@ -98,6 +98,30 @@ struct ExprDev {
   unsigned long long* g_passed;  // events that passed the filters (entry count)
 };
 
+// Exactly summed statistics (HIST_STATS_EXACT, 1D): see stats_exact.cu.
+constexpr int kExactStats = 4;     // sum w, sum w^2, sum wx, sum wx^2
+constexpr int kExactLimbs = 6;     // radix-2^32 limbs per statistic
+constexpr int kExactFastTop = 32 * (kExactLimbs - 2) - 1;  // largest bit offset of a term's lowest bit
+constexpr int kEscapeLimbs = 72;   // limbs of the escape accumulator (every finite double)
+constexpr int kEscapeBias = 1100;  // its lowest limb is 2^-1100
+struct ExactParams {
+  const double* x;
+  const double* w;              // nullptr: unit weights
+  long long n;
+  long long lo_key, hi_key;     // the in-range keys [T[1], T[nbins+1])
+  int32_t stat_overflows;
+  int32_t grid[kExactStats];    // each statistic's grid exponent
+  long long* limbs;             // [kExactStats][kExactLimbs]
+  long long* escape;            // [kExactStats][kEscapeLimbs]
+  unsigned long long* special;  // [kExactStats][3]: NaN, +inf, -inf terms
+};
+int launch_stats_exact(const ExactParams& p, bool unit, int sm_count, void* stream);
+int launch_exact_normalise(long long* limbs, void* stream);
+
+// The exact value of sum_j limbs[j] 2^(32 j + grid) + sum_k esc[k] 2^(32 k - kEscapeBias),
+// rounded once to binary64 (nearest, ties to even), with the special-term counts.
+double exact_round(const long long* limbs, int grid, const long long* esc, const unsigned long long* special);
+
 struct FillParams {
   AxisDev ax[kMaxDim];
   ExprDev ex;                   // used by the expression kernels only

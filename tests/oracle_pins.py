@@ -455,6 +455,29 @@ def check_define_filter_vs_python_loops(seed=11):
         assert all(m[i] == fn(float(x[i])) for i in range(300))
 
 
+def check_exact_stats_vs_fractions(seed=12):
+    """The exact statistics against exact rational sums of the same rounded
+    terms (fractions.Fraction), rounded once by float(); specials."""
+    rng = np.random.default_rng(seed)
+    axes = [oracle_axis_fixed(10, -2.0, 2.0)]
+    x = rng.normal(0, 1.2, 400)
+    w = rng.uniform(-3, 3, 400) * 10.0 ** rng.integers(-12, 12, 400)
+    got = oracle.exact_stats(axes, x, w)
+    g = oracle.locate(axes, x.reshape(1, -1))
+    m = (g >= 1) & (g <= 10)
+    xs, ws = x[m].tolist(), w[m].tolist()
+    terms = [ws, [a * a for a in ws], [a * b for a, b in zip(ws, xs)], [(a * b) * b for a, b in zip(ws, xs)]]
+    for k in range(4):
+        want = float(sum(Fraction(t) for t in terms[k]))
+        assert got[k] == want, (k, got[k], want)
+    w2 = w.copy()
+    w2[int(np.flatnonzero(m)[0])] = math.nan
+    assert all(math.isnan(v) for v in oracle.exact_stats(axes, x, w2))
+    w3 = w.copy()
+    w3[int(np.flatnonzero(m)[1])] = math.inf
+    assert oracle.exact_stats(axes, x, w3)[0] == math.inf
+
+
 ALL_CHECKS = [
     check_golden_fixed, check_golden_variable, check_fixed_dyadic_exact,
     check_fixed_vs_rational, check_fixed_centres, check_fixed_range_edges,
@@ -463,4 +486,5 @@ ALL_CHECKS = [
     check_golden_fill, check_fill_counts_vs_numpy, check_fill_sums_vs_library,
     check_stats_vs_fsum, check_stats_closed_form_centres, check_flows_and_specials,
     check_fills_accumulate, check_sumw2_vs_bincount, check_define_filter_vs_python_loops,
+    check_exact_stats_vs_fractions,
 ]
