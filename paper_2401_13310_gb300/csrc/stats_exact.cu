@@ -56,8 +56,14 @@ __device__ __forceinline__ void exact_add(Limbs& L, double t, int g, const Exact
       a1 = -a1;
       a2 = -a2;
     }
-#pragma unroll
-    for (int j = 0; j < kExactLimbs; ++j) L.v[j] += (j == l ? a0 : 0) + (j == l + 1 ? a1 : 0) + (j == l + 2 ? a2 : 0);
+    // the terms of one statistic share their magnitude, so l is nearly
+    // always the same across a warp: a branch per limb offset is cheap
+    switch (l) {
+      case 0: L.v[0] += a0; L.v[1] += a1; L.v[2] += a2; break;
+      case 1: L.v[1] += a0; L.v[2] += a1; L.v[3] += a2; break;
+      case 2: L.v[2] += a0; L.v[3] += a1; L.v[4] += a2; break;
+      default: L.v[3] += a0; L.v[4] += a1; L.v[5] += a2; break;
+    }
     return;
   }
   // escape: an exact add at the term's own position among the 2^-1100 limbs
