@@ -239,6 +239,32 @@ __device__ __forceinline__ void ff_acc(FF& s, FF t) {
   s.hi = sum;
 }
 
+// The same double-word arithmetic on two independent lanes at once, with
+// Blackwell's packed FP32x2 instructions (two events per instruction; per
+// lane the numerics are exactly those of the scalar forms above: a - b is
+// computed as fma(b, -1, a), one rounding).
+struct FF2 {
+  float2 hi, lo;
+};
+
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+
+__device__ __forceinline__ FF2 ff2_mul(FF2 a, FF2 b) {
+  const float2 p = __fmul2_rn(a.hi, b.hi);
+  float2 e = __ffma2_rn(a.hi, b.hi, __fmul2_rn(p, make_float2(-1.0f, -1.0f)));
+  e = __ffma2_rn(a.hi, b.lo, e);
+  e = __ffma2_rn(a.lo, b.hi, e);
+  return {p, e};
+}
+
+__device__ __forceinline__ void ff2_acc(FF2& s, FF2 t) {
+  const float2 sum = __fadd2_rn(s.hi, t.hi);
+  const float2 bp = f2_sub(sum, s.hi);
+  const float2 err = __fadd2_rn(f2_sub(s.hi, f2_sub(sum, bp)), f2_sub(t.hi, bp));
+  s.lo = __fadd2_rn(s.lo, __fadd2_rn(t.lo, err));
+  s.hi = sum;
+}
+
 // Exact FP32 -> binary64 widening with integer operations (the conversion
 // instruction runs on the binary64 pipe at half its add rate).  Normal
 // values and zeros only; the double-word parts here are never subnormal.

@@ -72,54 +72,52 @@ struct NStats {
 template <int NDIM, bool UNIT>
 struct StatAcc {
   static constexpr int NS = NStats<NDIM>::NS;
-  FF s[NS];      // double-word partial sums of slots 3.. (slots 0-2 unused)
+  FF2 s[NS];     // double-word partial sums of slots 3.. on two lanes (the two events of a pair)
   double d[NS];  // binary64 sums, refreshed every flush
   double w2;     // sum w^2, one binary64 FMA per event (weighted fills)
 
   __device__ __forceinline__ void init() {
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-      s[k].hi = 0.0f;
-      s[k].lo = 0.0f;
+      s[k].hi = make_float2(0.0f, 0.0f);
+      s[k].lo = make_float2(0.0f, 0.0f);
       d[k] = 0.0;
     }
     w2 = 0.0;
   }
 
-  // Coordinates (and weight) already split; wb = the weight's bits.
-  __device__ __forceinline__ void add_ff(const FF* c, FF W, unsigned long long wb) {
+  // Coordinates and weight of two events, already split and packed (a lane
+  // whose event takes no part is all zeros: it adds exact zeros).
+  __device__ __forceinline__ void add_ff2(const FF2* c, FF2 W) {
     if (UNIT) {
-      ff_acc(s[3], c[0]);
-      ff_acc(s[4], ff_mul(c[0], c[0]));
+      ff2_acc(s[3], c[0]);
+      ff2_acc(s[4], ff2_mul(c[0], c[0]));
       if (NDIM >= 2) {
-        ff_acc(s[5], c[1]);
-        ff_acc(s[6], ff_mul(c[1], c[1]));
-        ff_acc(s[7], ff_mul(c[0], c[1]));
+        ff2_acc(s[5], c[1]);
+        ff2_acc(s[6], ff2_mul(c[1], c[1]));
+        ff2_acc(s[7], ff2_mul(c[0], c[1]));
       }
       if (NDIM >= 3) {
-        ff_acc(s[8], c[2]);
-        ff_acc(s[9], ff_mul(c[2], c[2]));
-        ff_acc(s[10], ff_mul(c[0], c[2]));
-        ff_acc(s[11], ff_mul(c[1], c[2]));
+        ff2_acc(s[8], c[2]);
+        ff2_acc(s[9], ff2_mul(c[2], c[2]));
+        ff2_acc(s[10], ff2_mul(c[0], c[2]));
+        ff2_acc(s[11], ff2_mul(c[1], c[2]));
       }
     } else {
-      // the binary64 pipe is otherwise idle: w^2 costs one issue slot there
-      const double w = __longlong_as_double((long long)wb);
-      w2 = __fma_rn(w, w, w2);
-      const FF WX = ff_mul(W, c[0]);
-      ff_acc(s[3], WX);
-      ff_acc(s[4], ff_mul(WX, c[0]));
+      const FF2 WX = ff2_mul(W, c[0]);
+      ff2_acc(s[3], WX);
+      ff2_acc(s[4], ff2_mul(WX, c[0]));
       if (NDIM >= 2) {
-        const FF WY = ff_mul(W, c[1]);
-        ff_acc(s[5], WY);
-        ff_acc(s[6], ff_mul(WY, c[1]));
-        ff_acc(s[7], ff_mul(WX, c[1]));
+        const FF2 WY = ff2_mul(W, c[1]);
+        ff2_acc(s[5], WY);
+        ff2_acc(s[6], ff2_mul(WY, c[1]));
+        ff2_acc(s[7], ff2_mul(WX, c[1]));
         if (NDIM >= 3) {
-          const FF WZ = ff_mul(W, c[2]);
-          ff_acc(s[8], WZ);
-          ff_acc(s[9], ff_mul(WZ, c[2]));
-          ff_acc(s[10], ff_mul(WX, c[2]));
-          ff_acc(s[11], ff_mul(WY, c[2]));
+          const FF2 WZ = ff2_mul(W, c[2]);
+          ff2_acc(s[8], WZ);
+          ff2_acc(s[9], ff2_mul(WZ, c[2]));
+          ff2_acc(s[10], ff2_mul(WX, c[2]));
+          ff2_acc(s[11], ff2_mul(WY, c[2]));
         }
       }
     }
@@ -128,9 +126,10 @@ struct StatAcc {
   __device__ __forceinline__ void flush() {
 #pragma unroll
     for (int k = 3; k < NS; ++k) {
-      d[k] = __dadd_rn(d[k], ff_to_double(s[k]));
-      s[k].hi = 0.0f;
-      s[k].lo = 0.0f;
+      const FF a = {s[k].hi.x, s[k].lo.x}, b = {s[k].hi.y, s[k].lo.y};
+      d[k] = __dadd_rn(d[k], __dadd_rn(ff_to_double(a), ff_to_double(b)));
+      s[k].hi = make_float2(0.0f, 0.0f);
+      s[k].lo = make_float2(0.0f, 0.0f);
     }
   }
 };
@@ -255,7 +254,13 @@ struct Filler {
       sumw2_global(p.g_sumw2, g, wb);
   }
 
-  __device__ __forceinline__ void event(const unsigned long long* cb, unsigned long long wb) {
+  // Whether an event enters the statistics, and through the double-word path.
+  struct StatIn {
+    bool take, fast;
+  };
+
+  // Steps 1 and 2 of one event (and its w^2 for HIST_SUMW2).
+  __device__ __forceinline__ StatIn bin_step(const unsigned long long* cb, unsigned long long wb) {
     // ---- step 1: the bin on every axis, linearised x fastest
     float xf[NDIM];
     unsigned ef[NDIM];
@@ -345,26 +350,96 @@ struct Filler {
     }
     // ---- per-bin sum of w^2 (ROOT's Sumw2)
     if (SW2) sumw2_add(g, wb);
-    // ---- step 3: statistics
-    if (!(inr || p.stat_overflows)) return;
+    StatIn si;
+    si.take = inr || p.stat_overflows;
     bool fast = (ACC != ACC_F64) && w_ok;
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) fast = fast && in_ff(ef[d]);
-    if (fast) {
-      FF cf[NDIM];
-#pragma unroll
-      for (int d = 0; d < NDIM; ++d) cf[d] = ff_split(cb[d], xf[d]);
-      FF W;
-      if (UNIT) {
-        W.hi = 1.0f;
-        W.lo = 0.0f;
-      } else {
-        W = ff_split(wb, hi24(wb));  // in-window weights lie in the double-word range
-      }
-      st.add_ff(cf, W, wb);
-    } else {
-      stat_f64<NDIM, UNIT>(slow, cb, wb);
+    si.fast = fast;
+    return si;
+  }
+
+  // ---- step 3: statistics of two events; the double-word sums run on two
+  // lanes of the packed FP32x2 instructions, one lane per event
+  __device__ __forceinline__ void stats2(const unsigned long long* ca, unsigned long long wa, StatIn ia,
+                                         const unsigned long long* cb, unsigned long long wb, StatIn ib) {
+    if (ia.take && !ia.fast) stat_f64<NDIM, UNIT>(slow, ca, wa);
+    if (ib.take && !ib.fast) stat_f64<NDIM, UNIT>(slow, cb, wb);
+    const bool fa = ia.take && ia.fast, fb = ib.take && ib.fast;
+    if constexpr (NDIM == 1) {
+      // 1D: the integer work, not the FP32 pipe, bounds the kernel; each
+      // event runs the scalar double-word forms on its own lane
+      if (fa) stat1(ca[0], wa, 0);
+      if (fb) stat1(cb[0], wb, 1);
+      return;
     }
+    if (!(fa || fb)) return;
+    FF2 c2[NDIM];
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+      const FF xa = ff_split(ca[d], hi24(ca[d])), xb = ff_split(cb[d], hi24(cb[d]));
+      c2[d].hi = make_float2(fa ? xa.hi : 0.0f, fb ? xb.hi : 0.0f);
+      c2[d].lo = make_float2(fa ? xa.lo : 0.0f, fb ? xb.lo : 0.0f);
+    }
+    FF2 W2;
+    if (UNIT) {
+      W2.hi = make_float2(fa ? 1.0f : 0.0f, fb ? 1.0f : 0.0f);
+      W2.lo = make_float2(0.0f, 0.0f);
+    } else {
+      // in-window weights lie in the double-word range
+      const FF a = ff_split(wa, hi24(wa)), b = ff_split(wb, hi24(wb));
+      W2.hi = make_float2(fa ? a.hi : 0.0f, fb ? b.hi : 0.0f);
+      W2.lo = make_float2(fa ? a.lo : 0.0f, fb ? b.lo : 0.0f);
+      // the binary64 pipe is otherwise idle: w^2 costs one issue slot there
+      const double da = fa ? __longlong_as_double((long long)wa) : 0.0;
+      const double db = fb ? __longlong_as_double((long long)wb) : 0.0;
+      st.w2 = __fma_rn(da, da, st.w2);
+      st.w2 = __fma_rn(db, db, st.w2);
+    }
+    st.add_ff2(c2, W2);
+  }
+
+  // One 1D event into lane `lane` of the double-word sums (scalar forms).
+  __device__ __forceinline__ void stat1(unsigned long long xb, unsigned long long wb, int lane) {
+    const FF X = ff_split(xb, hi24(xb));
+    FF W;
+    if (UNIT) {
+      W.hi = 1.0f;
+      W.lo = 0.0f;
+    } else {
+      W = ff_split(wb, hi24(wb));
+      const double w = __longlong_as_double((long long)wb);
+      st.w2 = __fma_rn(w, w, st.w2);
+    }
+    FF s3 = lane ? FF{st.s[3].hi.y, st.s[3].lo.y} : FF{st.s[3].hi.x, st.s[3].lo.x};
+    FF s4 = lane ? FF{st.s[4].hi.y, st.s[4].lo.y} : FF{st.s[4].hi.x, st.s[4].lo.x};
+    const FF WX = UNIT ? X : ff_mul(W, X);
+    ff_acc(s3, WX);
+    ff_acc(s4, ff_mul(WX, X));
+    if (lane) {
+      st.s[3].hi.y = s3.hi; st.s[3].lo.y = s3.lo;
+      st.s[4].hi.y = s4.hi; st.s[4].lo.y = s4.lo;
+    } else {
+      st.s[3].hi.x = s3.hi; st.s[3].lo.x = s3.lo;
+      st.s[4].hi.x = s4.hi; st.s[4].lo.x = s4.lo;
+    }
+  }
+
+  __device__ __forceinline__ void event(const unsigned long long* cb, unsigned long long wb) {
+    const StatIn i = bin_step(cb, wb);
+    stats2(cb, wb, i, cb, wb, StatIn{false, false});
+  }
+
+  __device__ __forceinline__ void event_pair(const unsigned long long* c0, unsigned long long w0,
+                                             const unsigned long long* c1, unsigned long long w1) {
+    if constexpr (NDIM == 1) {  // one event after the other, as scalar code schedules best
+      event(c0, w0);
+      event(c1, w1);
+      return;
+    }
+    const StatIn i0 = bin_step(c0, w0);
+    const StatIn i1 = bin_step(c1, w1);
+    stats2(c0, w0, i0, c1, w1, i1);
   }
 };
 
@@ -417,8 +492,7 @@ __device__ __forceinline__ void fill_pairs(Filler<NDIM, ACC, SMEM, LOC, SW2>& f,
       for (int d = 0; d < NDIM; ++d) load_pair<VEC>(p.col[d], 2 * qn, n0[d], n1[d]);
       if (ACC != ACC_UNIT) load_pair<VEC>(p.w, 2 * qn, nw0, nw1);
     }
-    f.event(c0, w0);
-    f.event(c1, w1);
+    f.event_pair(c0, w0, c1, w1);
     if (++iters == kFlushIters) {
       f.st.flush();
       iters = 0;
