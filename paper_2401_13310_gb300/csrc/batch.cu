@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256, MINB) k_batch_fill(const __grid_constant_
       }
       // every histogram of this column
       for (int h = p.col_begin[c]; h < p.col_begin[c + 1]; ++h) {
-        const BatchHistDev d = sdesc[h];  // a copy: the shared bins' atomics cannot alias it
+        const BatchHistDev& d = sdesc[h];  // read in place: its fields load as they are used
         const bool staged = d.ax.smem_off >= 0;
         const long long* T = staged ? skeys + d.ax.smem_off : d.ax.T;
         const int* Thi = staged ? shi + d.ax.smem_off : nullptr;
