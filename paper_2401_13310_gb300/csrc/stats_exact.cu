@@ -98,19 +98,44 @@ __global__ void __launch_bounds__(kThreads, 2) k_stats_exact(const __grid_consta
   unsigned long long special[kExactStats][3] = {};
   const unsigned long long* xq = reinterpret_cast<const unsigned long long*>(p.x);
   const unsigned long long* wq = reinterpret_cast<const unsigned long long*>(p.w);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const unsigned long long xb = __ldcs(xq + i);
+  auto one = [&](unsigned long long xb, unsigned long long wb) {
     const long long key = key_of(xb);
-    if (!p.stat_overflows && !(key >= p.lo_key && key < p.hi_key)) continue;
+    if (!p.stat_overflows && !(key >= p.lo_key && key < p.hi_key)) return;
     const double x = __longlong_as_double((long long)xb);
-    const double w = UNIT ? 1.0 : __longlong_as_double((long long)__ldcs(wq + i));
+    const double w = UNIT ? 1.0 : __longlong_as_double((long long)wb);
     const double wx = UNIT ? x : __dmul_rn(w, x);
     exact_add(acc[0], w, p.grid[0], p, 0, special[0]);
     exact_add(acc[1], UNIT ? 1.0 : __dmul_rn(w, w), p.grid[1], p, 1, special[1]);
     exact_add(acc[2], wx, p.grid[2], p, 2, special[2]);
     exact_add(acc[3], __dmul_rn(wx, x), p.grid[3], p, 3, special[3]);
+  };
+  // pairs of events, the next pair's loads in flight while this one is added
+  const long long npairs = p.n >> 1;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  unsigned long long x0 = 0, x1 = 0, w0 = 0, w1 = 0;
+  auto load = [&](long long k, unsigned long long& a, unsigned long long& b, unsigned long long& c,
+                  unsigned long long& d) {
+    a = __ldcs(xq + 2 * k);
+    b = __ldcs(xq + 2 * k + 1);
+    if (!UNIT) {
+      c = __ldcs(wq + 2 * k);
+      d = __ldcs(wq + 2 * k + 1);
+    }
+  };
+  if (q < npairs) load(q, x0, x1, w0, w1);
+  for (; q < npairs; q += stride) {
+    unsigned long long nx0 = 0, nx1 = 0, nw0 = 0, nw1 = 0;
+    if (q + stride < npairs) load(q + stride, nx0, nx1, nw0, nw1);
+    one(x0, w0);
+    one(x1, w1);
+    x0 = nx0;
+    x1 = nx1;
+    w0 = nw0;
+    w1 = nw1;
   }
+  if ((p.n & 1) && blockIdx.x == 0 && threadIdx.x == 0)
+    one(__ldcs(xq + p.n - 1), UNIT ? 0ull : __ldcs(wq + p.n - 1));
   // normalise, then sum over the warp, the block and the grid (exact integers)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
