@@ -139,6 +139,21 @@ __device__ __forceinline__ int locate_bucket(const AxisDev& a, const long long* 
   return k + pos;
 }
 
+// LOC_LEARNED: the trained index model's bin k0 when its two thresholds
+// bracket the key (most events), else an exact search of the certified
+// window around it; -1 when even the window misses (the caller then runs
+// the full binary search).
+__device__ __forceinline__ int locate_learned(const AxisDev& a, const long long* T, unsigned long long b,
+                                              long long key) {
+  const float kh = lm_eval(a.lm, est_float(b));
+  const int k0 = min(max((int)floorf(__fadd_rn(kh, 0.5f)), 0), a.nbins + 1);
+  if (T[k0] <= key && key < T[k0 + 1]) return k0;
+  const int lo = max(k0 - a.lm.window, 0);
+  const int hi = min(k0 + a.lm.window, a.nbins + 1);
+  if (T[lo] <= key && key < T[hi + 1]) return lo + bsearch_keys(T + lo, hi - lo + 1, key);
+  return -1;
+}
+
 // Bin of one coordinate on one axis (Sec. 3.1 step 1), exact.
 // xf: the coordinate as FP32 (hi24), valid when in_f32 of its exponent field.
 __device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T, const int* Thi, const int* cnt,
@@ -159,13 +174,8 @@ __device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T,
   const long long key = key_of(b);
   if (a.mode == LOC_BUCKET) return locate_bucket(a, T, cnt, b, key);
   if (a.mode == LOC_LEARNED) {
-    // the trained index model, then an exact search of the certified window;
-    // a window that does not bracket the key falls back to the full search
-    const float kh = lm_eval(a.lm, est_float(b));
-    const int k0 = (int)floorf(__fadd_rn(kh, 0.5f));
-    const int lo = max(k0 - a.lm.window, 0);
-    const int hi = min(k0 + a.lm.window, a.nbins + 1);
-    if (lo <= hi && T[lo] <= key && key < T[hi + 1]) return lo + bsearch_keys(T + lo, hi - lo + 1, key);
+    const int k = locate_learned(a, T, b, key);
+    if (k >= 0) return k;
   }
   if (Thi != nullptr) return bsearch_hi(T, Thi, a.nbins + 2, key);
   return bsearch_keys(T, a.nbins + 2, key);
@@ -191,11 +201,8 @@ __device__ __forceinline__ int locate_mode(const AxisDev& a, const long long* T,
   const long long key = key_of(b);
   if (LOC == LOC_BUCKET) return locate_bucket(a, T, cnt, b, key);
   if (LOC == LOC_LEARNED) {
-    const float kh = lm_eval(a.lm, est_float(b));
-    const int k0 = (int)floorf(__fadd_rn(kh, 0.5f));
-    const int lo = max(k0 - a.lm.window, 0);
-    const int hi = min(k0 + a.lm.window, a.nbins + 1);
-    if (lo <= hi && T[lo] <= key && key < T[hi + 1]) return lo + bsearch_keys(T + lo, hi - lo + 1, key);
+    const int k = locate_learned(a, T, b, key);
+    if (k >= 0) return k;
   }
   if (Thi != nullptr) return bsearch_hi(T, Thi, a.nbins + 2, key);
   return bsearch_keys(T, a.nbins + 2, key);
