@@ -225,11 +225,43 @@ def measure_filter_define(B, W, hbm: float, n: int) -> dict:
             "fused_hbm_frac": 16 * n / (fused * 1e-3) / 1e9 / hbm}
 
 
+def measure_paper_histo1d(B, W, hbm: float, n: int) -> dict:
+    """The paper's own benchmark shape (Sec. 4.2: Histo1D, 1000 bins on
+    [0,1], binary64 values uniform on [0,1], bulks of 32768 events, timed
+    from host data to the fetched result) at n events: device-resident
+    fill, and host-resident fills through the pipeline with the paper's
+    32768-event bulks and with 16M-event bulks, each ending in hist_result."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(21)
+    x = torch.rand(n, dtype=torch.float64, device="cuda", generator=g)
+    xh = x.cpu().pin_memory()
+    h = B.Hist([W.fixed(1000, 0.0, 1.0)])
+    res = {"events": n, "bins": 1000}
+    res["device_ms"] = _timed(lambda: h.fill(x), 5)
+
+    def host(bulk):
+        def run():
+            h.fill_host(xh, None, bulk=bulk)
+            h.result()
+        return run
+    res["host_bulk32768_ms"] = _timed(host(32768), 2)
+    res["host_bulk16M_ms"] = _timed(host(1 << 24), 3)
+    for k in ("device", "host_bulk32768", "host_bulk16M"):
+        res[k + "_gev_per_s"] = n / (res[k + "_ms"] * 1e-3) / 1e9
+    res["device_hbm_frac"] = 8 * n / (res["device_ms"] * 1e-3) / 1e9 / hbm
+    h.close()
+    del x, xh
+    torch.cuda.empty_cache()
+    return res
+
+
 def measure_forms(B, W, hbm: float, args) -> dict:
     """The batched and learned forms beside the plain one, same GPU."""
     import torch
     out = {"precision": measure_precisions(B, W, hbm, args.events),
-           "filter_define": measure_filter_define(B, W, hbm, args.events)}
+           "filter_define": measure_filter_define(B, W, hbm, args.events),
+           "paper_histo1d": measure_paper_histo1d(B, W, hbm, 2 * args.events)}
     # batched: 64 histograms (10 .. 1e5 bins, fixed and variable) on the
     # columns pT, phi, eta with binary64 weights
     n4 = args.batch_events
