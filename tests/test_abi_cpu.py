@@ -78,7 +78,23 @@ def test_host_argument_errors(lib):
     assert lib.hist_counts(None, None) == B.HIST_ERR_ARG
     assert lib.hist_reset(None) == B.HIST_ERR_ARG
     assert lib.hist_locate(None, None, 5, None, None) == B.HIST_ERR_ARG
+    assert lib.hist_fill_host(None, None, None, 10, 0, None) == B.HIST_ERR_ARG
+    assert lib.hist_fill_columns(None, None, 1, None, None, 0, None, 10, None) == B.HIST_ERR_ARG
+    assert lib.hist_sumw2(None, None) == B.HIST_ERR_ARG
+    assert lib.hist_locator_mode(None, 0) == B.HIST_ERR_ARG
+    assert lib.hist_set_kernel_timing(None, 1) == B.HIST_ERR_ARG
+    assert lib.hist_kernel_time(None, None, None) == B.HIST_ERR_ARG
+    assert lib.hist_batch_fill(None, None, 0, None, 10, None) == B.HIST_ERR_ARG
+    assert lib.hist_batch_tune(None, None, 0, None, 10, None) == B.HIST_ERR_ARG
+    assert lib.hist_batch_configure(None, 0, 1 << 16, 30, -1, 2, 4, None) == B.HIST_ERR_ARG
+    assert lib.hist_batch_create(None, 0, None, 0, None) == B.HIST_ERR_ARG
+    assert lib.hist_train_locator(None, 0, None, None) == B.HIST_ERR_ARG
+    lib.hist_batch_free(None)
     lib.hist_free(None)
+    for bad in (1 << 20, 3 << 8):  # an unknown flag; an unknown locator
+        with pytest.raises(B.HistError) as e:
+            B.hist_book([{"kind": "fixed", "nbins": 1, "xmin": 0.0, "xmax": 1.0}], flags=bad)
+        assert e.value.code == B.HIST_ERR_ARG
     with pytest.raises(B.HistError) as e:
         B.hist_book([{"kind": "fixed", "nbins": 1, "xmin": 0.0, "xmax": 1.0}], flags=1 << 20)
     assert e.value.code == B.HIST_ERR_ARG
