@@ -115,16 +115,25 @@ __device__ __noinline__ int locate_exact(const long long* T, int nbins, int k, u
 // is monotone and the host placed every threshold with the same arithmetic.
 __device__ __forceinline__ int locate_bucket(const AxisDev& a, const long long* T, const int* cnt,
                                              unsigned long long b, long long key) {
-  if (key < a.bk.lo_key) return 0;
-  if (key >= a.bk.hi_key) return a.nbins + 1;
   int bk;
-  if (a.bk.key_map) {
-    bk = (int)((key >> a.bk.shift) - a.bk.kbase);
+  if (a.bk.key_map && a.bk.shift > 0) {
+    // the key map is monotone over every key (NaN's included) and T[1]
+    // lies in bucket 0: clamped out-of-range keys land in the end buckets,
+    // whose counts and thresholds give 0 and nbins + 1 -- no range tests
+    long long q = (key >> a.bk.shift) - a.bk.kbase;
+    q = q < 0 ? 0 : (q > a.bk.nbk - 1 ? a.bk.nbk - 1 : q);
+    bk = (int)q;
   } else {
-    const float t = fminf(fmaxf(__fmaf_rn(est_float(b), a.bk.scale, a.bk.offset), -1.0f), (float)a.bk.nbk);
-    bk = __float2int_rd(t);
+    if (key < a.bk.lo_key) return 0;
+    if (key >= a.bk.hi_key) return a.nbins + 1;
+    if (a.bk.key_map) {
+      bk = (int)((key >> a.bk.shift) - a.bk.kbase);
+    } else {
+      const float t = fminf(fmaxf(__fmaf_rn(est_float(b), a.bk.scale, a.bk.offset), -1.0f), (float)a.bk.nbk);
+      bk = __float2int_rd(t);
+    }
+    bk = min(max(bk, 0), a.bk.nbk - 1);
   }
-  bk = min(max(bk, 0), a.bk.nbk - 1);
   if (a.bk.single) {
     const longlong2 e = reinterpret_cast<const longlong2*>(cnt)[bk];
     return (int)e.y + (key >= e.x ? 1 : 0);

@@ -231,8 +231,23 @@ FillParams make_params(const hist* h, const double* values, const double* weight
   return p;
 }
 
+// A captured host-pipeline graph holds the scratch pointers: drop it when
+// they move (it is captured again on its next use).
+void drop_host_graph(hist* h) {
+  if (h->host_exec) {
+    if (h->have_done) cudaEventSynchronize(h->done);
+    cudaGraphExecDestroy(h->host_exec);
+    h->host_exec = nullptr;
+  }
+}
+
 int ensure_scratch(hist* h, int grid, int acc, bool smem_bins) {
   const size_t need = smem_bins ? (size_t)grid * (size_t)h->nbins_total * part_bin_bytes(acc, 0) : 16;
+  const bool grows = need > h->part_bins_bytes || grid > h->part_stats_blocks ||
+                     ((smem_bins && (h->flags & HIST_SUMW2)) &&
+                      (size_t)grid * (size_t)h->nbins_total * 8 > h->part_sumw2_bytes);
+  if (grows && h->capturing) return HIST_ERR_CUDA;  // pipeline_prepare sized them before the capture
+  if (grows) drop_host_graph(h);
   if (need > h->part_bins_bytes) {
     cudaFree(h->part_bins);
     h->part_bins = nullptr;

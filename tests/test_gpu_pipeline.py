@@ -111,3 +111,31 @@ def test_fill_host_graph_replays_and_recaptures(B):
     assert stats[0] == ref.stats_acc[0]
     assert_sums_close(bins, ref.bins_acc, ref.bins_abs, RTOL, "bins")
     assert_sums_close(stats[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, "stats")
+
+
+def test_fill_host_graph_survives_scratch_growth(B):
+    """A replayed small-bulk graph holds the fill scratch; a larger device
+    fill in between grows that scratch, and the next host fill must be
+    captured anew (same results as plain fills)."""
+    import torch
+    wl = W.cfg2a(n=300_000)
+    v = torch.from_numpy(np.ascontiguousarray(wl.values[:, :100_000])).pin_memory()
+    w = torch.from_numpy(np.ascontiguousarray(wl.weights[:100_000])).pin_memory()
+    big_v = torch.from_numpy(np.ascontiguousarray(wl.values)).cuda()
+    big_w = torch.from_numpy(np.ascontiguousarray(wl.weights)).cuda()
+    h = B.Hist(wl.axes, B.HIST_TRACK_COUNTS)
+    try:
+        h.fill_host(v, w, bulk=32768)  # captured with small-launch scratch
+        h.fill(big_v, big_w)           # grows the scratch
+        h.fill_host(v, w, bulk=32768)  # same arguments: replay must not use the old scratch
+        torch.cuda.synchronize()
+        bins, stats = h.result()
+        counts = h.counts()
+    finally:
+        h.close()
+    allv = np.concatenate([wl.values[:, :100_000], wl.values, wl.values[:, :100_000]], axis=1)
+    allw = np.concatenate([wl.weights[:100_000], wl.weights, wl.weights[:100_000]])
+    ref = oracle.fill(wl.axes, allv, allw)
+    assert np.array_equal(counts, ref.counts)
+    assert_sums_close(bins, ref.bins_acc, ref.bins_abs, RTOL, "bins")
+    assert_sums_close(stats[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, "stats")
