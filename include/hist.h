@@ -288,7 +288,9 @@ typedef struct {
   int32_t events_per_thread; /* events each thread holds per pass over the histograms */
 } hist_batch_tuning_t;
 
-/* Autotune the batch: time the candidate strategies, shared-memory budgets
+/* Autotune the batch (for fills like the sample: a unit-weight sample lets
+ * the wide strategy keep one word per shared bin, which a later weighted
+ * fill widens again): time the candidate strategies, shared-memory budgets
  * (which histograms keep shared-memory bins; the slice size), blocks per SM,
  * events per thread and work caps per slice on the given sample of events, writing into scratch accumulators (the member histograms are not
  * changed), and keep the fastest for later fills.  Synchronous.  report may

@@ -1200,6 +1200,7 @@ struct hist_batch {
   int slice_replicas = 1, slice_window = 0;
   int pace_tiles = -1;                    // pacing window in tiles: -1 default, 0 off
   int wide_minb = 2, wide_kev = 4;        // wide: blocks per SM compiled for, events per thread
+  bool placed_unit = false;               // wide: shared bins placed at one word per bin (unit fills only)
   double slice_cap = 0.0;
   SliceDev* d_slices = nullptr;
   SliceFragDev* d_frags = nullptr;
@@ -1250,8 +1251,8 @@ void batch_place(hist_batch* b, int budget) {
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->hs[x]->nbins[0] < b->hs[y]->nbins[0]; });
   b->sbin_off.assign(nh, -1);
   int words = 0;
-  for (int i : order) {
-    const int need = 2 * (b->hs[i]->nbins[0] + 2);
+  for (int i : order) {  // one word per bin suffices for unit weights, two for fixed-point sums
+    const int need = (b->placed_unit ? 1 : 2) * (b->hs[i]->nbins[0] + 2);
     if ((long long)(words + need) * 4 > budget) break;
     b->sbin_off[i] = words;
     words += need;
@@ -1876,6 +1877,10 @@ extern "C" int hist_batch_fill(hist_batch_t* b, const double* const* cols, int n
       if (b->strategy == 1 && (rc = slice_upload(b)) != HIST_OK) return rc;
       break;
     }
+  if (weights != nullptr && b->placed_unit && b->strategy == 0) {  // bins placed for unit fills only
+    b->placed_unit = false;
+    if ((rc = batch_configure(b, b->smem_budget)) != HIST_OK) return rc;
+  }
   for (hist* h : b->hs)
     if ((rc = order_after_previous(h, s)) != HIST_OK) return rc;
   if ((rc = batch_reserve(b, n)) != HIST_OK) return rc;
@@ -1962,6 +1967,7 @@ extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int n
   if (cudaSetDevice(b->device) != cudaSuccess) return HIST_ERR_CUDA;
   for (hist* h : b->hs)
     if (h->have_done && cudaEventSynchronize(h->done) != cudaSuccess) return HIST_ERR_CUDA;
+  b->placed_unit = weights == nullptr;  // unit samples place one word per bin (a weighted fill re-places)
   // candidates: the wide strategy at five budgets, the sliced one at three
   // budgets times three work caps (unless the batch was created with a fixed
   // strategy)

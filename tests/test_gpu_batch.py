@@ -195,3 +195,31 @@ def test_batch_configurations_agree_exactly(B):
             assert np.array_equal(b0, b1), f"hist {i} bins differ between configurations"
             ref = oracle.fill([bw.axes[i]], bw.columns[bw.col_of_hist[i]].reshape(1, -1), bw.weights)
             assert_sums_close(s1[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, f"hist {i} stats")
+
+
+def test_batch_tuned_for_unit_then_weighted_fill(B):
+    """A batch tuned on a unit-weight sample keeps one word per shared bin;
+    a weighted fill afterwards re-places the bins (two words) and both fills
+    match the oracle."""
+    bw = W.cfg4(n=120_001)
+    hists = [B.Hist([ax]) for ax in bw.axes]
+    batch = None
+    try:
+        batch = B.Batch(hists, bw.col_of_hist, B.HIST_BATCH_WIDE)
+        cols = [to_device(np.ascontiguousarray(bw.columns[c])) for c in range(3)]
+        batch.tune(cols, None)
+        batch.fill(cols, None)
+        batch.fill(cols, to_device(bw.weights))
+        ones = np.ones(bw.n)
+        for i, (h, ax, c) in enumerate(zip(hists, bw.axes, bw.col_of_hist)):
+            bins, stats = h.result()
+            x2 = np.concatenate([bw.columns[c], bw.columns[c]]).reshape(1, -1)
+            w2 = np.concatenate([ones, bw.weights])
+            ref = oracle.fill([ax], x2, w2)
+            assert_sums_close(bins, ref.bins_acc, ref.bins_abs, RTOL, f"hist {i} bins")
+            assert_sums_close(stats[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, f"hist {i} stats")
+    finally:
+        if batch is not None:
+            batch.close()
+        for h in hists:
+            h.close()
