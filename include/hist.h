@@ -80,8 +80,9 @@ typedef struct {
  * rounded once to binary64 -- bit-reproducible whatever the launch shape,
  * the order of atomics or the split into fills, and equal to a correctly
  * rounded exact sum (math.fsum) of the same terms.  A second pass over
- * each bulk accumulates them in integer limbs (see the design notes); it
- * costs one more read of the bulk.  Not with hist_fill_columns or batches
+ * each bulk accumulates them in integer limbs on a per-statistic grid (an
+ * escape accumulator takes the terms outside it); it costs one more read
+ * of the bulk.  Not with hist_fill_columns or batches
  * (HIST_ERR_UNSUPPORTED); ND histograms: HIST_ERR_UNSUPPORTED at booking. */
 #define HIST_STATS_EXACT (1u << 3)
 /* Accumulation of weighted bin contents (bits 4-5):

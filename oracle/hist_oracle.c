@@ -20,8 +20,8 @@
  *   Sec. 3.2 (Native CUDA): in one dimension the statistics are four sums,
  *     the sum of weights, of squared weights, of weight*x and of weight*x^2.
  *
- * Readings taken where the paper is silent or ambiguous (each is one line of
- * the design notes' readings table):
+ * Readings taken where the paper is silent or ambiguous (R1-R9; each is
+ * pinned by the oracle's tests):
  *   R1  variable bins are lower-inclusive [e_j, e_{j+1}): bin = 1 + the index
  *       of the last edge <= x (an upper-bound search), which matches the
  *       fixed-width formula on its own edges.
