@@ -120,9 +120,17 @@ __device__ __forceinline__ int locate_bucket(const AxisDev& a, const long long* 
     // the key map is monotone over every key (NaN's included) and T[1]
     // lies in bucket 0: clamped out-of-range keys land in the end buckets,
     // whose counts and thresholds give 0 and nbins + 1 -- no range tests
-    long long q = (key >> a.bk.shift) - a.bk.kbase;
-    q = q < 0 ? 0 : (q > a.bk.nbk - 1 ? a.bk.nbk - 1 : q);
-    bk = (int)q;
+    if (a.bk.shift >= 32) {
+      // key >> shift and kbase are 32-bit values: the same map on the key's
+      // high word (the difference, after the lower clamp, is taken unsigned)
+      const int hk = (int)(key >> 32) >> (a.bk.shift - 32);
+      const int kb = (int)a.bk.kbase;
+      bk = (int)min((unsigned)max(hk, kb) - (unsigned)kb, (unsigned)(a.bk.nbk - 1));
+    } else {
+      long long q = (key >> a.bk.shift) - a.bk.kbase;
+      q = q < 0 ? 0 : (q > a.bk.nbk - 1 ? a.bk.nbk - 1 : q);
+      bk = (int)q;
+    }
   } else {
     if (key < a.bk.lo_key) return 0;
     if (key >= a.bk.hi_key) return a.nbins + 1;

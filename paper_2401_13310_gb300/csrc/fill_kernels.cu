@@ -56,7 +56,7 @@ namespace {
 #ifndef HGB_MIN_BLOCKS_1D
 #define HGB_MIN_BLOCKS_1D 4  // 1D kernels fit in 64 registers: four 256-thread blocks per SM
 #endif
-constexpr int kFlushIters = 32;  // two events per iteration: 64 events between binary64 flushes
+constexpr int kFlushIters = 32;  // pairs of events (64 events) between binary64 flushes
 
 // ---------------------------------------------------------------- statistics
 
@@ -196,6 +196,24 @@ __device__ __noinline__ void sumw2_shared(unsigned* words, double* g_sumw2, long
   atomicAdd(a + 1, __fadd_rn(err, pl));
 }
 
+// Signed fixed-point value V into a shared bin's low 64 bits (words a[0],
+// a[1]): a 96-bit add with carries.  Each atomic returns the old word, so the
+// carry it produced is known exactly whatever the interleaving; the rare
+// top-word change (a carry out of bit 63, or the sign of a negative addend
+// not absorbed by a carry) goes to the global high word, which holds the sum
+// in units of 2^32.  Out of line: the hot loop keeps the positive case only.
+__device__ __noinline__ void fx_add_shared(unsigned* a, long long* ghi, long long V) {
+  const unsigned v0 = (unsigned)V;
+  const unsigned o0 = atomicAdd(a, v0);
+  const unsigned c0 = (o0 + v0 < o0) ? 1u : 0u;
+  const unsigned a1 = (unsigned)((unsigned long long)V >> 32) + c0;
+  const unsigned c1a = (a1 < c0) ? 1u : 0u;
+  const unsigned o1 = atomicAdd(a + 1, a1);
+  const unsigned c1 = c1a | ((o1 + a1 < o1) ? 1u : 0u);
+  const int top = (int)(V >> 63) + (int)c1;
+  if (top != 0) atomicAdd(reinterpret_cast<unsigned long long*>(ghi), (unsigned long long)((long long)top << 32));
+}
+
 __device__ __noinline__ void f64_bin(double* bins, long long slot, unsigned long long wb) {
   atomicAdd(&bins[slot], __longlong_as_double((long long)wb));
 }
@@ -270,7 +288,9 @@ struct Filler {
     for (int d = 0; d < NDIM; ++d) {
       ef[d] = exp_field(cb[d]);
       xf[d] = hi24(cb[d]);
-      const int k = locate_mode<LOC>(p.ax[d], Tax[d], Thi[d], BKx[d], cb[d], xf[d], in_f32(ef[d]));
+      // (the FP32 estimate is trusted inside the double-word range, a subset
+      // of the exact-truncation range that the statistics test anyway)
+      const int k = locate_mode<LOC>(p.ax[d], Tax[d], Thi[d], BKx[d], cb[d], xf[d], in_ff(ef[d]));
       inr = inr && ((unsigned)(k - 1) < (unsigned)p.ax[d].nbins);
       g += (long long)k * (d == 0 ? 1 : (d == 1 ? stride1 : stride2));
     }
@@ -281,41 +301,44 @@ struct Filler {
         atomicAdd(&sbins[g], 1u);
       else
         atomicAdd(&p.g_unit[g], 1ull);
-    } else if (ACC == ACC_FX) {
+    } else if (ACC == ACC_FX && SMEM) {
+      // the weight's fixed-point value U = trunc(|w| 2^(1065 - elo)) as two
+      // u32 words, from 32-bit funnel shifts of its significand (the same
+      // value as fx_of): M << 10 >> (20 - rel), 5 <= 20 - rel <= 20
+      const unsigned whi = (unsigned)(wb >> 32), wlo = (unsigned)wb;
+      const unsigned rel = ((whi >> 20) & 0x7FFu) - (unsigned)p.fx_elo;
+      w_ok = rel < 16u;
+      if (!w_ok) {
+        slow_bin(p.g_f64, g, wb);
+      } else {
+        const unsigned mh = (whi & 0x000FFFFFu) | 0x00100000u;
+        const unsigned sh = 20u - rel;
+        const unsigned h10 = __funnelshift_l(wlo, mh, 10);
+        const unsigned u0 = __funnelshift_r(wlo << 10, h10, sh);
+        const unsigned u1 = h10 >> sh;  // < 2^26
+        unsigned* a = &sbins[2 * g];
+        if ((int)whi < 0) {
+          fx_add_shared(a, &p.g_hi[g], -(long long)(((unsigned long long)u1 << 32) | u0));
+        } else {
+          // 64-bit add with carries (a positive addend: the only top-word
+          // change is a carry out of bit 63, added to the global high word)
+          const unsigned o0 = atomicAdd(a, u0);
+          const unsigned a1 = u1 + ((o0 + u0 < o0) ? 1u : 0u);
+          const unsigned o1 = atomicAdd(a + 1, a1);
+          if (o1 + a1 < o1) atomicAdd(reinterpret_cast<unsigned long long*>(&p.g_hi[g]), 1ull << 32);
+        }
+      }
+      if (p.track_counts) atomicAdd(&sbins[2 * (int)p.nbins_total + g], 1u);
+    } else if (ACC == ACC_FX) {  // bins in global memory
       long long V;
       w_ok = fx_of(wb, p.fx_elo, &V);
       if (!w_ok) {
         slow_bin(p.g_f64, g, wb);
       } else if (V != 0) {
-        if (SMEM) {
-          // 96-bit add with carries: each atomic returns the old word, so the
-          // carry it produced is known exactly whatever the interleaving.  The
-          // low 64 bits live in shared memory; the rare top-word increment
-          // (a carry out of bit 63, or the sign of a negative addend not
-          // absorbed by a carry) goes straight to the global high word, which
-          // holds the sum in units of 2^32.
-          unsigned* a = &sbins[2 * g];
-          const unsigned v0 = (unsigned)V;
-          const unsigned o0 = atomicAdd(a, v0);
-          const unsigned c0 = (o0 + v0 < o0) ? 1u : 0u;
-          const unsigned a1 = (unsigned)((unsigned long long)V >> 32) + c0;
-          const unsigned c1a = (a1 < c0) ? 1u : 0u;
-          const unsigned o1 = atomicAdd(a + 1, a1);
-          const unsigned c1 = c1a | ((o1 + a1 < o1) ? 1u : 0u);
-          const int top = (int)(V >> 63) + (int)c1;
-          if (top != 0)
-            atomicAdd(reinterpret_cast<unsigned long long*>(&p.g_hi[g]), (unsigned long long)((long long)top << 32));
-        } else {
-          atomicAdd(&p.g_lo[g], (unsigned long long)(unsigned)V);
-          atomicAdd(reinterpret_cast<unsigned long long*>(&p.g_hi[g]), (unsigned long long)(V >> 32));
-        }
+        atomicAdd(&p.g_lo[g], (unsigned long long)(unsigned)V);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&p.g_hi[g]), (unsigned long long)(V >> 32));
       }
-      if (p.track_counts) {
-        if (SMEM)
-          atomicAdd(&sbins[2 * (int)p.nbins_total + g], 1u);
-        else
-          atomicAdd(&p.g_count[g], 1ull);
-      }
+      if (p.track_counts) atomicAdd(&p.g_count[g], 1ull);
     } else if (ACC == ACC_F32C) {
       // FP32 compensated partials: the weight as hi + lo (FP32 double-word);
       // hi goes to the block's FP32 bin by an atomic that returns the old
@@ -460,51 +483,45 @@ __device__ __forceinline__ void load_pair(const double* __restrict__ p, long lon
   }
 }
 
-#ifndef HGB_PREFETCH
-#define HGB_PREFETCH 1
-#endif
-
-// All full pairs of events, grid-strided.  The next pair's loads are issued
-// before the current pair is processed, so each thread keeps two pairs of
-// loads in flight across the long per-event work.
+// All full pairs of events, grid-strided: thread t takes pairs t, t + T,
+// t + 2T, ... (T threads), counted with 32-bit indices from its own column
+// pointers.  Two register buffers alternate: the next pair's loads are
+// issued before the current pair is processed, so each thread keeps two
+// pairs of loads in flight across the long per-event work, and nothing is
+// copied between buffers.
 template <int NDIM, int ACC, bool SMEM, int LOC, bool SW2, bool VEC>
 __device__ __forceinline__ void fill_pairs(Filler<NDIM, ACC, SMEM, LOC, SW2>& f, long long npairs) {
   const FillParams& p = f.p;
   const long long nthreads = (long long)gridDim.x * blockDim.x;
-  int iters = 0;
-  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  unsigned long long c0[NDIM], c1[NDIM], w0 = 0x3FF0000000000000ull, w1 = 0x3FF0000000000000ull;
-  if (HGB_PREFETCH && q < npairs) {
+  const long long q0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q0 >= npairs) return;
+  const int cnt = (int)((npairs - q0 + nthreads - 1) / nthreads);  // pairs of this thread
+  const double* xc[NDIM];
 #pragma unroll
-    for (int d = 0; d < NDIM; ++d) load_pair<VEC>(p.col[d], 2 * q, c0[d], c1[d]);
-    if (ACC != ACC_UNIT) load_pair<VEC>(p.w, 2 * q, w0, w1);
-  }
-  for (; q < npairs; q += nthreads) {
-    if (!HGB_PREFETCH) {
+  for (int d = 0; d < NDIM; ++d) xc[d] = p.col[d] + 2 * q0;
+  const double* wc = ACC != ACC_UNIT ? p.w + 2 * q0 : nullptr;
+  const long long step = 2 * nthreads;
+  auto load = [&](int it, unsigned long long* e0, unsigned long long* e1, unsigned long long& w0,
+                  unsigned long long& w1) {
+    const long long off = (long long)it * step;
 #pragma unroll
-      for (int d = 0; d < NDIM; ++d) load_pair<VEC>(p.col[d], 2 * q, c0[d], c1[d]);
-      if (ACC != ACC_UNIT) load_pair<VEC>(p.w, 2 * q, w0, w1);
-    }
-    unsigned long long n0[NDIM], n1[NDIM], nw0 = 0x3FF0000000000000ull, nw1 = 0x3FF0000000000000ull;
-    const long long qn = q + nthreads;
-    if (HGB_PREFETCH && qn < npairs) {
-#pragma unroll
-      for (int d = 0; d < NDIM; ++d) load_pair<VEC>(p.col[d], 2 * qn, n0[d], n1[d]);
-      if (ACC != ACC_UNIT) load_pair<VEC>(p.w, 2 * qn, nw0, nw1);
-    }
-    f.event_pair(c0, w0, c1, w1);
-    if (++iters == kFlushIters) {
+    for (int d = 0; d < NDIM; ++d) load_pair<VEC>(xc[d], off, e0[d], e1[d]);
+    if (ACC != ACC_UNIT) load_pair<VEC>(wc, off, w0, w1);
+  };
+  unsigned long long a0[NDIM], a1[NDIM], aw0 = 0x3FF0000000000000ull, aw1 = 0x3FF0000000000000ull;
+  unsigned long long b0[NDIM], b1[NDIM], bw0 = 0x3FF0000000000000ull, bw1 = 0x3FF0000000000000ull;
+  load(0, a0, a1, aw0, aw1);
+  int it = 0, iters = 0;
+  while (true) {
+    if (it + 1 < cnt) load(it + 1, b0, b1, bw0, bw1);
+    f.event_pair(a0, aw0, a1, aw1);
+    if (++it >= cnt) break;
+    if (it + 1 < cnt) load(it + 1, a0, a1, aw0, aw1);
+    f.event_pair(b0, bw0, b1, bw1);
+    if (++it >= cnt) break;
+    if (++iters == kFlushIters / 2) {  // two pairs per turn of the loop
       f.st.flush();
       iters = 0;
-    }
-    if (HGB_PREFETCH) {
-#pragma unroll
-      for (int d = 0; d < NDIM; ++d) {
-        c0[d] = n0[d];
-        c1[d] = n1[d];
-      }
-      w0 = nw0;
-      w1 = nw1;
     }
   }
 }

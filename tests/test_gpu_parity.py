@@ -192,6 +192,27 @@ def test_specials_and_stat_overflows(B):
     assert np.array_equal(np.isnan(bins), np.isnan(ref.bins_acc))
 
 
+@pytest.mark.parametrize("p_neg,wmax", [(0.5, 1.5), (0.9, 1.5), (0.5, 255.0)])
+def test_signed_weights_few_bins(B, p_neg, wmax):
+    """Weights of both signs (mostly negative ones in one case) piled into
+    three shared bins: the carry and borrow chains of the fixed-point words
+    run thousands of times per block, totals go negative, and the bins are
+    identical whether the events come in one fill or in seven (every weight
+    lies in the fixed-point window, so the sums are exact)."""
+    rng = np.random.default_rng(12)
+    n = 2_000_003
+    x = rng.uniform(-0.5, 3.5, n)  # the flows too
+    mag = rng.uniform(2.0 ** -8, wmax, n)
+    w = np.where(rng.random(n) < p_neg, -mag, mag)
+    axes = [W.fixed(3, 0.0, 3.0)]
+    ref = oracle.fill(axes, x.reshape(1, -1), w, threads=4)
+    one = gpu_fill(axes, x, w, flags=B.HIST_TRACK_COUNTS)
+    many = gpu_fill(axes, x, w, flags=B.HIST_TRACK_COUNTS, chunks=7)
+    check_against_oracle(axes, x, w, *one, ref, RTOL, RTOL, what="signed weights")
+    assert np.array_equal(one[0], many[0])
+    assert np.array_equal(one[2], many[2])
+
+
 def test_unit_and_weighted_fills_mix(B):
     """A unit-weight fill followed by a weighted fill of the same histogram."""
     import torch
