@@ -142,14 +142,32 @@ __global__ void __launch_bounds__(256, MINB) k_batch_fill(const __grid_constant_
         const long long* T = staged ? skeys + d.ax.smem_off : d.ax.T;
         const int* Thi = staged ? shi + d.ax.smem_off : nullptr;
         const bool in_smem = d.sbin_off >= 0;
+        if (d.ax.mode == LOC_BUCKET) {
+          // the kEv bins first: their table loads overlap (an invalid
+          // event's zero coordinate still maps to a bin; it is not added)
+          long long key[kEv];
+          int k[kEv];
 #pragma unroll
-        for (int e = 0; e < kEv; ++e) {
-          if (!valid[e]) continue;
-          const int k = locate_axis(d.ax, T, Thi, d.ax.bk.cnt, xb[e], xf[e], f32ok[e]);
-          if (in_smem)
-            batch_add<UNIT, true>(d, sbins, k, V[e], wok[e], wb[e]);
-          else
-            batch_add<UNIT, false>(d, sbins, k, V[e], wok[e], wb[e]);
+          for (int e = 0; e < kEv; ++e) key[e] = key_of(xb[e]);
+          locate_bucket_n<kEv>(d.ax, T, d.ax.bk.cnt, xb, key, k);
+#pragma unroll
+          for (int e = 0; e < kEv; ++e) {
+            if (!valid[e]) continue;
+            if (in_smem)
+              batch_add<UNIT, true>(d, sbins, k[e], V[e], wok[e], wb[e]);
+            else
+              batch_add<UNIT, false>(d, sbins, k[e], V[e], wok[e], wb[e]);
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < kEv; ++e) {
+            if (!valid[e]) continue;
+            const int k = locate_axis(d.ax, T, Thi, d.ax.bk.cnt, xb[e], xf[e], f32ok[e]);
+            if (in_smem)
+              batch_add<UNIT, true>(d, sbins, k, V[e], wok[e], wb[e]);
+            else
+              batch_add<UNIT, false>(d, sbins, k, V[e], wok[e], wb[e]);
+          }
         }
       }
       // statistics of this column

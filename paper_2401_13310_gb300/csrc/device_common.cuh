@@ -110,27 +110,32 @@ __device__ __noinline__ int locate_exact(const long long* T, int nbins, int k, u
   return k;
 }
 
-// LOC_BUCKET: range tests on the key, the coordinate's bucket, then the
-// bucket's own thresholds (at most a few) by binary lifting.  Exact: the map
-// is monotone and the host placed every threshold with the same arithmetic.
+// Bucket of a key under the key map of an axis (key_map set, shift > 0).
+// The map is monotone over every key (NaN's included) and T[1] lies in
+// bucket 0: clamped out-of-range keys land in the end buckets, whose counts
+// and thresholds give 0 and nbins + 1 -- no range tests.
+__device__ __forceinline__ int key_bucket(const AxisDev& a, long long key) {
+  if (a.bk.shift >= 32) {
+    // key >> shift and kbase are 32-bit values: the same map on the key's
+    // high word (the difference, after the lower clamp, is taken unsigned)
+    const int hk = (int)(key >> 32) >> (a.bk.shift - 32);
+    const int kb = (int)a.bk.kbase;
+    return (int)min((unsigned)max(hk, kb) - (unsigned)kb, (unsigned)(a.bk.nbk - 1));
+  }
+  long long q = (key >> a.bk.shift) - a.bk.kbase;
+  q = q < 0 ? 0 : (q > a.bk.nbk - 1 ? a.bk.nbk - 1 : q);
+  return (int)q;
+}
+
+// LOC_BUCKET: the coordinate's bucket (range tests on the key unless the key
+// map makes them unnecessary), then the bucket's own thresholds (at most a
+// few) by binary lifting.  Exact: the map is monotone and the host placed
+// every threshold with the same arithmetic.
 __device__ __forceinline__ int locate_bucket(const AxisDev& a, const long long* T, const int* cnt,
                                              unsigned long long b, long long key) {
   int bk;
   if (a.bk.key_map && a.bk.shift > 0) {
-    // the key map is monotone over every key (NaN's included) and T[1]
-    // lies in bucket 0: clamped out-of-range keys land in the end buckets,
-    // whose counts and thresholds give 0 and nbins + 1 -- no range tests
-    if (a.bk.shift >= 32) {
-      // key >> shift and kbase are 32-bit values: the same map on the key's
-      // high word (the difference, after the lower clamp, is taken unsigned)
-      const int hk = (int)(key >> 32) >> (a.bk.shift - 32);
-      const int kb = (int)a.bk.kbase;
-      bk = (int)min((unsigned)max(hk, kb) - (unsigned)kb, (unsigned)(a.bk.nbk - 1));
-    } else {
-      long long q = (key >> a.bk.shift) - a.bk.kbase;
-      q = q < 0 ? 0 : (q > a.bk.nbk - 1 ? a.bk.nbk - 1 : q);
-      bk = (int)q;
-    }
+    bk = key_bucket(a, key);
   } else {
     if (key < a.bk.lo_key) return 0;
     if (key >= a.bk.hi_key) return a.nbins + 1;
@@ -154,6 +159,48 @@ __device__ __forceinline__ int locate_bucket(const AxisDev& a, const long long* 
     if (q <= n_in && T[k + q] <= key) pos = q;
   }
   return k + pos;
+}
+
+// LOC_BUCKET for N coordinates at once, step by step, so that the table
+// loads of the N events (in L2 when the tables are large) are in flight
+// together rather than one event's chain after another's.  Same bins as
+// locate_bucket.
+template <int N>
+__device__ __forceinline__ void locate_bucket_n(const AxisDev& a, const long long* T, const int* cnt,
+                                                const unsigned long long* b, const long long* key, int* k) {
+  if (!(a.bk.key_map && a.bk.shift > 0)) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) k[i] = locate_bucket(a, T, cnt, b[i], key[i]);
+    return;
+  }
+  int bk[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) bk[i] = key_bucket(a, key[i]);
+  if (a.bk.single) {
+    longlong2 e[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) e[i] = reinterpret_cast<const longlong2*>(cnt)[bk[i]];
+#pragma unroll
+    for (int i = 0; i < N; ++i) k[i] = (int)e[i].y + (key[i] >= e[i].x ? 1 : 0);
+    return;
+  }
+  int c0[N], n_in[N], pos[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    c0[i] = cnt[bk[i]];
+    n_in[i] = cnt[bk[i] + 1] - c0[i];
+    pos[i] = 0;
+  }
+  for (int step = a.bk.top; step > 0; step >>= 1) {
+    long long t[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) t[i] = T[c0[i] + min(pos[i] + step, n_in[i])];  // (always a threshold of the bucket's range)
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (pos[i] + step <= n_in[i] && t[i] <= key[i]) pos[i] += step;
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) k[i] = c0[i] + pos[i];
 }
 
 // LOC_LEARNED: the trained index model's bin k0 when its two thresholds
@@ -198,6 +245,12 @@ __device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T,
   return bsearch_keys(T, a.nbins + 2, key);
 }
 
+// Kernel-template value of the locate for LOC_BUCKET axes whose key map
+// works on the key's high word (shift >= 32) with at most one threshold per
+// bucket (a (threshold, count) pair table): the fill kernels' most common
+// variable-axis case, specialised so it runs without the map-type tests.
+constexpr int kLocBucketHiSingle = 4;
+
 // Find-bin with the axis mode fixed at compile time (LOC >= 0: the 1D
 // kernels are specialised per mode so each keeps only its own path), or
 // chosen at run time (LOC < 0).
@@ -205,6 +258,14 @@ template <int LOC>
 __device__ __forceinline__ int locate_mode(const AxisDev& a, const long long* T, const int* Thi, const int* cnt,
                                            unsigned long long b, float xf, bool f32ok) {
   if (LOC < 0) return locate_axis(a, T, Thi, cnt, b, xf, f32ok);
+  if (LOC == kLocBucketHiSingle) {  // key_bucket's high-word map, then the pair
+    const long long key = key_of(b);
+    const int hk = (int)(key >> 32) >> (a.bk.shift - 32);
+    const int kb = (int)a.bk.kbase;
+    const int bk = (int)min((unsigned)max(hk, kb) - (unsigned)kb, (unsigned)(a.bk.nbk - 1));
+    const longlong2 e = reinterpret_cast<const longlong2*>(cnt)[bk];
+    return (int)e.y + (key >= e.x ? 1 : 0);
+  }
   if (LOC == LOC_AFFINE) {  // as in locate_axis
     const float v = __fmaf_rn(xf, a.scale, a.offset);
     const float t = __fadd_rd(v, kMagic);

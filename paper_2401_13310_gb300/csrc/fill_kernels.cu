@@ -277,8 +277,10 @@ struct Filler {
     bool take, fast;
   };
 
-  // Steps 1 and 2 of one event (and its w^2 for HIST_SUMW2).
-  __device__ __forceinline__ StatIn bin_step(const unsigned long long* cb, unsigned long long wb) {
+  // Steps 1 and 2 of one event (and its w^2 for HIST_SUMW2); with PRE the
+  // 1D bin kpre was found already.
+  template <bool PRE = false>
+  __device__ __forceinline__ StatIn bin_step(const unsigned long long* cb, unsigned long long wb, int kpre = 0) {
     // ---- step 1: the bin on every axis, linearised x fastest
     float xf[NDIM];
     unsigned ef[NDIM];
@@ -290,7 +292,7 @@ struct Filler {
       xf[d] = hi24(cb[d]);
       // (the FP32 estimate is trusted inside the double-word range, a subset
       // of the exact-truncation range that the statistics test anyway)
-      const int k = locate_mode<LOC>(p.ax[d], Tax[d], Thi[d], BKx[d], cb[d], xf[d], in_ff(ef[d]));
+      const int k = PRE ? kpre : locate_mode<LOC>(p.ax[d], Tax[d], Thi[d], BKx[d], cb[d], xf[d], in_ff(ef[d]));
       inr = inr && ((unsigned)(k - 1) < (unsigned)p.ax[d].nbins);
       g += (long long)k * (d == 0 ? 1 : (d == 1 ? stride1 : stride2));
     }
@@ -455,6 +457,18 @@ struct Filler {
 
   __device__ __forceinline__ void event_pair(const unsigned long long* c0, unsigned long long w0,
                                              const unsigned long long* c1, unsigned long long w1) {
+    if constexpr (NDIM == 1 && LOC == LOC_BUCKET) {
+      // both bins first: the table loads of the two events overlap
+      const unsigned long long b[2] = {c0[0], c1[0]};
+      const long long key[2] = {key_of(c0[0]), key_of(c1[0])};
+      int k[2];
+      locate_bucket_n<2>(p.ax[0], Tax[0], BKx[0], b, key, k);
+      const StatIn i0 = bin_step<true>(c0, w0, k[0]);
+      stats2(c0, w0, i0, c0, w0, StatIn{false, false});
+      const StatIn i1 = bin_step<true>(c1, w1, k[1]);
+      stats2(c1, w1, i1, c1, w1, StatIn{false, false});
+      return;
+    }
     if constexpr (NDIM == 1) {  // one event after the other, as scalar code schedules best
       event(c0, w0);
       event(c1, w1);
@@ -794,6 +808,8 @@ const void* fill_fn(int loc, bool sw2, bool expr) {
     if (loc == LOC_AFFINE) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_AFFINE, false, false>);
     if (loc == LOC_LEARNED) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_LEARNED, false, false>);
     if (loc == LOC_BUCKET) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_BUCKET, false, false>);
+    if (loc == kLocBucketHiSingle)
+      return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, kLocBucketHiSingle, false, false>);
     return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_BSEARCH, false, false>);
   }
 }
@@ -828,8 +844,15 @@ size_t smem_bin_bytes(int acc_mode, int track_counts, int sumw2) {
   return 16;
 }
 
+// The first axis's locate as a kernel-template value.
+int fill_loc(const FillParams& p) {
+  const AxisDev& a = p.ax[0];
+  if (a.mode == LOC_BUCKET && a.bk.key_map && a.bk.shift >= 32 && a.bk.single) return kLocBucketHiSingle;
+  return a.mode;
+}
+
 int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shape) {
-  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0, p.ax[0].mode, p.sumw2 != 0, p.ex.nsrc > 0);
+  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0, fill_loc(p), p.sumw2 != 0, p.ex.nsrc > 0);
   if (fn == nullptr) return -1;
   const int block = 256;
   size_t smem = (((size_t)p.table_keys * 12 + 15) & ~(size_t)15) + (((size_t)p.table_bk * 4 + 15) & ~(size_t)15);
@@ -851,7 +874,7 @@ int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shap
 }
 
 int launch_fill(const FillParams& p, int acc_mode, const LaunchShape& s, void* stream) {
-  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0, p.ax[0].mode, p.sumw2 != 0, p.ex.nsrc > 0);
+  const void* fn = pick_fill(p.ndim, acc_mode, p.smem_bins != 0, fill_loc(p), p.sumw2 != 0, p.ex.nsrc > 0);
   if (fn == nullptr) return -1;
   void* args[] = {const_cast<FillParams*>(&p)};
   const cudaError_t e = cudaLaunchKernel(fn, dim3(s.grid), dim3(s.block), args, s.smem, (cudaStream_t)stream);
