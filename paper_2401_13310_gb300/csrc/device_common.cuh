@@ -110,32 +110,27 @@ __device__ __noinline__ int locate_exact(const long long* T, int nbins, int k, u
   return k;
 }
 
-// Bucket of a key under the key map of an axis (key_map set, shift > 0).
-// The map is monotone over every key (NaN's included) and T[1] lies in
-// bucket 0: clamped out-of-range keys land in the end buckets, whose counts
-// and thresholds give 0 and nbins + 1 -- no range tests.
-__device__ __forceinline__ int key_bucket(const AxisDev& a, long long key) {
-  if (a.bk.shift >= 32) {
-    // key >> shift and kbase are 32-bit values: the same map on the key's
-    // high word (the difference, after the lower clamp, is taken unsigned)
-    const int hk = (int)(key >> 32) >> (a.bk.shift - 32);
-    const int kb = (int)a.bk.kbase;
-    return (int)min((unsigned)max(hk, kb) - (unsigned)kb, (unsigned)(a.bk.nbk - 1));
-  }
-  long long q = (key >> a.bk.shift) - a.bk.kbase;
-  q = q < 0 ? 0 : (q > a.bk.nbk - 1 ? a.bk.nbk - 1 : q);
-  return (int)q;
-}
-
-// LOC_BUCKET: the coordinate's bucket (range tests on the key unless the key
-// map makes them unnecessary), then the bucket's own thresholds (at most a
-// few) by binary lifting.  Exact: the map is monotone and the host placed
-// every threshold with the same arithmetic.
+// LOC_BUCKET: range tests on the key, the coordinate's bucket, then the
+// bucket's own thresholds (at most a few) by binary lifting.  Exact: the map
+// is monotone and the host placed every threshold with the same arithmetic.
 __device__ __forceinline__ int locate_bucket(const AxisDev& a, const long long* T, const int* cnt,
                                              unsigned long long b, long long key) {
   int bk;
   if (a.bk.key_map && a.bk.shift > 0) {
-    bk = key_bucket(a, key);
+    // the key map is monotone over every key (NaN's included) and T[1]
+    // lies in bucket 0: clamped out-of-range keys land in the end buckets,
+    // whose counts and thresholds give 0 and nbins + 1 -- no range tests
+    if (a.bk.shift >= 32) {
+      // key >> shift and kbase are 32-bit values: the same map on the key's
+      // high word (the difference, after the lower clamp, is taken unsigned)
+      const int hk = (int)(key >> 32) >> (a.bk.shift - 32);
+      const int kb = (int)a.bk.kbase;
+      bk = (int)min((unsigned)max(hk, kb) - (unsigned)kb, (unsigned)(a.bk.nbk - 1));
+    } else {
+      long long q = (key >> a.bk.shift) - a.bk.kbase;
+      q = q < 0 ? 0 : (q > a.bk.nbk - 1 ? a.bk.nbk - 1 : q);
+      bk = (int)q;
+    }
   } else {
     if (key < a.bk.lo_key) return 0;
     if (key >= a.bk.hi_key) return a.nbins + 1;
@@ -159,6 +154,19 @@ __device__ __forceinline__ int locate_bucket(const AxisDev& a, const long long* 
     if (q <= n_in && T[k + q] <= key) pos = q;
   }
   return k + pos;
+}
+
+// Bucket of a key under the key map of an axis (key_map set, shift > 0), as
+// in locate_bucket.
+__device__ __forceinline__ int key_bucket(const AxisDev& a, long long key) {
+  if (a.bk.shift >= 32) {
+    const int hk = (int)(key >> 32) >> (a.bk.shift - 32);
+    const int kb = (int)a.bk.kbase;
+    return (int)min((unsigned)max(hk, kb) - (unsigned)kb, (unsigned)(a.bk.nbk - 1));
+  }
+  long long q = (key >> a.bk.shift) - a.bk.kbase;
+  q = q < 0 ? 0 : (q > a.bk.nbk - 1 ? a.bk.nbk - 1 : q);
+  return (int)q;
 }
 
 // LOC_BUCKET for N coordinates at once, step by step, so that the table
@@ -247,8 +255,9 @@ __device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T,
 
 // Kernel-template value of the locate for LOC_BUCKET axes whose key map
 // works on the key's high word (shift >= 32) with at most one threshold per
-// bucket (a (threshold, count) pair table): the fill kernels' most common
-// variable-axis case, specialised so it runs without the map-type tests.
+// bucket (a (threshold, count) pair table): the weighted 1D fills' most
+// common variable-axis case, specialised so it runs without the map-type
+// tests.
 constexpr int kLocBucketHiSingle = 4;
 
 // Find-bin with the axis mode fixed at compile time (LOC >= 0: the 1D
@@ -258,7 +267,7 @@ template <int LOC>
 __device__ __forceinline__ int locate_mode(const AxisDev& a, const long long* T, const int* Thi, const int* cnt,
                                            unsigned long long b, float xf, bool f32ok) {
   if (LOC < 0) return locate_axis(a, T, Thi, cnt, b, xf, f32ok);
-  if (LOC == kLocBucketHiSingle) {  // key_bucket's high-word map, then the pair
+  if (LOC == kLocBucketHiSingle) {  // locate_bucket's high-word map, then the pair
     const long long key = key_of(b);
     const int hk = (int)(key >> 32) >> (a.bk.shift - 32);
     const int kb = (int)a.bk.kbase;
