@@ -86,3 +86,26 @@ def test_bucket_fill_counts_equal_binary_search(B, name, axis, mode):
     assert np.array_equal(out[0][1], out[1][1])  # exact fixed-point bins: order-independent
     ref = oracle.fill([axis], x.reshape(1, -1), w)
     assert np.array_equal(out[0][0], ref.counts)
+
+
+@pytest.mark.parametrize("name,axis,mode", _axes(), ids=[a[0] for a in _axes()])
+def test_bucket_unit_fill_counts_exact(B, name, axis, mode):
+    """Unit weights through the fill kernels on every axis (bucket map, pair
+    table, binary-search fallback): counts bit-exact against the oracle,
+    including the edges, their predecessors and the special values."""
+    import torch
+    rng = np.random.default_rng(13)
+    T = B.hist_axis_thresholds(axis)
+    x = np.concatenate([edge_probe_values(axis, T, rng, nrand=200_000), np.zeros(5)])
+    h = B.Hist([axis])
+    try:
+        h.fill(to_device(x.reshape(1, -1)), None)
+        torch.cuda.synchronize()
+        got = h.counts()
+        bins, stats = h.result()
+    finally:
+        h.close()
+    ref = oracle.fill([axis], x.reshape(1, -1), None)
+    assert np.array_equal(got, ref.counts), f"{name}: counts differ at {np.flatnonzero(got != ref.counts)[:10]}"
+    assert np.array_equal(bins, ref.counts.astype(np.float64))
+    assert stats[0] == ref.stats_acc[0]
