@@ -478,6 +478,69 @@ def check_exact_stats_vs_fractions(seed=12):
     assert oracle.exact_stats(axes, x, w3)[0] == math.inf
 
 
+def check_chunk_parallel_fill_and_locate(seed=13):
+    """The chunk-parallel modes (oracle_fill_mt, oracle_locate_mt) that the
+    full-size parity tests use as their reference, at several thread counts
+    (more threads than events included) and ragged sizes: bins from
+    numpy.searchsorted (variable axis) and exact dyadic arithmetic (fixed
+    axis), counts from numpy.bincount of those bins, compensated per-bin and
+    statistics sums within a few ulps of math.fsum, every event counted once.
+    A hand-made bin whose compensated value exists only in the correction
+    terms (1e16 + 1 - 1e16 inside each chunk) pins the merge of those terms."""
+    rng = np.random.default_rng(seed)
+    edges = np.unique(np.sort(rng.uniform(-3, 3, 37)))
+    assert len(edges) == 37  # 36 bins + 2 flows: linear stride 38
+    ax_var = {"kind": "variable", "edges": edges}
+    ax_fix = oracle_axis_fixed(16, -4.0, 4.0)
+
+    def bins_var(x):
+        return np.searchsorted(edges, x, side="right")  # NaN sorts last: overflow
+
+    def bins_fix(x):
+        b = np.where(x < -4.0, 0, np.where(x >= 4.0, 17, 0))
+        inr = (x >= -4.0) & (x < 4.0)
+        b[inr] = 1 + np.floor(2.0 * (x[inr] + 4.0)).astype(np.int64)  # exact for x = k 2^-20
+        return b
+
+    for n in (0, 1, 5, 7, 1001, 20011):
+        x = rng.normal(0, 1.6, n)
+        x[::97] = NAN
+        y = rng.integers(-5 * 2 ** 20, 5 * 2 ** 20, n) * 2.0 ** -20
+        w = rng.uniform(-0.5, 2.0, n)
+        for axes, v, gi in (([ax_var], x.reshape(1, n), bins_var(x)),
+                            ([ax_var, ax_fix], np.stack([x, y]), bins_var(x) + 38 * bins_fix(y))):
+            nb = oracle.nbins_total(axes)
+            inr = np.ones(n, dtype=bool)
+            for d, ax in enumerate(axes):
+                bd = bins_var(v[d]) if ax["kind"] == "variable" else bins_fix(v[d])
+                inr &= (bd >= 1) & (bd <= (len(edges) - 1 if ax["kind"] == "variable" else 16))
+            terms = _terms_numpy(v[:, inr], w[inr])
+            for threads in (2, 3, 7, 16):
+                got = oracle.locate(axes, v, threads=threads)
+                assert np.array_equal(got, gi), f"locate_mt n={n} threads={threads}"
+                r = oracle.fill(axes, v, w, threads=threads)
+                assert np.array_equal(r.counts, np.bincount(gi, minlength=nb).astype(np.uint64)), \
+                    f"fill_mt counts n={n} threads={threads}"
+                assert r.stats_acc[0] == n and r.stats_seq[0] == n
+                for g in np.flatnonzero(r.counts):
+                    ref = math.fsum(w[gi == g])
+                    assert abs(r.bins_acc[g] - ref) <= 2 * math.ulp(ref) + 1e-300, (n, threads, g)
+                    assert abs(r.bins_seq[g] - ref) <= 1e-12 * r.bins_abs[g] + 1e-300, (n, threads, g)
+                for k, t in enumerate(terms, start=1):
+                    ref = math.fsum(t)
+                    assert abs(r.stats_acc[k] - ref) <= 4 * math.ulp(ref) + 1e-300, (n, threads, k)
+    # every chunk holds 1e16, 1, -1e16 in bin 1: its value lives in the
+    # compensation term, which the merge must carry over
+    n = 12
+    x = np.full(n, float(edges[0]))
+    w = np.tile([1e16, 1.0, -1e16], 4)
+    for threads in (2, 4):
+        r = oracle.fill([ax_var], x.reshape(1, n), w, threads=threads)
+        assert r.bins_acc[1] == 4.0, (threads, r.bins_acc[1])
+        r = oracle.fill([ax_var], x.reshape(1, n), w * 0.5, threads=threads)
+        assert r.stats_acc[1] == 2.0, (threads, r.stats_acc[1])
+
+
 ALL_CHECKS = [
     check_golden_fixed, check_golden_variable, check_fixed_dyadic_exact,
     check_fixed_vs_rational, check_fixed_centres, check_fixed_range_edges,
@@ -486,5 +549,5 @@ ALL_CHECKS = [
     check_golden_fill, check_fill_counts_vs_numpy, check_fill_sums_vs_library,
     check_stats_vs_fsum, check_stats_closed_form_centres, check_flows_and_specials,
     check_fills_accumulate, check_sumw2_vs_bincount, check_define_filter_vs_python_loops,
-    check_exact_stats_vs_fractions,
+    check_exact_stats_vs_fractions, check_chunk_parallel_fill_and_locate,
 ]

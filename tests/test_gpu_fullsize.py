@@ -1,0 +1,151 @@
+"""Full-size parity of the batched and learned-locator workloads.
+
+The 64-histogram batch (5e7 weighted events on three columns, 10 .. 1e5 bins
+per histogram, fixed and variable axes) and the 8 variable axes of 1e4 .. 1e6
+mixture-quantile edges (1e8 unit-weight values) against the chunk-parallel
+CPU oracle on all host cores, in every form the benchmark times: plain
+per-histogram fills, the tuned batch, and each batch strategy pinned; for the
+8-axis workload with the bucket-map, binary-search and learned locators.
+Counts and unit-weight bins bit-exact; weighted bins and statistics within
+1e-12 of the sum of |terms| (Sec. 3.1 of the paper defines the fill; the
+oracle restates it).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_13310_gb300 import workloads as W
+from tests.helpers import assert_sums_close, to_device
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+N4 = 50_000_000
+N5 = 100_000_000
+
+
+def _threads():
+    return max(1, len(os.sched_getaffinity(0)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2401_13310_gb300 import _build
+    _build.build()
+    from paper_2401_13310_gb300 import binding
+    binding.load()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def cfg4_ref():
+    bw = W.cfg4(n=N4)
+    refs = [oracle.fill([ax], bw.columns[c].reshape(1, -1), bw.weights, threads=_threads())
+            for ax, c in zip(bw.axes, bw.col_of_hist)]
+    return bw, refs
+
+
+def _check_weighted(results, bw, refs, what, counts=None):
+    for i, ((bins, stats), ref) in enumerate(zip(results, refs)):
+        if counts is not None:
+            assert np.array_equal(counts[i], ref.counts), f"{what} hist {i}: counts differ"
+        assert_sums_close(bins, ref.bins_acc, ref.bins_abs, RTOL, f"{what} hist {i} bins")
+        assert stats[0] == ref.stats_acc[0], f"{what} hist {i}: entries"
+        assert_sums_close(stats[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, f"{what} hist {i} stats")
+
+
+def test_cfg4_full_size_plain_and_batched(B, cfg4_ref):
+    """64 histograms x 5e7 events: the 64 plain fills (with per-bin counts),
+    the batch after tuning on a 4e6-event sample, and the wide and sliced
+    strategies pinned -- each against the oracle."""
+    import torch
+    bw, refs = cfg4_ref
+    cols = [to_device(np.ascontiguousarray(bw.columns[c])) for c in range(3)]
+    w = to_device(bw.weights)
+    # plain: one launch per histogram
+    hists = [B.Hist([ax], B.HIST_TRACK_COUNTS) for ax in bw.axes]
+    try:
+        for h, c in zip(hists, bw.col_of_hist):
+            h.fill(cols[c], w)
+        torch.cuda.synchronize()
+        _check_weighted([h.result() for h in hists], bw, refs, "plain", counts=[h.counts() for h in hists])
+    finally:
+        for h in hists:
+            h.close()
+    # batched: tuned, then each strategy pinned
+    plans = [("tuned", None), ("wide", (0, 48 << 10, 30, -1, 2, 2)), ("sliced", (1, 200 << 10, 30, -1, 2, 4))]
+    for name, cfg in plans:
+        hists = [B.Hist([ax]) for ax in bw.axes]
+        batch = None
+        try:
+            batch = B.Batch(hists, bw.col_of_hist, B.HIST_BATCH_GRAPH)
+            if cfg is None:
+                batch.tune([c[:4_000_000] for c in cols], w[:4_000_000])
+            else:
+                batch.configure(*cfg)
+            batch.fill(cols, w)
+            torch.cuda.synchronize()
+            _check_weighted([h.result() for h in hists], bw, refs, f"batch {name}")
+        finally:
+            if batch is not None:
+                batch.close()
+            for h in hists:
+                h.close()
+
+
+@pytest.fixture(scope="module")
+def cfg5_ref():
+    bw = W.cfg5(n=N5)
+    refs = [oracle.fill([ax], bw.columns, None, threads=_threads()) for ax in bw.axes]
+    return bw, refs
+
+
+def _check_unit(results, refs, what, counts=None):
+    for i, ((bins, stats), ref) in enumerate(zip(results, refs)):
+        if counts is not None:
+            assert np.array_equal(counts[i], ref.counts), f"{what} hist {i}: counts differ"
+        bad = np.flatnonzero(bins != ref.counts.astype(np.float64))
+        assert bad.size == 0, f"{what} hist {i}: {bad.size} bins differ, first {bad[:5]}"
+        assert stats[0] == ref.stats_acc[0]
+        assert_sums_close(stats[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, f"{what} hist {i} stats")
+
+
+@pytest.mark.parametrize("locator", ["default", "bsearch", "learned"])
+def test_cfg5_full_size_locators(B, cfg5_ref, locator):
+    """8 axes with 1e4 .. 1e6 mixture-quantile edges, 1e8 mixture values,
+    unit weights: plain fills and the tuned batch, with the default
+    (bucket-map) locator, plain binary search, and the trained learned
+    locator -- bins bit-exact against the oracle."""
+    import torch
+    bw, refs = cfg5_ref
+    col = to_device(np.ascontiguousarray(bw.columns[0]))
+    flags = B.HIST_LOCATOR_BSEARCH if locator != "default" else 0
+    hists = [B.Hist([ax], flags) for ax in bw.axes]
+    batch = None
+    try:
+        modes = [B.hist_locator_mode(h.h, 0) for h in hists]
+        if locator == "learned":
+            reps = [h.train_locator(0) for h in hists]
+            assert all(0 <= r["window"] <= 64 for r in reps)
+            modes = [B.hist_locator_mode(h.h, 0) for h in hists]
+            assert all(m == "learned" for m in modes), modes
+        elif locator == "bsearch":
+            assert all(m == "bsearch" for m in modes), modes
+        for h in hists:
+            h.fill(col, None)
+        torch.cuda.synchronize()
+        _check_unit([h.result() for h in hists], refs, f"plain {locator}", counts=[h.counts() for h in hists])
+        for h in hists:
+            h.reset()
+        batch = B.Batch(hists, bw.col_of_hist, B.HIST_BATCH_GRAPH)
+        batch.tune([col[:8_000_000]], None)
+        batch.fill([col], None)
+        torch.cuda.synchronize()
+        _check_unit([h.result() for h in hists], refs, f"batch {locator}")
+    finally:
+        if batch is not None:
+            batch.close()
+        for h in hists:
+            h.close()

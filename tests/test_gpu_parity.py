@@ -53,6 +53,29 @@ def test_locate_edges_bit_exact(B, axis):
     assert bad.size == 0, f"{bad.size} mismatches, e.g. x={x[bad[:5]]!r} got {got[bad[:5]]} ref {ref[bad[:5]]}"
 
 
+@pytest.mark.parametrize("weighted", [False, True])
+@pytest.mark.parametrize("axis", LOCATE_AXES, ids=lambda a: f"{a['kind']}{a.get('nbins', len(a.get('edges', [])) - 1)}")
+def test_fill_edges_bit_exact(B, axis, weighted):
+    """The same probes through hist_fill_bulk: the fill kernels carry their
+    own locate (compiled per locate mode, the FP32 estimate gated on the
+    double-word range, the specialised bucket kernel for weighted fills), so
+    every threshold, its neighbouring keys and the special values go through
+    it too, in shuffled order; counts bit-exact against the oracle, and the
+    unit-weight bins equal to the counts."""
+    rng = np.random.default_rng(6)
+    T = B.hist_axis_thresholds(axis)
+    x = edge_probe_values(axis, T, rng)
+    x = x[rng.permutation(x.size)]
+    w = rng.uniform(0.5, 1.5, x.size) if weighted else None
+    ref = oracle.fill([axis], x.reshape(1, -1), w)
+    bins, stats, counts = gpu_fill([axis], x, w, flags=B.HIST_TRACK_COUNTS)
+    bad = np.flatnonzero(counts != ref.counts)
+    assert bad.size == 0, f"{bad.size} bins with other counts, e.g. {bad[:5]}: {counts[bad[:5]]} vs {ref.counts[bad[:5]]}"
+    if not weighted:
+        assert np.array_equal(bins, ref.counts.astype(np.float64))
+    assert stats[0] == x.size
+
+
 def test_locate_nd_bit_exact(B):
     rng = np.random.default_rng(8)
     axes = [W.fixed(30, -2.0, 2.0), W.variable(np.sort(rng.uniform(-3, 3, 41))), W.fixed(5, 0.0, 1.0)]
@@ -286,24 +309,26 @@ def test_zero_and_tiny_coordinates(B, weighted):
 
 
 @pytest.mark.parametrize("name,n", [("2a", 2_000_003), ("2b", 2_000_003), ("3b", 1_000_001), ("1", 1 << 20)])
-def test_fp32c_within_stated_bound(B, name, n):
+def test_fp32c_within_tolerance(B, name, n):
     """HIST_PREC_FP32C (FP32 compensated shared-memory partials): counts
-    exact, every bin within the stated bound
+    exact; every bin within 1e-12 of its sum |w| -- the tolerance of the
+    binary64 paths.  The stated bound per bin,
         |err| <= 2^-48 ((m + 1)^2 + 1) A + B 2^-53 A
-    (m <= the bin's entries, A = sum |w| of the bin, B <= 1216 blocks), the
-    statistics (double-word path) within 1e-12 of sum |term|."""
+    (m = the bin's entries in one block, A = sum |w| of the bin, B blocks),
+    is a worst case that reaches 1e-12 A near 14 entries per bin and block;
+    the errors measured are near 1e-15 A.  A compensation that lost the
+    TwoSum error term would be off by about 2^-24 of a block's partial per
+    entry, orders of magnitude above the tolerance
+    (tests/test_precision_model.py shows both on a CPU model of the same
+    arithmetic).  Statistics (double-word path) within 1e-12 of sum
+    |term|."""
     wl = W.CONFIGS[name](n=n)
     w = wl.weights if wl.weights is not None else np.random.default_rng(3).uniform(0.5, 1.5, n)
     flags = B.HIST_TRACK_COUNTS | B.HIST_PREC_FP32C
     ref = oracle.fill(wl.axes, wl.values, w, threads=4)
     bins, stats, counts = gpu_fill(wl.axes, wl.values, w, flags=flags)
     assert np.array_equal(counts, ref.counts)
-    m = ref.counts.astype(np.float64)
-    A = ref.bins_abs
-    bound = 2.0 ** -48 * ((m + 1.0) ** 2 + 1.0) * A + 1216 * 2.0 ** -53 * A
-    err = np.abs(bins - ref.bins_acc)
-    assert np.all(err <= bound), f"cfg{name}: worst bin error / bound {np.max(err / np.maximum(bound, 1e-300)):.3g}"
-    rel = np.max(err / np.maximum(A, 1e-300))
+    rel = assert_sums_close(bins, ref.bins_acc, ref.bins_abs, RTOL, f"cfg{name} FP32C bins")
     print(f"cfg{name} FP32C: max |err| / sum|w| per bin = {rel:.3g}")
     assert stats[0] == ref.stats_acc[0]
     assert_sums_close(stats[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, f"cfg{name} FP32C stats")

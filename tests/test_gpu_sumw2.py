@@ -1,14 +1,19 @@
 """Per-bin sum of squared weights (HIST_SUMW2, ROOT's Sumw2) against the
 oracle, in every precision mode, for shared-memory bins (compensated FP32
 words) and global bins (binary64 atomics), unit and weighted fills mixed.
-Bound per bin, A = sum w^2 of its entries, m <= its entry count, B <= 1216
-blocks:  |err| <= 2^-44 A + 2^-48 ((m + 1)^2 + 1) A + B 2^-53 A."""
+Every bin within 1e-12 of A = the sum of w^2 over its entries (the tolerance
+of the binary64 paths).  The stated bound of the compensated FP32 words, with
+m = the bin's entries in one block and B blocks,
+    |err| <= 2^-44 A + 2^-48 ((m + 1)^2 + 1) A + B 2^-53 A,
+is a worst case; the errors measured are near 1e-14 A, and a dropped TwoSum
+error term would be orders of magnitude above the tolerance
+(tests/test_precision_model.py)."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2401_13310_gb300 import workloads as W
-from tests.helpers import to_device
+from tests.helpers import assert_sums_close, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -22,9 +27,7 @@ def B():
     return binding
 
 
-def _bound(counts, A):
-    m = counts.astype(np.float64)
-    return 2.0 ** -44 * A + 2.0 ** -48 * ((m + 1.0) ** 2 + 1.0) * A + 1216 * 2.0 ** -53 * A
+RTOL = 1e-12
 
 
 @pytest.mark.parametrize("name,n", [("2a", 1_000_003), ("2b", 1_000_003), ("3a", 300_001), ("3b", 500_001)])
@@ -46,11 +49,8 @@ def test_sumw2_matches_oracle(B, name, n, prec):
     s2, a2 = oracle.sumw2(wl.axes, wl.values, wl.weights)
     c1, _ = oracle.sumw2(wl.axes, np.ascontiguousarray(wl.values[:, :half]), None)
     ref = s2 + c1
-    counts = oracle.fill(wl.axes, wl.values, wl.weights).counts
-    err = np.abs(got - ref)
-    bound = _bound(counts, a2) + 1e-300
-    assert np.all(err <= bound), f"cfg{name} {prec}: worst error/bound {np.max(err / bound):.3g}"
-    print(f"cfg{name} {prec}: max |err| / sum w^2 = {np.max(err / np.maximum(a2 + c1, 1e-300)):.3g}")
+    rel = assert_sums_close(got, ref, a2 + c1, RTOL, f"cfg{name} {prec} sumw2")
+    print(f"cfg{name} {prec}: max |err| / sum w^2 = {rel:.3g}")
 
 
 def test_sumw2_requires_flag_and_rejects_batches(B):

@@ -30,6 +30,14 @@ MUTANTS = [
     ("if (b < 1 || b > axes[d].nbins) in_range = 0;", "if (b < 1) in_range = 0;"),
     ("term[9] = wx * z;", "term[9] = wy * z;"),
     ("o->bins_seq[g] += w;", "o->bins_seq[g] += fabs(w);"),
+    # the chunk-parallel modes: split, merge, compensation merge, locate
+    ("j->i1 = n * (t + 1) / nthreads;", "j->i1 = n * (t + 1) / nthreads - (t + 1 < nthreads);"),
+    ("counts[g] += p->counts[g];", "counts[g] = p->counts[g];"),
+    ("neumaier_add(&bins_acc_s[g], &bins_acc_c[g], p->bins_acc_c[g]);", ""),
+    ("neumaier_add(&stats_acc_s[k], &stats_acc_c[k], p->stats_acc_c[k]);", ""),
+    ("bins_seq[g] += p->bins_seq[g];", "bins_seq[g] = p->bins_seq[g];"),
+    ("int32_t b = find_bin(&j->axes[d], j->values[(int64_t)d * j->n + i]);",
+     "int32_t b = find_bin(&j->axes[d], j->values[(int64_t)d * j->n + i - (i > j->i0)]);"),
 ]
 
 

@@ -1,13 +1,18 @@
-"""The allocation-free fill (hist_fill_bulk_noalloc) against the regular
-entry points (hist_book + hist_fill_bulk + hist_result), through the C ABI.
+"""The allocation-free fill (hist_fill_bulk_noalloc) against the CPU oracle
+and against the regular entry points (hist_book + hist_fill_bulk +
+hist_result), through the C ABI.
 
 hist_fill_bulk_noalloc exists for callers that cannot call cudaMalloc (code
 under another framework's memory manager, allocation-free real-time loops):
-its scratch is one fixed library array shared by all calls.  Two calls in a
-row must each give the same answer as the regular path on the same bulk --
-the second call must not see the first call's leftovers.  This file sorts
-last so that a run stopping at the first failure has run everything else.
+its scratch is one fixed library array shared by all calls.  Every call must
+give the oracle's answer on its own bulk -- unit-weight bins and the entry
+count bit-exact, weighted bins and statistics within 1e-12 of the sum of
+|terms| -- and the same answer as the regular path; calls in a row must not
+see the earlier calls' leftovers, whatever their sizes.  This file sorts last
+so that a run stopping at the first failure has run everything else.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -43,14 +48,21 @@ def _noalloc(B, axis, x, w, flags=0):
 
 def _compare(B, axis, x, w, flags=0, what=""):
     got_bins, got_stats = _noalloc(B, axis, x, w, flags)
-    ref_bins, ref_stats, _ = gpu_fill([axis], x.reshape(1, -1), w, flags=flags)
-    scale = oracle.fill([axis], x.reshape(1, -1), w, stat_overflows=bool(flags & B.HIST_STAT_OVERFLOWS))
-    assert_sums_close(got_bins, ref_bins, scale.bins_abs, RTOL, f"{what} bins")
-    assert got_stats[0] == ref_stats[0]
-    assert_sums_close(got_stats[1:], ref_stats[1:], scale.stats_abs[1:], RTOL, f"{what} stats")
+    ref = oracle.fill([axis], x.reshape(1, -1), w, stat_overflows=bool(flags & B.HIST_STAT_OVERFLOWS))
+    # against the oracle
+    if w is None:
+        assert np.array_equal(got_bins, ref.counts.astype(np.float64)), f"{what}: unit-weight bins"
+    else:
+        assert_sums_close(got_bins, ref.bins_acc, ref.bins_abs, RTOL, f"{what} bins")
+    assert got_stats[0] == ref.stats_acc[0] == x.shape[0], f"{what}: entries"
+    assert_sums_close(got_stats[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, f"{what} stats")
+    # against the regular path on the same bulk
+    reg_bins, reg_stats, _ = gpu_fill([axis], x.reshape(1, -1), w, flags=flags)
+    assert_sums_close(got_bins, reg_bins, ref.bins_abs, RTOL, f"{what} bins vs regular path")
+    assert_sums_close(got_stats[1:], reg_stats[1:], ref.stats_abs[1:], RTOL, f"{what} stats vs regular path")
 
 
-def test_noalloc_matches_regular_path_twice_in_a_row(B):
+def test_noalloc_matches_oracle_twice_in_a_row(B):
     rng = np.random.default_rng(21)
     axis = W.fixed(1000, -5.0, 5.0)
     for call in range(2):
@@ -71,6 +83,53 @@ def test_noalloc_unit_and_variable_axis_twice_in_a_row(B):
     x = rng.uniform(-0.5, 1.5, 50_001)
     w = rng.uniform(0.5, 1.5, 50_001)
     _compare(B, axis2, x, w, flags=B.HIST_STAT_OVERFLOWS, what="small axis")
+
+
+def test_noalloc_largest_axes_then_a_small_one(B):
+    """The largest accepted axes (nbins = 1022: 1024 bins with the flows,
+    every threshold and per-block bin slot of the scratch in use), fixed and
+    variable, unit and weighted, then a 5-bin axis that must not see their
+    leftovers."""
+    rng = np.random.default_rng(23)
+    big_fixed = W.fixed(1022, -3.0, 3.0)
+    big_var = W.variable(np.sort(rng.uniform(-3.0, 3.0, 1023)))
+    n = 400_003
+    x = rng.normal(0, 1.2, n)
+    w = rng.uniform(0.5, 1.5, n)
+    _compare(B, big_fixed, x, w, what="1022 fixed weighted")
+    _compare(B, big_var, x, None, what="1022 variable unit")
+    _compare(B, big_var, x, w, what="1022 variable weighted")
+    small = W.fixed(5, -1.0, 1.0)
+    xs = rng.uniform(-1.5, 1.5, 10_007)
+    _compare(B, small, xs, None, what="5 bins after 1022")
+    _compare(B, small, xs, rng.uniform(0.5, 1.5, 10_007), what="5 bins weighted after 1022")
+
+
+def test_noalloc_odd_weights(B):
+    """Weights outside the fixed-point window (zero, tiny, large), negative
+    ones, and one +inf and one NaN weight in separate bins: the binary64
+    words and their compensated sum, as the regular path forms them."""
+    rng = np.random.default_rng(24)
+    axis = W.fixed(40, -2.0, 2.0)
+    n = 100_001
+    x = rng.normal(0, 0.8, n)
+    w = rng.uniform(-1.5, 1.5, n)
+    w[::5] = 0.0
+    w[1::7] = 1e3
+    w[2::11] = -1e-4
+    w[3::13] = 3e-9
+    _compare(B, axis, x, w, what="odd weights")
+    x2 = x.copy()
+    w2 = w.copy()
+    x2[:2] = [-1.99, 1.99]  # bins 1 and 40
+    w2[:2] = [math.inf, math.nan]
+    got_bins, got_stats = _noalloc(B, axis, x2, w2)
+    reg_bins, reg_stats, _ = gpu_fill([axis], x2.reshape(1, -1), w2)
+    ref = oracle.fill([axis], x2.reshape(1, -1), w2)
+    assert got_bins[1] == math.inf and math.isnan(got_bins[40])
+    assert_sums_close(got_bins, ref.bins_acc, ref.bins_abs, RTOL, "specials bins vs oracle")
+    assert_sums_close(got_bins, reg_bins, ref.bins_abs, RTOL, "specials bins vs regular path")
+    assert got_stats[0] == n and math.isnan(got_stats[1]) and math.isnan(reg_stats[1])
 
 
 def test_noalloc_rejects_oversized_axis(B):
