@@ -319,7 +319,12 @@ void hist_batch_free(hist_batch_t *b);
 /* ---- learned locator (variable axes) ------------------------------------
  * A trained piecewise-linear index model predicts the bin of a coordinate;
  * an exact search inside a certified window corrects it, and a full binary
- * search judges every window miss, so results stay bit-exact.  The model
+ * search judges every window miss, so results stay bit-exact.  The window
+ * is certified for every non-NaN coordinate: the model, as the fill
+ * evaluates it, is monotone in the coordinate within a segment, so its
+ * largest index error lies at an end of a bin, of a segment, or of a
+ * monotone piece of the FP32 truncation -- the certifier evaluates every
+ * such end (NaN coordinates take the full search).  The model
  * over S uniform segments of u = (xf - u0) * u_scale (xf: the coordinate
  * truncated to FP32) has knots K[j] = base[j] + theta[j] (base: exact int32
  * bin at the knot; theta: a bf16 residual), k^ = K[s] (1 - t) + K[s+1] t.
@@ -368,7 +373,10 @@ int hist_locator_loss_grad(int nseg, float u0, float u_scale, const int32_t *bas
  *   stats_out: device double [5] = [N, sum w, sum w^2, sum wx, sum wx^2].
  * values: device [n]; weights: device [n] or NULL (unit weights); flags: 0
  * or HIST_STAT_OVERFLOWS.  Same semantics and accuracy as hist_book +
- * hist_fill_bulk + hist_result on that bulk.  Asynchronous on `stream`.
+ * hist_fill_bulk + hist_result on that bulk.  Asynchronous on `stream`: the
+ * call only enqueues kernels (the axis thresholds reach the device as a
+ * kernel argument, not by a copy).  The fill runs at most 304 blocks (two
+ * per SM of a 152-SM GB300), the size the scratch's per-block region holds.
  * No device or host memory is allocated: the scratch is one fixed library
  * array of about 5 MB per device, held until the process exits.  The first
  * call on a device looks up that array's address (cudaGetSymbolAddress), so

@@ -999,7 +999,7 @@ int lm_certify(const LearnedDev& m, const long long* dT, int nbins, int* d_err, 
   if (launch_lm_certify(m, dT, nbins, d_err, nullptr) != 0) return HIST_ERR_CUDA;
   int err = 0;
   if (cudaMemcpy(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return HIST_ERR_CUDA;
-  *window = err + 1;  // one more bin covers FP32 non-monotonicity between the evaluated ends
+  *window = err;  // the largest error over every non-NaN coordinate (see learned.cu)
   return HIST_OK;
 }
 

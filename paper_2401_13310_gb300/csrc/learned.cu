@@ -11,9 +11,19 @@
 //   loss      L = (1/N) sum_i r_i^2
 //   backward  dL/dtheta[s_i] += 2 r_i (1 - t_i) / N,
 //             dL/dtheta[s_i + 1] += 2 r_i t_i / N
-// with K[j] = base[j] + theta[j].  The certifier evaluates the stored model
-// (bf16 residuals) at both ends of every bin with the fill's own device
-// function and records the largest index error.
+// with K[j] = base[j] + theta[j].  The certifier bounds the index error of
+// the stored model (bf16 residuals) over every non-NaN coordinate, with the
+// fill's own device function: within one segment the evaluated model is a
+// monotone function of the coordinate's key (each step -- truncation to
+// FP32, x - u0, the scaling, u - s, the fused multiply-add with fixed knots
+// -- is a correctly rounded monotone operation), and so is the rounded
+// index; the bin is constant on each bin's key range.  So on every run of
+// keys that lies in one bin and one segment, the error is largest at one
+// of the run's two ends, and every such end is a bin end, a segment end, or
+// an end of a monotone piece of the FP32 truncation (its saturation at
+// 2^128).  The certifier evaluates all of them; the largest error is the
+// window.  (A NaN coordinate's FP32 value does not follow its key; NaNs,
+// like any window miss, take the full binary search.)
 
 #include <cuda_runtime.h>
 
@@ -90,6 +100,63 @@ __device__ __forceinline__ unsigned long long bits_of_key(long long k) {
   return (k >= 0) ? (unsigned long long)k : ((unsigned long long)(-k) | 0x8000000000000000ull);
 }
 
+// Segment of the model at the FP32 value xf, as lm_eval computes it.
+__device__ __forceinline__ int lm_segment(const LearnedDev& m, float xf) {
+  float u = __fmul_rn(__fsub_rn(xf, m.u0), m.u_scale);
+  u = fmaxf(u, 0.0f);
+  return (int)fminf(u, (float)(m.nseg - 1));
+}
+
+// Bin of a key: the largest k in [0, nbins + 1] with T[k] <= key.
+__device__ __forceinline__ int bin_of_key(const long long* T, int nbins, long long key) {
+  int base = 0, len = nbins + 2;
+  while (len > 1) {
+    const int half = len >> 1;
+    base = (T[base + half] <= key) ? base + half : base;
+    len -= half;
+  }
+  return base;
+}
+
+__device__ __forceinline__ int key_error(const LearnedDev& m, const long long* T, int nbins, long long key) {
+  const float kh = lm_eval(m, trunc24(bits_of_key(key)));
+  const int k0 = (int)floorf(__fadd_rn(kh, 0.5f));
+  return abs(k0 - bin_of_key(T, nbins, key));
+}
+
+constexpr long long kKeyInf = 0x7FF0000000000000LL;  // key of +inf (-inf: its negation)
+constexpr long long kKey2p128 = 0x47F0000000000000LL;  // key of 2^128, where the FP32 truncation saturates
+
+// Segment boundaries and the ends of the truncation's monotone pieces:
+// thread b < nseg - 1 finds the first key of segment b + 1 (the model's
+// segment is monotone in the key between the saturation points; bisection
+// over keys) and evaluates that key and the one before it; the special
+// keys (+-inf, +-2^128 and their neighbours) are evaluated by thread 0.
+__global__ void __launch_bounds__(256) k_lm_certify_knots(const LearnedDev m, const long long* __restrict__ T,
+                                                          int nbins, int* __restrict__ max_err) {
+  int worst = 0;
+  const int nb = m.nseg - 1;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    // within [-(2^128) + 1 key, 2^128 - 1 key] the truncation is monotone
+    long long lo = -kKey2p128 + 1, hi = kKey2p128 - 1;
+    if (lm_segment(m, trunc24(bits_of_key(lo))) > b || lm_segment(m, trunc24(bits_of_key(hi))) <= b) continue;
+    while (hi - lo > 1) {  // invariant: segment(lo) <= b < segment(hi)
+      const long long mid = lo + ((hi - lo) >> 1);
+      if (lm_segment(m, trunc24(bits_of_key(mid))) <= b)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    worst = max(worst, max(key_error(m, T, nbins, lo), key_error(m, T, nbins, hi)));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const long long sp[8] = {-kKeyInf, -kKey2p128, -kKey2p128 + 1, kKey2p128 - 1, kKey2p128, kKeyInf, 0, -1};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) worst = max(worst, key_error(m, T, nbins, sp[i]));
+  }
+  atomicMax(max_err, worst);
+}
+
 // Largest |round(k^) - bin| over both ends of every bin (and the two flow
 // sides), evaluated with the fill's device function.
 __global__ void __launch_bounds__(256) k_lm_certify(const LearnedDev m, const long long* __restrict__ T, int nbins,
@@ -142,6 +209,10 @@ int launch_lm_certify(const LearnedDev& m, const long long* T, int nbins, int* m
   long long blocks = ((long long)nbins + 2 + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   k_lm_certify<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(m, T, nbins, max_err);
+  if (cudaGetLastError() != cudaSuccess) return -2;
+  long long kblocks = ((long long)m.nseg + 255) / 256;
+  if (kblocks > 152 * 8) kblocks = 152 * 8;
+  k_lm_certify_knots<<<(int)kblocks, 256, 0, (cudaStream_t)stream>>>(m, T, nbins, max_err);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

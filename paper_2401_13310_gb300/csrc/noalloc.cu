@@ -21,6 +21,14 @@
 // on the GPU (different streams, or different host threads, without
 // ordering between them) race on the array and give wrong results; order
 // them on one stream or with events.
+//
+// The axis thresholds travel to the device by value, as a kernel parameter
+// of the set-up kernel (at most 1025 keys, 8.2 KB), so no host-to-device
+// copy from pageable memory is needed: the call only enqueues kernels.
+// The fill runs at most kNoallocMaxGrid blocks (the per-block partials
+// region of the scratch is sized for that many); on a GPU whose regular
+// fill would launch more, this fill launches fewer, larger-strided blocks
+// (same results, possibly lower throughput).
 
 #include <cuda_runtime.h>
 
@@ -52,6 +60,16 @@ constexpr size_t kOffPartBins = kOffPartStats + 8 * kMaxStats * kNoallocMaxGrid;
 constexpr size_t kNoallocScratchBytes = kOffPartBins + 16 * (size_t)kNoallocMaxBins * kNoallocMaxGrid;
 static_assert(kOffLo >= 8 * (kNoallocMaxBins + 1), "threshold region too small");
 static_assert(kOffPartStats % 256 == 0 && kOffPartBins % 256 == 0, "misaligned scratch region");
+static_assert(kOffPartBins - kOffPartStats >= 8 * (size_t)kMaxStats * kNoallocMaxGrid,
+              "statistics partials region smaller than kNoallocMaxGrid blocks");
+static_assert((kOffPartStats - kOffLo) % 8 == 0, "accumulator region not a whole number of words");
+
+// The thresholds of one axis, passed by value to the set-up kernel.
+struct NoallocTable {
+  int64_t T[kNoallocMaxBins + 1];  // nbins + 3 keys
+  int nkeys;
+};
+static_assert(sizeof(NoallocTable) <= 32000, "kernel parameter beyond the 32 KB limit");
 
 // The scratch itself (about 5 MB).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
@@ -72,6 +90,27 @@ unsigned char* scratch_on_current_device(int device) {
   return g_scratch_ptr[device];
 }
 
+// Set-up of one call: the thresholds into the scratch, the accumulators
+// (fixed-point words, counts, binary64 words, statistics) to zero.
+__global__ void __launch_bounds__(256) k_noalloc_setup(const __grid_constant__ NoallocTable t,
+                                                      unsigned char* __restrict__ s) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  long long* T = reinterpret_cast<long long*>(s + kOffT);
+  for (int i = tid; i < t.nkeys; i += nthr) T[i] = t.T[i];
+  unsigned long long* z = reinterpret_cast<unsigned long long*>(s + kOffLo);
+  constexpr int kWords = (int)((kOffPartStats - kOffLo) / 8);
+  for (int i = tid; i < kWords; i += nthr) z[i] = 0ull;
+}
+
+// Neumaier's compensated addition (s, c) += v, as hist_result sums the
+// binary64 words.
+__device__ __forceinline__ void comp_add(double& s, double& c, double v) {
+  const double t = __dadd_rn(s, v);
+  if (isfinite(t))
+    c = __dadd_rn(c, fabs(s) >= fabs(v) ? __dadd_rn(__dsub_rn(s, t), v) : __dadd_rn(__dsub_rn(v, t), s));
+  s = t;
+}
+
 // Turn the exact accumulators into binary64 bin contents and statistics,
 // as hist_result does on the host: content = (fixed-point words + unit
 // entries) rounded once, plus the binary64 slow-path words; sum w is the
@@ -85,37 +124,39 @@ __global__ void __launch_bounds__(256) k_noalloc_finish(const unsigned char* __r
   const double* f64 = reinterpret_cast<const double*>(s + kOffF64);
   const double* st = reinterpret_cast<const double*>(s + kOffStats);
   __shared__ __int128 s_fx[256];
-  __shared__ double s_f64[256];
+  __shared__ double s_f64[256], s_c[256];
   __shared__ unsigned long long s_unit[256];
   const int shift = 1065 - fx_elo;
   const double lsb = ldexp(1.0, -shift);
   __int128 sel_fx = 0;
-  double sel_f64 = 0.0;
+  double sel_f64 = 0.0, sel_c = 0.0;
   unsigned long long sel_unit = 0;
   for (int g = threadIdx.x; g < nbins_total; g += blockDim.x) {
     const __int128 fx = ((__int128)hi[g] << 32) + (__int128)lo[g] + ((__int128)unit[g] << shift);
     bins_out[g] = __dadd_rn(__dmul_rn((double)fx, lsb), f64[g]);
     if (stat_all || (g >= 1 && g <= nbins)) {
       sel_fx += fx;
-      sel_f64 = __dadd_rn(sel_f64, f64[g]);
+      comp_add(sel_f64, sel_c, f64[g]);
       sel_unit += unit[g];
     }
   }
   s_fx[threadIdx.x] = sel_fx;
   s_f64[threadIdx.x] = sel_f64;
+  s_c[threadIdx.x] = sel_c;
   s_unit[threadIdx.x] = sel_unit;
   __syncthreads();
   if (threadIdx.x == 0) {
     __int128 a = 0;
-    double b = 0.0;
+    double b = 0.0, c = 0.0;
     unsigned long long u = 0;
     for (int t = 0; t < (int)blockDim.x; ++t) {
       a += s_fx[t];
-      b = __dadd_rn(b, s_f64[t]);
+      comp_add(b, c, s_f64[t]);
+      comp_add(b, c, s_c[t]);
       u += s_unit[t];
     }
     stats_out[0] = (double)n_entries;
-    stats_out[1] = __dadd_rn(__dmul_rn((double)a, lsb), b);
+    stats_out[1] = __dadd_rn(__dmul_rn((double)a, lsb), __dadd_rn(b, c));
     stats_out[2] = __dadd_rn(st[2], (double)u);
     stats_out[3] = st[3];
     stats_out[4] = st[4];
@@ -144,22 +185,21 @@ extern "C" int hist_fill_bulk_noalloc(const hist_axis_t* axis, const double* val
   if (s == nullptr) return HIST_ERR_CUDA;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
-  // thresholds on the host stack, copied into the scratch (a copy from
-  // pageable memory returns once the source has been read)
+  // thresholds built on the host, handed to the set-up kernel by value
+  // (with the zeroing of the accumulators, which start at zero every call)
   const int nb = axis->nbins;
-  int64_t T[kNoallocMaxBins + 1];
+  NoallocTable tab;
+  tab.nkeys = nb + 3;
   float scale = 0.0f, offset = 0.0f, eps = 1.0f;
   int32_t mode = LOC_BSEARCH;
   if (axis->kind == HIST_AXIS_FIXED) {
-    build_fixed_thresholds(nb, axis->xmin, axis->xmax, T);
+    build_fixed_thresholds(nb, axis->xmin, axis->xmax, tab.T);
     if (affine_estimate(nb, axis->xmin, axis->xmax, &scale, &offset, &eps)) mode = LOC_AFFINE;
   } else {
-    build_variable_thresholds(nb, axis->edges, T);
+    build_variable_thresholds(nb, axis->edges, tab.T);
   }
-  if (cudaMemcpyAsync(s + kOffT, T, sizeof(int64_t) * (size_t)(nb + 3), cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return HIST_ERR_CUDA;
-  // the accumulators start at zero for every call
-  if (cudaMemsetAsync(s + kOffLo, 0, kOffPartStats - kOffLo, st) != cudaSuccess) return HIST_ERR_CUDA;
+  k_noalloc_setup<<<8, 256, 0, st>>>(tab, s);
+  if (cudaGetLastError() != cudaSuccess) return HIST_ERR_CUDA;
 
   if (n > 0) {
     const int acc = (weights == nullptr) ? ACC_UNIT : ACC_FX;
