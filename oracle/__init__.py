@@ -263,21 +263,37 @@ def fill(axes, values, weights=None, stat_overflows: bool = False,
 
 
 def exact_stats(axes, values, weights=None, stat_overflows: bool = False):
-    """1D statistics as the exact sums of their rounded terms (R6: w, w*w,
-    w*x, (w*x)*x, binary64), each rounded once (math.fsum is the correctly
-    rounded sum of its inputs), over the in-range entries (R5).  Returns
-    [sum w, sum w^2, sum wx, sum wx^2]; NaN when a term is NaN or infinities
-    of both signs meet, +-inf for infinities of one sign."""
-    assert len(axes) == 1
-    x = np.asarray(values, dtype=np.float64).reshape(-1)
-    w = np.ones_like(x) if weights is None else np.asarray(weights, dtype=np.float64)
-    b = locate(axes, x.reshape(1, -1))
-    nb = nbins_total(axes)
-    m = np.ones(x.shape[0], dtype=bool) if stat_overflows else (b >= 1) & (b <= nb - 2)
-    x, w = x[m], w[m]
+    """The statistics as the exact sums of their rounded terms, each sum
+    rounded once (math.fsum is the correctly rounded sum of its inputs),
+    over the in-range entries (R5: every axis in range).  The terms are
+    those of R6, binary64, each product rounded left to right: 1D w, w*w,
+    w*x, (w*x)*x; 2D adds w*y, (w*y)*y, (w*x)*y; 3D adds w*z, (w*z)*z,
+    (w*x)*z, (w*y)*z.  Returns [sum w, sum w^2, sum wx, ...] (4, 7 or 11
+    values); NaN when a term is NaN or infinities of both signs meet, +-inf
+    for infinities of one sign."""
+    ndim = len(axes)
+    v = np.asarray(values, dtype=np.float64).reshape(ndim, -1)
+    n = v.shape[1]
+    w = np.ones(n) if weights is None else np.asarray(weights, dtype=np.float64)
+    m = np.ones(n, dtype=bool)
+    if not stat_overflows:
+        for d, ax in enumerate(axes):
+            b = locate([ax], v[d].reshape(1, -1))
+            nb = nbins_total([ax])
+            m &= (b >= 1) & (b <= nb - 2)
+    v, w = v[:, m], w[m]
     with np.errstate(all="ignore"):
+        x = v[0]
         wx = w * x
         terms = [w, w * w, wx, wx * x]
+        if ndim >= 2:
+            y = v[1]
+            wy = w * y
+            terms += [wy, wy * y, wx * y]
+        if ndim >= 3:
+            z = v[2]
+            wz = w * z
+            terms += [wz, wz * z, wx * z, wy * z]
     out = []
     for t in terms:
         if np.isnan(t).any() or (np.isposinf(t).any() and np.isneginf(t).any()):

@@ -476,6 +476,37 @@ def check_exact_stats_vs_fractions(seed=12):
     w3 = w.copy()
     w3[int(np.flatnonzero(m)[1])] = math.inf
     assert oracle.exact_stats(axes, x, w3)[0] == math.inf
+    # 2D and 3D: ROOT's TH2/TH3 term sets (R6), an entry taken only when
+    # every axis is in range, per-event terms from Python float arithmetic
+    for ndim in (2, 3):
+        axs = [oracle_axis_fixed(10, -2.0, 2.0), {"kind": "variable", "edges": np.array([-1.0, 0.0, 0.5, 3.0])},
+               oracle_axis_fixed(7, -1.5, 2.5)][:ndim]
+        v = np.stack([rng.normal(0, 1.2, 300), rng.normal(0.5, 1.0, 300), rng.normal(0.2, 1.3, 300)][:ndim])
+        w = rng.uniform(-3, 3, 300) * 10.0 ** rng.integers(-9, 9, 300)
+        got = oracle.exact_stats(axs, v, w)
+        lo = [-2.0, -1.0, -1.5]
+        hi = [2.0, 3.0, 2.5]
+        sel = [i for i in range(300) if all(lo[d] <= v[d, i] < hi[d] for d in range(ndim))]
+        assert 50 < len(sel) < 300
+        rows = []
+        for i in sel:
+            wi, xi = float(w[i]), float(v[0, i])
+            wxi = wi * xi
+            r = [wi, wi * wi, wxi, wxi * xi]
+            if ndim >= 2:
+                yi = float(v[1, i])
+                wyi = wi * yi
+                r += [wyi, wyi * yi, wxi * yi]
+            if ndim >= 3:
+                zi = float(v[2, i])
+                wzi = wi * zi
+                r += [wzi, wzi * zi, wxi * zi, wyi * zi]
+            rows.append(r)
+        nterm = {2: 7, 3: 11}[ndim]
+        assert len(got) == nterm
+        for k in range(nterm):
+            want = float(sum(Fraction(r[k]) for r in rows))
+            assert got[k] == want, (ndim, k, got[k], want)
 
 
 def check_chunk_parallel_fill_and_locate(seed=13):
