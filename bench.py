@@ -256,10 +256,35 @@ def measure_paper_histo1d(B, W, hbm: float, n: int) -> dict:
     return res
 
 
+def measure_nd(B, W, hbm: float, n: int) -> dict:
+    """The 2D (1000 x 1000 bins, correlated Gaussian pairs) and 3D (100^3
+    bins, uniform triples) weighted fills: global-memory bins, one 64-bit
+    integer atomic per event; fill kernel alone (library event pairs)."""
+    import torch
+    out = {}
+    for tag, cfg, bpe in (("3a_2d_1000x1000", W.cfg3a, 24), ("3b_3d_100x100x100", W.cfg3b, 32)):
+        wl = cfg(n=n, device="cuda")
+        h = B.Hist(wl.axes)
+        for _ in range(3):
+            h.fill(wl.values, wl.weights)
+        torch.cuda.synchronize()
+        B.hist_set_kernel_timing(h.h, True)
+        call_ms = _timed(lambda: h.fill(wl.values, wl.weights), 20)
+        ms, k = B.hist_kernel_time(h.h)
+        h.close()
+        out[tag] = {"kernel_ms": ms / k, "call_ms": call_ms, "gev_per_s": n / (ms / k * 1e-3) / 1e9,
+                    "hbm_frac": bpe * n / (ms / k * 1e-3) / 1e9 / hbm}
+        del wl
+        torch.cuda.empty_cache()
+    return out
+
+
 def measure_forms(B, W, hbm: float, args) -> dict:
     """The batched and learned forms beside the plain one, same GPU."""
+    import numpy as np
     import torch
     out = {"precision": measure_precisions(B, W, hbm, args.events),
+           "nd": measure_nd(B, W, hbm, args.events),
            "filter_define": measure_filter_define(B, W, hbm, args.events),
            "paper_histo1d": measure_paper_histo1d(B, W, hbm, 2 * args.events)}
     # batched: 64 histograms (10 .. 1e5 bins, fixed and variable) on the
@@ -277,8 +302,31 @@ def measure_forms(B, W, hbm: float, args) -> dict:
     t_plain = _timed(plain4, 3)
     batch = B.Batch(hists, bw.col_of_hist, B.HIST_BATCH_GRAPH)
     tune = batch.tune([c[:4_000_000] for c in cols], w[:4_000_000])
+    for h in hists:
+        h.reset()
+    batch.fill(cols, w)
+    exact_bins = [h.result()[0] for h in hists]  # one fill: the exact fixed-point bins
     t_fused = _timed(lambda: batch.fill(cols, w), 3)
     nh = len(hists)
+    batch.close()
+    for h in hists:
+        h.close()
+    # the same batch with FP32 compensated shared-memory partials
+    hists = [B.Hist([ax], B.HIST_PREC_FP32C) for ax in bw.axes]
+    batch = B.Batch(hists, bw.col_of_hist, B.HIST_BATCH_GRAPH)
+    tune_c = batch.tune([c[:4_000_000] for c in cols], w[:4_000_000])
+    for h in hists:
+        h.reset()
+    batch.fill(cols, w)
+    dev = 0.0
+    for h, ref in zip(hists, exact_bins):
+        got = h.result()[0]
+        # weights are positive: a bin's exact content is its sum of |w|
+        dev = max(dev, float(np.max(np.abs(got - ref) / np.maximum(ref, 1e-300))))
+    t_fused_c = _timed(lambda: batch.fill(cols, w), 3)
+    batch.close()
+    for h in hists:
+        h.close()
     out["batched64"] = {
         "events": n4, "histograms": nh,
         "plain_ms": t_plain, "fused_ms": t_fused, "fused_speedup": t_plain / t_fused,
@@ -287,10 +335,11 @@ def measure_forms(B, W, hbm: float, args) -> dict:
         "plain_hbm_frac": 16 * n4 * nh / (t_plain * 1e-3) / 1e9 / hbm,
         "fused_hbm_frac": 32 * n4 / (t_fused * 1e-3) / 1e9 / hbm,
         "tuning": tune,
+        "fused_fp32c_ms": t_fused_c, "fused_fp32c_speedup": t_plain / t_fused_c, "tuning_fp32c": tune_c,
+        "fp32c_max_rel_dev_per_bin": dev,
+        "fp32c_note": "per-bin |FP32C - exact fixed point| / exact (weights > 0: the exact content is the bin's "
+                      "sum |w|; the fixed-point bins are within 2^-42 of it, pinned against the oracle by the tests)",
     }
-    batch.close()
-    for h in hists:
-        h.close()
     del cols, w
     torch.cuda.empty_cache()
     # learned locator: 8 variable axes, 1e4 .. 1e6 mixture-quantile edges,

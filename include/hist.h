@@ -75,15 +75,17 @@ typedef struct {
 #define HIST_TRACK_COUNTS (1u << 0)   /* keep per-bin entry counts for weighted fills */
 #define HIST_STAT_OVERFLOWS (1u << 1) /* include under/overflow entries in the statistics */
 #define HIST_SUMW2 (1u << 2)          /* also keep each bin's sum of squared weights (ROOT's Sumw2) */
-/* HIST_STATS_EXACT (1D): the statistics sum w, w^2, w*x, w*x^2 become the
- * exact sums of their rounded terms (w, fl(w*w), fl(w*x), fl(fl(w*x)*x)),
- * rounded once to binary64 -- bit-reproducible whatever the launch shape,
- * the order of atomics or the split into fills, and equal to a correctly
- * rounded exact sum (math.fsum) of the same terms.  A second pass over
- * each bulk accumulates them in integer limbs on a per-statistic grid (an
- * escape accumulator takes the terms outside it); it costs one more read
- * of the bulk.  Not with hist_fill_columns or batches
- * (HIST_ERR_UNSUPPORTED); ND histograms: HIST_ERR_UNSUPPORTED at booking. */
+/* HIST_STATS_EXACT: the statistics become the exact sums of their rounded
+ * terms -- 1D w, fl(w*w), fl(w*x), fl(fl(w*x)*x); 2D adds fl(w*y),
+ * fl(fl(w*y)*y), fl(fl(w*x)*y); 3D adds fl(w*z), fl(fl(w*z)*z),
+ * fl(fl(w*x)*z), fl(fl(w*y)*z) -- rounded once to binary64:
+ * bit-reproducible whatever the launch shape, the order of atomics or the
+ * split into fills, and equal to a correctly rounded exact sum (math.fsum)
+ * of the same terms.  Extra passes over each bulk (one per four
+ * statistics: one in 1D, two in 2D, three in 3D) accumulate them in
+ * integer limbs on a per-statistic grid (an escape accumulator takes the
+ * terms outside it).  Not with hist_fill_columns or batches
+ * (HIST_ERR_UNSUPPORTED). */
 #define HIST_STATS_EXACT (1u << 3)
 /* Accumulation of weighted bin contents (bits 4-5):
  *   HIST_PREC_FP64   (default) exact fixed-point sums of each weight truncated
@@ -251,7 +253,12 @@ int hist_kernel_time(hist_t *h, double *ms, int64_t *launches);
  *             together so that each event is read from HBM once (from L2
  *             by the other slices).
  * Histograms that share a column and range share their statistics sums.
- * Results and accuracy per histogram are those of hist_fill_bulk. */
+ * Results and accuracy per histogram are those of hist_fill_bulk.
+ * Precision: a batch whose members are all booked with HIST_PREC_FP32C
+ * runs the FP32 compensated form (wide strategy only): small histograms
+ * keep per-block FP32 (hi, lo) bins with TwoSum on the atomic's old value,
+ * flushed in binary64; large ones take binary64 atomics.  Every other batch
+ * keeps exact fixed-point bins (as HIST_PREC_FP64). */
 typedef struct hist_batch hist_batch_t;
 
 #define HIST_BATCH_GRAPH (1u << 0)  /* replay the fill's launches as a cached CUDA graph */
@@ -263,7 +270,9 @@ typedef struct hist_batch hist_batch_t;
  * pairs (statistics groups).
  * The batch references the histograms (they must outlive it) and owns its
  * device descriptors and scratch.  Errors: HIST_ERR_ARG, HIST_ERR_UNSUPPORTED
- * (ND histogram, more than 16 statistics groups), HIST_ERR_OOM, HIST_ERR_CUDA. */
+ * (ND histogram, more than 16 statistics groups, HIST_PREC_FP32C members
+ * mixed with others, or all FP32C with HIST_BATCH_SLICED), HIST_ERR_OOM,
+ * HIST_ERR_CUDA. */
 int hist_batch_create(hist_t *const *hists, int nh, const int32_t *col_of_hist, uint32_t flags,
                       hist_batch_t **out);
 

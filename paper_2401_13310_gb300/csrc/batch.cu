@@ -18,6 +18,13 @@
 //    so the order does not matter);
 //  * large histograms add every event to the global accumulators with two
 //    64-bit integer atomics (exact);
+//  * a batch of histograms booked with HIST_PREC_FP32C runs the FP32
+//    compensated form instead: each weight split into FP32 hi + lo once per
+//    event; a small histogram's shared bin is an FP32 (hi, lo) pair, hi
+//    added by an atomic whose returned old value gives the rounding error
+//    exactly (TwoSum), which goes with lo to the lo word; blocks add their
+//    pairs into the binary64 bins in binary64 at the end; large histograms
+//    take binary64 atomics (one per event);
 //  * statistics are shared by the histograms with the same column and range
 //    and accumulated once per event for the column's common core (see
 //    batch_stats.cuh), binary64 per thread: the binary64 pipe is otherwise
@@ -34,6 +41,23 @@
 namespace hgb {
 namespace {
 
+
+// FP32 compensated form: W = hi + lo of the weight (wok: in the double-word
+// range; other weights take a binary64 atomic).
+template <bool SMEM>
+__device__ __forceinline__ void batch_add_f32c(const BatchHistDev& d, unsigned* sbins, int k, FF W, bool wok,
+                                               unsigned long long wb) {
+  if (!SMEM || !wok) {
+    atomicAdd(&d.g_f64[k], __longlong_as_double((long long)wb));
+    return;
+  }
+  float* a = reinterpret_cast<float*>(&sbins[d.sbin_off + 2 * k]);
+  const float old = atomicAdd(a, W.hi);
+  const float sum = __fadd_rn(old, W.hi);
+  const float bv = __fsub_rn(sum, old);
+  const float err = __fadd_rn(__fsub_rn(old, __fsub_rn(sum, bv)), __fsub_rn(W.hi, bv));
+  atomicAdd(a + 1, __fadd_rn(err, W.lo));
+}
 
 template <bool UNIT, bool SMEM>
 __device__ __forceinline__ void batch_add(const BatchHistDev& d, unsigned* sbins, int k, long long V, bool wok,
@@ -71,7 +95,24 @@ __device__ __forceinline__ void batch_add(const BatchHistDev& d, unsigned* sbins
   }
 }
 
-template <bool UNIT, int MINB, int KEV>
+// One event's bin update for one histogram, in the batch's precision.
+template <bool UNIT, bool F32C>
+__device__ __forceinline__ void batch_update(const BatchHistDev& d, unsigned* sbins, bool in_smem, int k, long long V,
+                                             FF W, bool wok, unsigned long long wb) {
+  if (F32C && !UNIT) {
+    if (in_smem)
+      batch_add_f32c<true>(d, sbins, k, W, wok, wb);
+    else
+      batch_add_f32c<false>(d, sbins, k, W, wok, wb);
+  } else {
+    if (in_smem)
+      batch_add<UNIT, true>(d, sbins, k, V, wok, wb);
+    else
+      batch_add<UNIT, false>(d, sbins, k, V, wok, wb);
+  }
+}
+
+template <bool UNIT, bool F32C, int MINB, int KEV>
 __global__ void __launch_bounds__(256, MINB) k_batch_fill(const __grid_constant__ BatchParams p) {
   constexpr int kEv = KEV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -112,14 +153,23 @@ __global__ void __launch_bounds__(256, MINB) k_batch_fill(const __grid_constant_
     bool valid[kEv];
     unsigned long long wb[kEv];
     long long V[kEv];
+    FF W[kEv];
     bool wok[kEv];
 #pragma unroll
     for (int e = 0; e < kEv; ++e) {
       const long long i = base + e * nthreads;
       valid[e] = i < n;
       wb[e] = (UNIT || !valid[e]) ? 0x3FF0000000000000ull : __ldcs(wq + i);
-      wok[e] = UNIT ? true : fx_of(wb[e], p.fx_elo, &V[e]);
-      if (UNIT) V[e] = 0;
+      V[e] = 0;
+      W[e].hi = W[e].lo = 0.0f;
+      if (UNIT) {
+        wok[e] = true;
+      } else if (F32C) {
+        wok[e] = in_ff(exp_field(wb[e]));
+        if (wok[e]) W[e] = ff_split(wb[e], hi24(wb[e]));
+      } else {
+        wok[e] = fx_of(wb[e], p.fx_elo, &V[e]);
+      }
     }
 #pragma unroll
     for (int c = 0; c < kBatchMaxCols; ++c) {
@@ -153,20 +203,14 @@ __global__ void __launch_bounds__(256, MINB) k_batch_fill(const __grid_constant_
 #pragma unroll
           for (int e = 0; e < kEv; ++e) {
             if (!valid[e]) continue;
-            if (in_smem)
-              batch_add<UNIT, true>(d, sbins, k[e], V[e], wok[e], wb[e]);
-            else
-              batch_add<UNIT, false>(d, sbins, k[e], V[e], wok[e], wb[e]);
+            batch_update<UNIT, F32C>(d, sbins, in_smem, k[e], V[e], W[e], wok[e], wb[e]);
           }
         } else {
 #pragma unroll
           for (int e = 0; e < kEv; ++e) {
             if (!valid[e]) continue;
             const int k = locate_axis(d.ax, T, Thi, d.ax.bk.cnt, xb[e], xf[e], f32ok[e]);
-            if (in_smem)
-              batch_add<UNIT, true>(d, sbins, k, V[e], wok[e], wb[e]);
-            else
-              batch_add<UNIT, false>(d, sbins, k, V[e], wok[e], wb[e]);
+            batch_update<UNIT, F32C>(d, sbins, in_smem, k, V[e], W[e], wok[e], wb[e]);
           }
         }
       }
@@ -189,6 +233,10 @@ __global__ void __launch_bounds__(256, MINB) k_batch_fill(const __grid_constant_
       if (UNIT) {
         const unsigned c = sbins[d.sbin_off + k];
         if (c) atomicAdd(&d.g_unit[k], (unsigned long long)c);
+      } else if (F32C) {
+        const float* f = reinterpret_cast<const float*>(&sbins[d.sbin_off + 2 * k]);
+        const double v = __dadd_rn((double)f[0], (double)f[1]);
+        if (v != 0.0) atomicAdd(&d.g_f64[k], v);
       } else {
         const unsigned a0 = sbins[d.sbin_off + 2 * k], a1 = sbins[d.sbin_off + 2 * k + 1];
         if (a0) atomicAdd(&d.g_lo[k], (unsigned long long)a0);
@@ -221,38 +269,45 @@ __global__ void k_batch_reduce(const BatchReduceParams r) {
 
 // The compiled variants: blocks per SM the registers allow (2 or 4) times
 // events per thread (2 or 4).
-const void* batch_fn(bool unit, int minb, int kev) {
-#define HGB_BATCH(U, M, K) \
-  if (unit == U && minb == M && kev == K) return reinterpret_cast<const void*>(&k_batch_fill<U, M, K>);
-  HGB_BATCH(false, 2, 4)
-  HGB_BATCH(false, 2, 2)
-  HGB_BATCH(false, 4, 4)
-  HGB_BATCH(false, 4, 2)
-  HGB_BATCH(true, 2, 4)
-  HGB_BATCH(true, 2, 2)
-  HGB_BATCH(true, 4, 4)
-  HGB_BATCH(true, 4, 2)
+// events per thread (2 or 4), and the precision of weighted batches
+// (exact fixed point or FP32 compensated).
+const void* batch_fn(bool unit, bool f32c, int minb, int kev) {
+#define HGB_BATCH(U, F, M, K) \
+  if (unit == U && f32c == F && minb == M && kev == K) return reinterpret_cast<const void*>(&k_batch_fill<U, F, M, K>);
+  HGB_BATCH(false, false, 2, 4)
+  HGB_BATCH(false, false, 2, 2)
+  HGB_BATCH(false, false, 4, 4)
+  HGB_BATCH(false, false, 4, 2)
+  HGB_BATCH(false, true, 2, 4)
+  HGB_BATCH(false, true, 2, 2)
+  HGB_BATCH(false, true, 4, 4)
+  HGB_BATCH(false, true, 4, 2)
+  HGB_BATCH(true, false, 2, 4)
+  HGB_BATCH(true, false, 2, 2)
+  HGB_BATCH(true, false, 4, 4)
+  HGB_BATCH(true, false, 4, 2)
 #undef HGB_BATCH
   return nullptr;
 }
 
 int batch_max_blocks_per_sm(int block, size_t smem, int minb, int kev, int* per_sm) {
-  const void* fn = batch_fn(false, minb, kev);
-  const void* fu = batch_fn(true, minb, kev);
-  if (fn == nullptr || fu == nullptr) return -1;
-  {  // always: it also loads the kernel before the occupancy query
+  int least = 1 << 30;
+  for (int v = 0; v < 3; ++v) {  // weighted fixed point, weighted FP32 compensated, unit
+    const void* fn = batch_fn(v == 2, v == 1, minb, kev);
+    if (fn == nullptr) return -1;
+    // always: it also loads the kernel before the occupancy query
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;
-    if (cudaFuncSetAttribute(fu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;
+    int a = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fn, block, smem) != cudaSuccess) return -2;
+    least = a < least ? a : least;
   }
-  int a = 0, b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fn, block, smem) != cudaSuccess) return -2;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fu, block, smem) != cudaSuccess) return -2;
-  *per_sm = a < b ? a : b;
+  *per_sm = least;
   return 0;
 }
 
-int launch_batch_fill(const BatchParams& p, int block, int grid, size_t smem, int minb, int kev, void* stream) {
-  const void* fn = batch_fn(p.w == nullptr, minb, kev);
+int launch_batch_fill(const BatchParams& p, int block, int grid, size_t smem, int minb, int kev, bool f32c,
+                      void* stream) {
+  const void* fn = batch_fn(p.w == nullptr, f32c && p.w != nullptr, minb, kev);
   if (fn == nullptr) return -1;
   {  // always: it also loads the kernel before the occupancy query
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -2;

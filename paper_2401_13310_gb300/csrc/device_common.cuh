@@ -236,7 +236,7 @@ __device__ __forceinline__ int locate_axis(const AxisDev& a, const long long* T,
     // clamp below puts k in the right flow bin.
     const float v = __fmaf_rn(xf, a.scale, a.offset);
     const float t = __fadd_rd(v, kMagic);
-    int k = __float_as_int(t) - 0x4B400000;
+    int k = (int)(__float_as_uint(t) - 0x4B400000u);  // (unsigned: no signed overflow for t < 0)
     const float fr = __fsub_rn(v, __fsub_rn(t, kMagic));
     const bool sure = f32ok && (fabsf(__fsub_rn(fr, 0.5f)) < 0.5f - a.eps);
     k = min(max(k, 0), a.nbins + 1);
@@ -278,7 +278,7 @@ __device__ __forceinline__ int locate_mode(const AxisDev& a, const long long* T,
   if (LOC == LOC_AFFINE) {  // as in locate_axis
     const float v = __fmaf_rn(xf, a.scale, a.offset);
     const float t = __fadd_rd(v, kMagic);
-    int k = __float_as_int(t) - 0x4B400000;
+    int k = (int)(__float_as_uint(t) - 0x4B400000u);  // (unsigned: no signed overflow for t < 0)
     const float fr = __fsub_rn(v, __fsub_rn(t, kMagic));
     const bool sure = f32ok && (fabsf(__fsub_rn(fr, 0.5f)) < 0.5f - a.eps);
     k = min(max(k, 0), a.nbins + 1);

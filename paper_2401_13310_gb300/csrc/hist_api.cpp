@@ -83,7 +83,7 @@ struct hist {
   unsigned long long* g_passed = nullptr;  // entries of filtered fills (counted on the device)
   // HIST_STATS_EXACT: limbs, escape limbs and special-term counts of the 4 statistics
   long long* d_exact = nullptr;
-  int32_t exact_grid[kExactStats] = {0, 0, 0, 0};
+  int32_t exact_grid[kExactStats] = {};
   int64_t exact_launches = 0;
   double* g_stats = nullptr;
   int64_t n_entries = 0;
@@ -342,17 +342,24 @@ int fill_impl(hist* h, const double* values, const double* weights, int64_t n, c
     if (ex != nullptr) return HIST_ERR_UNSUPPORTED;
     ExactParams e;
     std::memset(&e, 0, sizeof(e));
-    e.x = values;
+    for (int d = 0; d < h->ndim; ++d) {
+      e.col[d] = values + (size_t)d * (size_t)n;
+      e.lo_key[d] = h->T_host[d][1];
+      e.hi_key[d] = h->T_host[d][h->nbins[d] + 1];
+    }
     e.w = weights;
     e.n = n;
-    e.lo_key = h->T_host[0][1];
-    e.hi_key = h->T_host[0][h->nbins[0] + 1];
+    e.ndim = h->ndim;
     e.stat_overflows = (h->flags & HIST_STAT_OVERFLOWS) ? 1 : 0;
     for (int k = 0; k < kExactStats; ++k) e.grid[k] = h->exact_grid[k];
     e.limbs = h->d_exact;
     e.escape = h->d_exact + kExactStats * kExactLimbs;
     e.special = reinterpret_cast<unsigned long long*>(h->d_exact + kExactStats * (kExactLimbs + kEscapeLimbs));
-    if (launch_stats_exact(e, weights == nullptr, h->sm_count, stream) != 0) return HIST_ERR_CUDA;
+    // statistics 1 .. nstats-1, up to kExactGroup per pass over the bulk
+    for (e.s0 = 0; e.s0 < h->nstats - 1; e.s0 += kExactGroup) {
+      e.ns = std::min(kExactGroup, h->nstats - 1 - e.s0);
+      if (launch_stats_exact(e, weights == nullptr, h->sm_count, stream) != 0) return HIST_ERR_CUDA;
+    }
     if (++h->exact_launches % 1024 == 0 && launch_exact_normalise(h->d_exact, stream) != 0) return HIST_ERR_CUDA;
   }
   if (acc == ACC_FX && !p.smem_bins) {
@@ -652,23 +659,25 @@ int hist_book(const hist_axis_t* axes, int ndim, uint32_t flags, hist_t** out) {
     if ((flags & HIST_SUMW2) && (rc = dalloc(&h->g_sumw2, nb * 8)) != HIST_OK) break;
     if ((rc = dalloc(&h->g_passed, 8)) != HIST_OK) break;
     if (flags & HIST_STATS_EXACT) {
-      if (ndim != 1) {
-        rc = HIST_ERR_UNSUPPORTED;
-        break;
-      }
       if ((rc = dalloc(&h->d_exact, kExactBytes)) != HIST_OK) break;
-      // grids: the statistic's largest expected term 2^T (|w| < 2^16, |x| < 2^X
-      // over the in-range coordinates) sets its 127-binade fast window
-      const double lo = axes[0].kind == HIST_AXIS_FIXED ? axes[0].xmin : axes[0].edges[0];
-      const double hi = axes[0].kind == HIST_AXIS_FIXED ? axes[0].xmax : axes[0].edges[axes[0].nbins];
-      int X = 64;
-      if (!(flags & HIST_STAT_OVERFLOWS)) {
-        int e = 0;
-        std::frexp(std::max(std::fabs(lo), std::fabs(hi)), &e);
-        X = e;  // |x| < 2^e
+      // grids: the statistic's largest expected term 2^T (|w| < 2^16, each
+      // coordinate |c_d| < 2^X_d over its in-range values) sets its
+      // 127-binade fast window
+      int X[kMaxDim] = {64, 64, 64};
+      for (int d = 0; d < ndim; ++d) {
+        const double lo = axes[d].kind == HIST_AXIS_FIXED ? axes[d].xmin : axes[d].edges[0];
+        const double hi = axes[d].kind == HIST_AXIS_FIXED ? axes[d].xmax : axes[d].edges[axes[d].nbins];
+        if (!(flags & HIST_STAT_OVERFLOWS)) {
+          int e = 0;
+          std::frexp(std::max(std::fabs(lo), std::fabs(hi)), &e);
+          X[d] = e;  // |c_d| < 2^e
+        }
       }
       const int Wb = 16;
-      const int T[kExactStats] = {Wb, 2 * Wb, Wb + X, Wb + 2 * X};
+      // w, w^2, wx, wx^2, wy, wy^2, wxy, wz, wz^2, wxz, wyz
+      const int T[kExactStats] = {Wb,        2 * Wb,           Wb + X[0],        Wb + 2 * X[0],
+                                  Wb + X[1], Wb + 2 * X[1],    Wb + X[0] + X[1], Wb + X[2],
+                                  Wb + 2 * X[2], Wb + X[0] + X[2], Wb + X[1] + X[2]};
       for (int k = 0; k < kExactStats; ++k) h->exact_grid[k] = std::max(T[k] - 52 - kExactFastTop, -1074);
     }
     if (cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess) {
@@ -881,7 +890,7 @@ int hist_result(hist_t* h, double* bins, double* stats) {
       const long long* esc = limbs + kExactStats * kExactLimbs;
       const unsigned long long* sp =
           reinterpret_cast<const unsigned long long*>(esc + kExactStats * kEscapeLimbs);
-      for (int k = 0; k < kExactStats; ++k)
+      for (int k = 0; k < h->nstats - 1; ++k)
         s[1 + k] = exact_round(limbs + k * kExactLimbs, h->exact_grid[k], esc + k * kEscapeLimbs, sp + 3 * k);
     }
     for (int k = 0; k < h->nstats; ++k) stats[k] = s[k];
@@ -1158,6 +1167,7 @@ struct hist_batch {
   int ncols = 0;             // columns referenced (max column + 1)
   int device = 0, sm_count = 0;
   uint32_t flags = 0;
+  bool f32c = false;         // every member booked HIST_PREC_FP32C: the FP32 compensated wide kernel
   int col_begin[kBatchMaxCols + 1] = {};
   BatchStatsSpec st = {};     // statistics groups and the cores of the columns
   int group_col[kBatchMaxGroups] = {};
@@ -1563,6 +1573,7 @@ int batch_part_stats(hist_batch* b) {
 }
 
 int slice_configure(hist_batch* b, int budget, double cap) {
+  if (b->f32c) return HIST_ERR_UNSUPPORTED;  // the sliced kernel keeps exact fixed-point bins only
   int maxopt = 0;
   if (cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess)
     return HIST_ERR_CUDA;
@@ -1696,7 +1707,7 @@ int batch_launch(const hist_batch* b, const double* const* cols, const double* w
     if (launch_slice_fill(p, kSliceBlock, b->grid, b->smem, s) != 0) return HIST_ERR_CUDA;
   } else {
     const BatchParams p = batch_params(b, cols, weights, n, tune);
-    if (launch_batch_fill(p, 256, b->grid, b->smem, b->wide_minb, b->wide_kev, s) != 0) return HIST_ERR_CUDA;
+    if (launch_batch_fill(p, 256, b->grid, b->smem, b->wide_minb, b->wide_kev, b->f32c, s) != 0) return HIST_ERR_CUDA;
   }
   BatchReduceParams r;
   std::memset(&r, 0, sizeof(r));
@@ -1719,8 +1730,10 @@ extern "C" int hist_batch_create(hist_t* const* hists, int nh, const int32_t* co
   if ((flags & HIST_BATCH_WIDE) && (flags & HIST_BATCH_SLICED)) return HIST_ERR_ARG;
   *out = nullptr;
   const uint32_t stat_flag = hists[0] ? (hists[0]->flags & HIST_STAT_OVERFLOWS) : 0;
+  int n_f32c = 0;
   for (int i = 0; i < nh; ++i) {
     if (hists[i] == nullptr || col_of_hist[i] < 0 || col_of_hist[i] >= kBatchMaxCols) return HIST_ERR_ARG;
+    n_f32c += hists[i]->acc_mode == ACC_F32C ? 1 : 0;
     if (hists[i]->ndim != 1) return HIST_ERR_UNSUPPORTED;
     if (hists[i]->flags & (HIST_SUMW2 | HIST_STATS_EXACT)) return HIST_ERR_UNSUPPORTED;
     if (hists[i]->device != hists[0]->device) return HIST_ERR_ARG;
@@ -1728,11 +1741,15 @@ extern "C" int hist_batch_create(hist_t* const* hists, int nh, const int32_t* co
     for (int j = 0; j < i; ++j)
       if (hists[j] == hists[i]) return HIST_ERR_ARG;
   }
+  // one precision per batch: every member FP32 compensated, or none
+  if (n_f32c != 0 && n_f32c != nh) return HIST_ERR_UNSUPPORTED;
+  if (n_f32c == nh && (flags & HIST_BATCH_SLICED)) return HIST_ERR_UNSUPPORTED;
   hist_batch* b = new (std::nothrow) hist_batch();
   if (b == nullptr) return HIST_ERR_OOM;
   int rc = HIST_OK;
   do {
     b->flags = flags;
+    b->f32c = n_f32c == nh;
     b->device = hists[0]->device;
     b->sm_count = hists[0]->sm_count;
     if (cudaSetDevice(b->device) != cudaSuccess) {
@@ -1845,7 +1862,7 @@ extern "C" int hist_batch_create(hist_t* const* hists, int nh, const int32_t* co
     if ((rc = batch_configure(b, 96 * 1024)) != HIST_OK) break;
     bool all_shared = true;
     for (int o : b->sbin_off) all_shared &= o >= 0;
-    if ((flags & HIST_BATCH_SLICED) || (!all_shared && !(flags & HIST_BATCH_WIDE)))
+    if (!b->f32c && ((flags & HIST_BATCH_SLICED) || (!all_shared && !(flags & HIST_BATCH_WIDE))))
       rc = slice_configure(b, kSliceDefaultBudget, kSliceDefaultCap);
   } while (false);
   if (rc != HIST_OK) {

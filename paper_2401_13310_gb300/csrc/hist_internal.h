@@ -98,18 +98,22 @@ struct ExprDev {
   unsigned long long* g_passed;  // events that passed the filters (entry count)
 };
 
-// Exactly summed statistics (HIST_STATS_EXACT, 1D): see stats_exact.cu.
-constexpr int kExactStats = 4;     // sum w, sum w^2, sum wx, sum wx^2
+// Exactly summed statistics (HIST_STATS_EXACT): see stats_exact.cu.
+constexpr int kExactStats = 11;    // statistics slots 1..11: sum w, w^2, wx, wx^2 (1D), + wy, wy^2, wxy (2D),
+                                   // + wz, wz^2, wxz, wyz (3D)
+constexpr int kExactGroup = 4;     // statistics summed in one pass (their limbs live in registers)
 constexpr int kExactLimbs = 6;     // radix-2^32 limbs per statistic
 constexpr int kExactFastTop = 32 * (kExactLimbs - 2) - 1;  // largest bit offset of a term's lowest bit
 constexpr int kEscapeLimbs = 72;   // limbs of the escape accumulator (every finite double)
 constexpr int kEscapeBias = 1100;  // its lowest limb is 2^-1100
 struct ExactParams {
-  const double* x;
+  const double* col[kMaxDim];   // coordinates, one column per axis
   const double* w;              // nullptr: unit weights
   long long n;
-  long long lo_key, hi_key;     // the in-range keys [T[1], T[nbins+1])
+  int32_t ndim;
   int32_t stat_overflows;
+  long long lo_key[kMaxDim], hi_key[kMaxDim];  // the in-range keys [T[1], T[nbins+1]) per axis
+  int32_t s0, ns;               // this pass sums statistics s0 .. s0 + ns - 1 (0 = sum w), ns <= kExactGroup
   int32_t grid[kExactStats];    // each statistic's grid exponent
   long long* limbs;             // [kExactStats][kExactLimbs]
   long long* escape;            // [kExactStats][kEscapeLimbs]
@@ -197,7 +201,7 @@ struct BatchHistDev {
   int32_t col;                  // column read by this histogram
   int32_t group;                // statistics group (same column and range)
   int32_t sbin_off;             // word offset of its per-block bins in shared memory, -1: global atomics
-  int32_t pad;
+  int32_t pad;                  // (the batch's precision is a kernel-template choice: see batch.cu)
   unsigned long long* g_lo;     // the histogram's accumulators (or tuning scratch)
   long long* g_hi;
   unsigned long long* g_unit;
@@ -282,7 +286,8 @@ int launch_slice_fill(const SliceParams& p, int block, int grid, size_t smem, vo
 int slice_max_blocks_per_sm(int block, size_t smem, int* per_sm);
 size_t slice_smem_bytes(int keys, int words, int frags);
 
-int launch_batch_fill(const BatchParams& p, int block, int grid, size_t smem, int minb, int kev, void* stream);
+int launch_batch_fill(const BatchParams& p, int block, int grid, size_t smem, int minb, int kev, bool f32c,
+                      void* stream);
 int batch_max_blocks_per_sm(int block, size_t smem, int minb, int kev, int* per_sm);
 int launch_batch_reduce(const BatchReduceParams& r, void* stream);
 

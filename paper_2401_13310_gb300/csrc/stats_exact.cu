@@ -1,10 +1,12 @@
-// stats_exact.cu -- order-independent, exactly summed 1D statistics.
+// stats_exact.cu -- order-independent, exactly summed statistics.
 //
-// With HIST_STATS_EXACT every statistic of a 1D histogram is the exact sum
-// of its rounded terms (w, fl(w*w), fl(w*x), fl(fl(w*x)*x), the terms of
-// Sec. 3.1's statistics as the oracle rounds them), rounded once to
-// binary64 on the host -- the same bits whatever the launch shape, the
-// order of the atomics or the way the events were split into fills.
+// With HIST_STATS_EXACT every statistic is the exact sum of its rounded
+// terms -- the terms of Sec. 3.1's statistics as the oracle rounds them:
+// w, fl(w*w), fl(w*x), fl(fl(w*x)*x) in 1D; ROOT's TH2/TH3 sets add
+// fl(w*y), fl(fl(w*y)*y), fl(fl(w*x)*y) in 2D and fl(w*z), fl(fl(w*z)*z),
+// fl(fl(w*x)*z), fl(fl(w*y)*z) in 3D -- rounded once to binary64 on the
+// host: the same bits whatever the launch shape, the order of the atomics
+// or the way the events were split into fills.
 //
 // Each term t = +-m 2^(E-1075) (m the 53-bit significand) is an integer
 // multiple of 2^g_s, g_s the statistic's grid, when E - 1075 >= g_s; it is
@@ -12,8 +14,10 @@
 // limbs absorb carries; each thread normalises them before the block and
 // grid sums, which are integer additions and hence exact and associative).
 // A term outside the grid's window (tiny, huge, subnormal) takes an escape
-// path into a 70-limb accumulator spanning every finite double; NaN and
-// infinite terms are counted instead.
+// path into a 72-limb accumulator spanning every finite double; NaN and
+// infinite terms are counted instead.  One pass sums up to four statistics
+// (their limbs fill the registers), so 2D and 3D fills take two and three
+// passes over the bulk.
 
 #include <cuda_runtime.h>
 
@@ -87,81 +91,86 @@ __device__ __forceinline__ void normalise(Limbs& L) {
   }
 }
 
-template <bool UNIT>
+// Term s (0-based statistic index) of one in-range event, rounded as defined.
+template <int NDIM>
+__device__ __forceinline__ double exact_term(int s, double w, const double* c) {
+  switch (s) {
+    case 0: return w;
+    case 1: return __dmul_rn(w, w);
+    case 2: return __dmul_rn(w, c[0]);
+    case 3: return __dmul_rn(__dmul_rn(w, c[0]), c[0]);
+    case 4: return NDIM >= 2 ? __dmul_rn(w, c[1 % NDIM]) : 0.0;
+    case 5: return NDIM >= 2 ? __dmul_rn(__dmul_rn(w, c[1 % NDIM]), c[1 % NDIM]) : 0.0;
+    case 6: return NDIM >= 2 ? __dmul_rn(__dmul_rn(w, c[0]), c[1 % NDIM]) : 0.0;
+    case 7: return NDIM >= 3 ? __dmul_rn(w, c[2 % NDIM]) : 0.0;
+    case 8: return NDIM >= 3 ? __dmul_rn(__dmul_rn(w, c[2 % NDIM]), c[2 % NDIM]) : 0.0;
+    case 9: return NDIM >= 3 ? __dmul_rn(__dmul_rn(w, c[0]), c[2 % NDIM]) : 0.0;
+    default: return NDIM >= 3 ? __dmul_rn(__dmul_rn(w, c[1 % NDIM]), c[2 % NDIM]) : 0.0;
+  }
+}
+
+template <bool UNIT, int NDIM>
 __global__ void __launch_bounds__(kThreads, 2) k_stats_exact(const __grid_constant__ ExactParams p) {
-  __shared__ long long sred[kThreads / 32][kExactStats][kExactLimbs];
-  Limbs acc[kExactStats];
+  __shared__ long long sred[kThreads / 32][kExactGroup][kExactLimbs];
+  Limbs acc[kExactGroup];
 #pragma unroll
-  for (int s = 0; s < kExactStats; ++s)
+  for (int j = 0; j < kExactGroup; ++j)
 #pragma unroll
-    for (int j = 0; j < kExactLimbs; ++j) acc[s].v[j] = 0;
-  unsigned long long special[kExactStats][3] = {};
-  const unsigned long long* xq = reinterpret_cast<const unsigned long long*>(p.x);
+    for (int l = 0; l < kExactLimbs; ++l) acc[j].v[l] = 0;
+  unsigned long long special[kExactGroup][3] = {};
   const unsigned long long* wq = reinterpret_cast<const unsigned long long*>(p.w);
-  auto one = [&](unsigned long long xb, unsigned long long wb) {
-    const long long key = key_of(xb);
-    if (!p.stat_overflows && !(key >= p.lo_key && key < p.hi_key)) return;
-    const double x = __longlong_as_double((long long)xb);
-    const double w = UNIT ? 1.0 : __longlong_as_double((long long)wb);
-    const double wx = UNIT ? x : __dmul_rn(w, x);
-    exact_add(acc[0], w, p.grid[0], p, 0, special[0]);
-    exact_add(acc[1], UNIT ? 1.0 : __dmul_rn(w, w), p.grid[1], p, 1, special[1]);
-    exact_add(acc[2], wx, p.grid[2], p, 2, special[2]);
-    exact_add(acc[3], __dmul_rn(wx, x), p.grid[3], p, 3, special[3]);
-  };
-  // pairs of events, the next pair's loads in flight while this one is added
-  const long long npairs = p.n >> 1;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  unsigned long long x0 = 0, x1 = 0, w0 = 0, w1 = 0;
-  auto load = [&](long long k, unsigned long long& a, unsigned long long& b, unsigned long long& c,
-                  unsigned long long& d) {
-    a = __ldcs(xq + 2 * k);
-    b = __ldcs(xq + 2 * k + 1);
-    if (!UNIT) {
-      c = __ldcs(wq + 2 * k);
-      d = __ldcs(wq + 2 * k + 1);
+  auto one = [&](long long i) {
+    double c[NDIM];
+    bool inr = true;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+      const unsigned long long xb = __ldcs(reinterpret_cast<const unsigned long long*>(p.col[d]) + i);
+      const long long key = key_of(xb);
+      inr = inr && key >= p.lo_key[d] && key < p.hi_key[d];
+      c[d] = __longlong_as_double((long long)xb);
+    }
+    if (!p.stat_overflows && !inr) return;
+    const double w = UNIT ? 1.0 : __longlong_as_double((long long)__ldcs(wq + i));
+#pragma unroll
+    for (int j = 0; j < kExactGroup; ++j) {
+      if (j >= p.ns) break;
+      const int st = p.s0 + j;
+      exact_add(acc[j], exact_term<NDIM>(st, w, c), p.grid[st], p, st, special[j]);
     }
   };
-  if (q < npairs) load(q, x0, x1, w0, w1);
-  for (; q < npairs; q += stride) {
-    unsigned long long nx0 = 0, nx1 = 0, nw0 = 0, nw1 = 0;
-    if (q + stride < npairs) load(q + stride, nx0, nx1, nw0, nw1);
-    one(x0, w0);
-    one(x1, w1);
-    x0 = nx0;
-    x1 = nx1;
-    w0 = nw0;
-    w1 = nw1;
+  // two events per thread and turn, the second's loads overlapping the first
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.n; i += 2 * stride) {
+    one(i);
+    if (i + stride < p.n) one(i + stride);
   }
-  if ((p.n & 1) && blockIdx.x == 0 && threadIdx.x == 0)
-    one(__ldcs(xq + p.n - 1), UNIT ? 0ull : __ldcs(wq + p.n - 1));
   // normalise, then sum over the warp, the block and the grid (exact integers)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int s = 0; s < kExactStats; ++s) {
-    normalise(acc[s]);
+  for (int j = 0; j < kExactGroup; ++j) {
+    normalise(acc[j]);
 #pragma unroll
-    for (int j = 0; j < kExactLimbs; ++j) {
-      long long v = acc[s].v[j];
+    for (int l = 0; l < kExactLimbs; ++l) {
+      long long v = acc[j].v[l];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) sred[warp][s][j] = v;
+      if (lane == 0) sred[warp][j][l] = v;
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      unsigned long long c = special[s][k];
+      unsigned long long cnt = special[j][k];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-      if (lane == 0 && c) atomicAdd(&p.special[s * 3 + k], c);
+      for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+      if (lane == 0 && cnt && j < p.ns) atomicAdd(&p.special[(p.s0 + j) * 3 + k], cnt);
     }
   }
   __syncthreads();
-  if (threadIdx.x < kExactStats * kExactLimbs) {
-    const int s = threadIdx.x / kExactLimbs, j = threadIdx.x % kExactLimbs;
+  if (threadIdx.x < kExactGroup * kExactLimbs) {
+    const int j = threadIdx.x / kExactLimbs, l = threadIdx.x % kExactLimbs;
     long long v = 0;
-    for (int wi = 0; wi < kThreads / 32; ++wi) v += sred[wi][s][j];
-    if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&p.limbs[s * kExactLimbs + j]), (unsigned long long)v);
+    for (int wi = 0; wi < kThreads / 32; ++wi) v += sred[wi][j][l];
+    if (v && j < p.ns)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&p.limbs[(p.s0 + j) * kExactLimbs + l]), (unsigned long long)v);
   }
 }
 
@@ -186,12 +195,20 @@ int launch_exact_normalise(long long* limbs, void* stream) {
 
 int launch_stats_exact(const ExactParams& p, bool unit, int sm_count, void* stream) {
   if (p.n <= 0) return 0;
+  if (p.ndim < 1 || p.ndim > kMaxDim || p.ns < 1 || p.ns > kExactGroup || p.s0 < 0 || p.s0 + p.ns > kExactStats)
+    return -1;
   long long grid = (p.n + kThreads - 1) / kThreads;
   if (grid > 2LL * sm_count * 4) grid = 2LL * sm_count * 4;
-  if (unit)
-    k_stats_exact<true><<<(int)grid, kThreads, 0, (cudaStream_t)stream>>>(p);
-  else
-    k_stats_exact<false><<<(int)grid, kThreads, 0, (cudaStream_t)stream>>>(p);
+  const cudaStream_t s = (cudaStream_t)stream;
+#define HGB_EXACT(U, D) \
+  if (unit == U && p.ndim == D) k_stats_exact<U, D><<<(int)grid, kThreads, 0, s>>>(p);
+  HGB_EXACT(true, 1)
+  HGB_EXACT(false, 1)
+  HGB_EXACT(true, 2)
+  HGB_EXACT(false, 2)
+  HGB_EXACT(true, 3)
+  HGB_EXACT(false, 3)
+#undef HGB_EXACT
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

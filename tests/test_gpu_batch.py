@@ -223,3 +223,57 @@ def test_batch_tuned_for_unit_then_weighted_fill(B):
             batch.close()
         for h in hists:
             h.close()
+
+
+@pytest.mark.parametrize("odd", [False, True])
+def test_batch_fp32c_matches_oracle(B, odd):
+    """A batch whose members are all booked HIST_PREC_FP32C runs the FP32
+    compensated form (per-block FP32 hi/lo bins with TwoSum on the atomic's
+    old value, binary64 atomics for the large members): bins and statistics
+    within 1e-12 of the oracle's sum of |terms|, after tuning (the wide
+    strategy only).  With odd weights (zero, negative, tiny, huge) the
+    events outside the double-word range take the binary64 path."""
+    bw = W.cfg4(n=200_003)
+    w = np.array(bw.weights, copy=True)
+    if odd:
+        rng = np.random.default_rng(44)
+        w[::53] = 0.0
+        w[1::47] = -rng.uniform(0.5, 1.5, w[1::47].shape[0])
+        w[2::61] = 1e-13
+        w[3::67] = 3e14
+    hists = [B.Hist([ax], B.HIST_PREC_FP32C) for ax in bw.axes]
+    batch = None
+    try:
+        with pytest.raises(B.HistError) as e:
+            B.Batch(hists, bw.col_of_hist, STRATEGIES["sliced"])
+        assert e.value.code == B.HIST_ERR_UNSUPPORTED
+        batch = B.Batch(hists, bw.col_of_hist, B.HIST_BATCH_GRAPH)
+        cols = [to_device(np.ascontiguousarray(bw.columns[c])) for c in range(3)]
+        rep = batch.tune(cols, to_device(w))
+        assert rep["strategy"] == 0
+        batch.fill(cols, to_device(w))
+        worst = 0.0
+        for i, (h, ax, c) in enumerate(zip(hists, bw.axes, bw.col_of_hist)):
+            bins, stats = h.result()
+            ref = oracle.fill([ax], bw.columns[c].reshape(1, -1), w)
+            worst = max(worst, assert_sums_close(bins, ref.bins_acc, ref.bins_abs, RTOL, f"fp32c hist {i} bins"))
+            assert stats[0] == ref.stats_acc[0]
+            assert_sums_close(stats[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, f"fp32c hist {i} stats")
+        print(f"FP32C batch: max |err| / sum|w| per bin = {worst:.3g}")
+    finally:
+        if batch is not None:
+            batch.close()
+        for h in hists:
+            h.close()
+
+
+def test_batch_rejects_mixed_precision(B):
+    h1 = B.Hist([W.fixed(10, 0.0, 1.0)], B.HIST_PREC_FP32C)
+    h2 = B.Hist([W.fixed(10, 0.0, 1.0)])
+    try:
+        with pytest.raises(B.HistError) as e:
+            B.Batch([h1, h2], [0, 0])
+        assert e.value.code == B.HIST_ERR_UNSUPPORTED
+    finally:
+        h1.close()
+        h2.close()

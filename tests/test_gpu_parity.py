@@ -332,3 +332,35 @@ def test_fp32c_within_tolerance(B, name, n):
     print(f"cfg{name} FP32C: max |err| / sum|w| per bin = {rel:.3g}")
     assert stats[0] == ref.stats_acc[0]
     assert_sums_close(stats[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, f"cfg{name} FP32C stats")
+
+
+@pytest.mark.parametrize("name", ["1", "2a", "2b"])
+@pytest.mark.parametrize("specials", [False, True])
+def test_count_and_plain_kernel_variants_agree(B, name, specials):
+    """1D fills with and without per-bin counts run different compiled
+    kernel variants (affine, bucket-map and specialised bucket locates):
+    the exact bins are bit-identical and both match the oracle.  With
+    specials, a sprinkling of events takes the rare per-event paths (NaN,
+    infinities, zeros, negative and tiny coordinates; zero and negative
+    weights, weights at the ends of the fixed-point window); n is odd (the
+    last event too).  (Weights outside the window take binary64 atomics,
+    whose sums depend on their order: other tests hold those to the
+    oracle's tolerance.)"""
+    wl = W.CONFIGS[name](n=1_000_001)
+    x = np.array(wl.values, copy=True)
+    w = None if wl.weights is None else np.array(wl.weights, copy=True)
+    if specials:
+        rng = np.random.default_rng(17)
+        idx = rng.choice(x.shape[1], 3000, replace=False)
+        x[0, idx[:1500]] = rng.choice([math.nan, math.inf, -math.inf, 0.0, -0.0, -3.0, 1e-300, 5e-324, 2e12, -0.5],
+                                      1500)
+        x[0, -1] = math.nan
+        if w is not None:
+            w[idx[1000:]] = rng.choice([0.0, -0.75, -2.0, 2.0 ** -8, 255.0, -(2.0 ** -8)], 2000)
+    plain = gpu_fill(wl.axes, x, w)
+    counted = gpu_fill(wl.axes, x, w, flags=B.HIST_TRACK_COUNTS)
+    assert np.array_equal(plain[0], counted[0]), "bins differ between the kernel variants"
+    assert plain[1][0] == counted[1][0] == x.shape[1]
+    ref = oracle.fill(wl.axes, x, w, threads=4)
+    check_against_oracle(wl.axes, x, w, *plain, ref, RTOL, RTOL, what=f"no counts cfg{name}")
+    check_against_oracle(wl.axes, x, w, *counted, ref, RTOL, RTOL, what=f"counts cfg{name}")
