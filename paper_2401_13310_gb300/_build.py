@@ -23,7 +23,7 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 
-CU_SOURCES = ["fill_kernels.cu", "noalloc.cu", "learned.cu", "batch.cu", "batch_slices.cu", "stats_exact.cu"]
+CU_SOURCES = ["fill_kernels.cu", "noalloc.cu", "learned.cu", "batch.cu", "batch_slices.cu", "batch_partition.cu", "stats_exact.cu"]
 CPP_SOURCES = ["hist_api.cpp", "axis_compile.cpp", "exact_round.cpp"]
 HEADERS = ["hist_internal.h", "fill_device.cuh", "axis_compile.h", "learned_eval.cuh", "device_common.cuh", "batch_stats.cuh"]
 

@@ -1219,6 +1219,25 @@ struct hist_batch {
   int* d_done = nullptr;
   long long done_cap = 0;
   size_t slices_cap = 0, frags_cap = 0, keys_cap = 0;
+  // partitioned plan (strategy 2; batch_partition.cu)
+  std::vector<long long> part_splits;
+  std::vector<PartRangeDev> part_range;
+  std::vector<PartSliceDev> part_slice;
+  int part_max_keys = 0, part_max_bins = 0, part_count_grid = 0, part_row = 8;
+  unsigned short* d_part_cum = nullptr;
+  long long* d_part_splits = nullptr;
+  PartRangeDev* d_part_ranges = nullptr;
+  PartSliceDev* d_part_slices = nullptr;
+  long long* d_part_keys = nullptr;
+  double* d_px = nullptr;            // the partitioned column and weights (capacity part_n_cap events)
+  double* d_pw = nullptr;
+  long long part_n_cap = 0, part_w_cap = 0;
+  unsigned* d_counts = nullptr;
+  unsigned long long* d_offsets = nullptr;
+  size_t counts_cap = 0;
+  PartItem* d_items = nullptr;
+  int* d_nitems = nullptr;
+  int items_cap = 0;
   // graph cache
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -1249,6 +1268,17 @@ void batch_release(hist_batch* b) {
   cudaFree(b->d_frags_tune);
   cudaFree(b->d_slice_keys);
   cudaFree(b->d_done);
+  cudaFree(b->d_part_splits);
+  cudaFree(b->d_part_ranges);
+  cudaFree(b->d_part_slices);
+  cudaFree(b->d_part_keys);
+  cudaFree(b->d_part_cum);
+  cudaFree(b->d_px);
+  cudaFree(b->d_pw);
+  cudaFree(b->d_counts);
+  cudaFree(b->d_offsets);
+  cudaFree(b->d_items);
+  cudaFree(b->d_nitems);
   for (void* q : b->scratch) cudaFree(q);
 }
 
@@ -1628,6 +1658,171 @@ int batch_configure(hist_batch* b, int budget) {
   return batch_upload(b);
 }
 
+// ---- partitioned strategy: planning (see batch_partition.cu) ----
+constexpr int kPartChunk = 1 << 19;   // events per fill work item at most
+
+// Bin of a key on a member's thresholds (the largest k with T[k] <= key).
+int host_bin(const std::vector<int64_t>& T, long long key) {
+  return (int)(std::upper_bound(T.begin(), T.end(), (int64_t)key) - T.begin()) - 1;
+}
+
+// Cut the column's key space into ranges that fit `budget` bytes of shared
+// memory: every member's thresholds sorted together; a range takes
+// thresholds until the next would pass its capacity C, the next range starts
+// at that threshold (a range's first threshold is a slice boundary, not one
+// of its interior thresholds).  A range costs, per interior threshold, one
+// bin of 8 bytes, one merged key of 8 bytes and one count row of 2 row_u16
+// bytes, plus per member 16 bytes of descriptor and one more bin.
+int part_configure(hist_batch* b, int budget) {
+  const int nh = (int)b->hs.size();
+  if (b->ncols != 1 || b->f32c || nh > kPartMaxMembers) return HIST_ERR_UNSUPPORTED;
+  int maxopt = 0;
+  if (cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess)
+    return HIST_ERR_CUDA;
+  const int limit = maxopt - 8 * 1024;  // the fill kernel's static arrays
+  if (budget > limit) budget = limit;
+  const int row = nh <= 8 ? 8 : 16;
+  const long long C = ((long long)budget - 24LL * nh - 2LL * row - 16) / (16 + 2 * row);
+  if (C < 16) return HIST_ERR_UNSUPPORTED;
+  std::vector<long long> all;
+  for (const hist* h : b->hs)
+    for (int k = 1; k <= h->nbins[0] + 1; ++k) all.push_back(h->T_host[0][k]);
+  std::sort(all.begin(), all.end());
+  std::vector<long long> splits;
+  long long acc = 0;
+  for (size_t i = 0; i < all.size();) {
+    size_t j = i;
+    while (j < all.size() && all[j] == all[i]) ++j;
+    const long long m = (long long)(j - i);
+    if (acc > 0 && acc + m > C) {
+      splits.push_back(all[i]);  // starts a range: its thresholds bound the slices there
+      acc = 0;
+    } else {
+      acc += m;
+    }
+    i = j;
+  }
+  const int nranges = (int)splits.size() + 1;
+  if (nranges > kPartMaxRanges) return HIST_ERR_UNSUPPORTED;
+  std::vector<PartRangeDev> ranges(nranges);
+  std::vector<PartSliceDev> slices((size_t)nranges * nh);
+  std::vector<long long> keys;
+  std::vector<uint16_t> cum;
+  int max_keys = 0, max_bins = 0;
+  std::vector<long long> merged;
+  for (int r = 0; r < nranges; ++r) {
+    const long long lo = r == 0 ? std::numeric_limits<long long>::min() : splits[(size_t)r - 1];
+    const long long hi_m1 = r + 1 < nranges ? splits[(size_t)r] - 1 : std::numeric_limits<long long>::max() - 1;
+    PartRangeDev& R = ranges[(size_t)r];
+    // the members' slices and their interior thresholds, merged and distinct
+    merged.clear();
+    int nb = 0;
+    std::vector<int> a(nh), e(nh);
+    for (int h = 0; h < nh; ++h) {
+      const std::vector<int64_t>& T = b->hs[(size_t)h]->T_host[0];
+      a[h] = host_bin(T, lo);
+      e[h] = host_bin(T, hi_m1);
+      PartSliceDev& S = slices[(size_t)r * nh + h];
+      S.a = a[h];
+      S.len = e[h] - a[h] + 1;
+      S.boff = nb;
+      S.pad = 0;
+      nb += S.len;
+      for (int k = a[h] + 1; k <= e[h]; ++k) merged.push_back(T[(size_t)k]);
+    }
+    std::sort(merged.begin(), merged.end());
+    merged.erase(std::unique(merged.begin(), merged.end()), merged.end());
+    const int M = (int)merged.size();
+    R.key_base = (int32_t)keys.size();
+    R.nkeys = M;
+    R.nbins = nb;
+    R.cum_base = (int32_t)cum.size();
+    keys.insert(keys.end(), merged.begin(), merged.end());
+    // row p: each member's count of its interior thresholds <= merged[p - 1]
+    const size_t row0 = cum.size();
+    cum.resize(row0 + (size_t)(M + 1) * row, 0);
+    for (int h = 0; h < nh; ++h) {
+      const std::vector<int64_t>& T = b->hs[(size_t)h]->T_host[0];
+      int k = a[h] + 1, c = 0;
+      for (int q = 1; q <= M; ++q) {
+        while (k <= e[h] && T[(size_t)k] <= merged[(size_t)q - 1]) {
+          ++k;
+          ++c;
+        }
+        cum[row0 + (size_t)q * row + h] = (uint16_t)c;
+      }
+    }
+    max_keys = std::max(max_keys, M);
+    max_bins = std::max(max_bins, nb);
+  }
+  if (keys.size() > (size_t)std::numeric_limits<int32_t>::max() ||
+      cum.size() > (size_t)std::numeric_limits<int32_t>::max())
+    return HIST_ERR_UNSUPPORTED;
+  const size_t fill_smem = part_fill_smem(max_keys, max_bins, nh, row);
+  if (fill_smem > (size_t)limit) return HIST_ERR_UNSUPPORTED;
+  int count_grid = 0, fill_per_sm = 0;
+  if (part_grids(b->sm_count, nranges, fill_smem, &count_grid, &fill_per_sm) != 0) return HIST_ERR_CUDA;
+  // upload the plan
+  cudaFree(b->d_part_splits);
+  cudaFree(b->d_part_ranges);
+  cudaFree(b->d_part_slices);
+  cudaFree(b->d_part_keys);
+  cudaFree(b->d_part_cum);
+  b->d_part_splits = nullptr;
+  b->d_part_ranges = nullptr;
+  b->d_part_slices = nullptr;
+  b->d_part_keys = nullptr;
+  b->d_part_cum = nullptr;
+  int rc;
+  if ((rc = dalloc(&b->d_part_splits, std::max<size_t>(splits.size(), 1) * 8)) != HIST_OK ||
+      (rc = dalloc(&b->d_part_ranges, sizeof(PartRangeDev) * ranges.size())) != HIST_OK ||
+      (rc = dalloc(&b->d_part_slices, sizeof(PartSliceDev) * slices.size())) != HIST_OK ||
+      (rc = dalloc(&b->d_part_keys, std::max<size_t>(keys.size(), 1) * 8)) != HIST_OK ||
+      (rc = dalloc(&b->d_part_cum, cum.size() * 2)) != HIST_OK)
+    return rc;
+  if ((!splits.empty() &&
+       cudaMemcpy(b->d_part_splits, splits.data(), splits.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(b->d_part_ranges, ranges.data(), sizeof(PartRangeDev) * ranges.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(b->d_part_slices, slices.data(), sizeof(PartSliceDev) * slices.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      (!keys.empty() && cudaMemcpy(b->d_part_keys, keys.data(), keys.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(b->d_part_cum, cum.data(), cum.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+    return HIST_ERR_CUDA;
+  b->part_splits.swap(splits);
+  b->part_range.swap(ranges);
+  b->part_slice.swap(slices);
+  b->part_max_keys = max_keys;
+  b->part_max_bins = max_bins;
+  b->part_row = row;
+  b->part_count_grid = count_grid;
+  // the counts of the count and scatter passes, one per (range, block)
+  const size_t nc = (size_t)nranges * count_grid;
+  if (nc > b->counts_cap) {
+    cudaFree(b->d_counts);
+    cudaFree(b->d_offsets);
+    b->d_counts = nullptr;
+    b->d_offsets = nullptr;
+    b->counts_cap = 0;
+    if ((rc = dalloc(&b->d_counts, nc * 4)) != HIST_OK || (rc = dalloc(&b->d_offsets, nc * 8)) != HIST_OK) return rc;
+    b->counts_cap = nc;
+  }
+  if (b->d_nitems == nullptr && (rc = dalloc(&b->d_nitems, 16)) != HIST_OK) return rc;
+  b->smem = fill_smem;
+  b->smem_budget = budget;
+  b->strategy = 2;
+  b->grid = 0;  // the fill's grid depends on the events: batch_reserve
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return HIST_OK;
+}
+
+int part_items(const hist_batch* b, int64_t n) {
+  return (int)b->part_range.size() + (int)((n + kPartChunk - 1) / kPartChunk) + 1;
+}
+
 int batch_check_args(const hist_batch* b, const double* const* cols, int ncols, const double* weights, int64_t n) {
   if (cols == nullptr || n < 0 || ncols < b->ncols) return HIST_ERR_ARG;
   for (int c = 0; c < b->ncols; ++c) {
@@ -1659,8 +1854,42 @@ BatchParams batch_params(const hist_batch* b, const double* const* cols, const d
   return p;
 }
 
-// Pacing counters of the sliced strategy for n events (before any capture).
-int batch_reserve(hist_batch* b, int64_t n) {
+// Scratch of a fill of n events (before any capture): the sliced strategy's
+// pacing counters; the partitioned strategy's copy of the column (and of the
+// weights, for weighted fills), work items and statistics partials.
+int batch_reserve(hist_batch* b, int64_t n, bool weighted) {
+  if (b->strategy == 2) {
+    int rc;
+    const long long cap = std::max<long long>(n, 1);
+    if (cap > b->part_n_cap) {
+      cudaFree(b->d_px);
+      b->d_px = nullptr;
+      b->part_n_cap = 0;
+      if ((rc = dalloc(&b->d_px, (size_t)cap * 8)) != HIST_OK) return rc;
+      b->part_n_cap = cap;
+    }
+    if (weighted && cap > b->part_w_cap) {
+      cudaFree(b->d_pw);
+      b->d_pw = nullptr;
+      b->part_w_cap = 0;
+      if ((rc = dalloc(&b->d_pw, (size_t)cap * 8)) != HIST_OK) return rc;
+      b->part_w_cap = cap;
+    }
+    const int items = part_items(b, n);
+    if (items > b->items_cap) {
+      cudaFree(b->d_items);
+      b->d_items = nullptr;
+      b->items_cap = 0;
+      if ((rc = dalloc(&b->d_items, sizeof(PartItem) * (size_t)items)) != HIST_OK) return rc;
+      b->items_cap = items;
+    }
+    if (items != b->grid && b->exec) {  // a captured fill launched another grid
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    b->grid = items;
+    return batch_part_stats(b);
+  }
   if (b->strategy != 1) return HIST_OK;
   const long long nt = (n + kSliceTile - 1) / kSliceTile;
   if (nt <= b->done_cap) return HIST_OK;
@@ -1675,7 +1904,39 @@ int batch_reserve(hist_batch* b, int64_t n) {
 
 int batch_launch(const hist_batch* b, const double* const* cols, const double* weights, int64_t n, bool tune,
                  cudaStream_t s) {
-  if (b->strategy == 1) {
+  if (b->strategy == 2) {
+    PartParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.col = cols[0];
+    p.w = weights;
+    p.px = b->d_px;
+    p.pw = weights != nullptr ? b->d_pw : nullptr;
+    p.splits = b->d_part_splits;
+    p.ranges = b->d_part_ranges;
+    p.slices = b->d_part_slices;
+    p.keys = b->d_part_keys;
+    p.cum = b->d_part_cum;
+    p.row_u16 = b->part_row;
+    p.hists = tune ? b->d_desc_tune : b->d_desc;
+    p.counts = b->d_counts;
+    p.offsets = b->d_offsets;
+    p.items = b->d_items;
+    p.nitems = b->d_nitems;
+    p.part_stats = b->d_part_stats;
+    p.n = n;
+    p.nranges = (int)b->part_range.size();
+    p.nh = (int)b->hs.size();
+    p.grid_count = b->part_count_grid;
+    p.fx_elo = kDefaultFxElo;
+    p.chunk = kPartChunk;
+    p.max_items = b->grid;
+    p.max_keys = b->part_max_keys;
+    p.max_bins = b->part_max_bins;
+    p.st = b->st;
+    if (p.max_items != part_items(b, n) || (weights != nullptr && b->part_w_cap < n) || b->part_n_cap < n)
+      return HIST_ERR_CUDA;  // batch_reserve sized the scratch for these events
+    if (launch_part_fill(p, weights == nullptr, b->grid, b->smem, s) != 0) return HIST_ERR_CUDA;
+  } else if (b->strategy == 1) {
     SliceParams p;
     std::memset(&p, 0, sizeof(p));
     for (int c = 0; c < b->ncols; ++c) p.col[c] = cols[c];
@@ -1900,7 +2161,7 @@ extern "C" int hist_batch_fill(hist_batch_t* b, const double* const* cols, int n
   }
   for (hist* h : b->hs)
     if ((rc = order_after_previous(h, s)) != HIST_OK) return rc;
-  if ((rc = batch_reserve(b, n)) != HIST_OK) return rc;
+  if ((rc = batch_reserve(b, n, weights != nullptr)) != HIST_OK) return rc;
   if (b->flags & HIST_BATCH_GRAPH) {
     std::vector<const double*> cv(cols, cols + b->ncols);
     if (b->exec == nullptr || cv != b->g_cols || weights != b->g_w || n != b->g_n) {
@@ -1957,10 +2218,14 @@ void batch_report(const hist_batch* b, hist_batch_tuning_t* r) {
   r->candidates = 1;
   r->smem_bytes = b->smem_budget;
   int per_sm = 0;
-  if (b->strategy == 0)
+  if (b->strategy == 0) {
     batch_max_blocks_per_sm(256, b->smem, b->wide_minb, b->wide_kev, &per_sm);
-  else
+  } else if (b->strategy == 1) {
     slice_max_blocks_per_sm(kSliceBlock, b->smem, &per_sm);
+  } else {
+    int cg = 0;
+    part_grids(b->sm_count, (int)b->part_range.size(), b->smem, &cg, &per_sm);
+  }
   r->blocks_per_sm = per_sm;
   int nsm = 0;
   if (b->strategy == 0)
@@ -1969,7 +2234,7 @@ void batch_report(const hist_batch* b, hist_batch_tuning_t* r) {
     nsm = (int)b->hs.size();
   r->smem_hists = nsm;
   r->strategy = b->strategy;
-  r->slices = b->strategy == 1 ? (int)b->slices.size() : 0;
+  r->slices = b->strategy == 1 ? (int)b->slices.size() : (b->strategy == 2 ? (int)b->part_range.size() : 0);
   r->replicas = b->strategy == 1 ? b->slice_replicas : 0;
   r->cost_cap_tenths = b->strategy == 1 ? (int)(10.0 * b->slice_cap + 0.5) : 0;
   r->events_per_thread = b->strategy == 0 ? b->wide_kev : 4;
@@ -2001,6 +2266,8 @@ extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int n
   if (!(b->flags & HIST_BATCH_WIDE))
     for (int kb : {96, 200})
       for (double cap : {3.0, 12.0}) cands.push_back({1, kb * 1024, cap, 2, 4});
+  if (!(b->flags & (HIST_BATCH_WIDE | HIST_BATCH_SLICED)) && b->ncols == 1 && !b->f32c)
+    for (int kb : {48, 100, 200}) cands.push_back({2, kb * 1024, 0.0, 2, 4});
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HIST_ERR_CUDA;
   double best = 1e300, worst = 0.0;
@@ -2010,7 +2277,8 @@ extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int n
   for (const Cand& c : cands) {
     b->wide_minb = c.minb;
     b->wide_kev = c.kev;
-    rc = c.strategy == 0 ? batch_configure(b, c.budget) : slice_configure(b, c.budget, c.cap);
+    rc = c.strategy == 0 ? batch_configure(b, c.budget)
+                         : (c.strategy == 1 ? slice_configure(b, c.budget, c.cap) : part_configure(b, c.budget));
     if (rc == HIST_ERR_UNSUPPORTED) {
       rc = HIST_OK;
       continue;
@@ -2021,7 +2289,7 @@ extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int n
       if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
       seen.push_back(sig);
     }
-    if ((rc = batch_reserve(b, n)) != HIST_OK) break;
+    if ((rc = batch_reserve(b, n, weights != nullptr)) != HIST_OK) break;
     if ((rc = batch_launch(b, cols, weights, n, true, nullptr)) != HIST_OK) break;  // warm-up
     cudaEventRecord(e0, nullptr);
     for (int r = 0; r < 3 && rc == HIST_OK; ++r) rc = batch_launch(b, cols, weights, n, true, nullptr);
@@ -2047,7 +2315,9 @@ extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int n
   if (rc != HIST_OK) return rc;
   b->wide_minb = best_c.minb;
   b->wide_kev = best_c.kev;
-  rc = best_c.strategy == 0 ? batch_configure(b, best_c.budget) : slice_configure(b, best_c.budget, best_c.cap);
+  rc = best_c.strategy == 0
+           ? batch_configure(b, best_c.budget)
+           : (best_c.strategy == 1 ? slice_configure(b, best_c.budget, best_c.cap) : part_configure(b, best_c.budget));
   if (rc != HIST_OK) return rc;
   if (report) {
     batch_report(b, report);
@@ -2061,7 +2331,7 @@ extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int n
 extern "C" int hist_batch_configure(hist_batch_t* b, int32_t strategy, int32_t smem_bytes, int32_t cost_cap_tenths,
                                     int32_t pace_tiles, int32_t blocks_per_sm, int32_t events_per_thread,
                                     hist_batch_tuning_t* info) {
-  if (b == nullptr || (strategy != 0 && strategy != 1) || smem_bytes < 1024 ||
+  if (b == nullptr || strategy < 0 || strategy > 2 || smem_bytes < 1024 ||
       (strategy == 1 && cost_cap_tenths < 10) || pace_tiles < -1 || (blocks_per_sm != 2 && blocks_per_sm != 4) ||
       (events_per_thread != 2 && events_per_thread != 4))
     return HIST_ERR_ARG;
@@ -2070,7 +2340,9 @@ extern "C" int hist_batch_configure(hist_batch_t* b, int32_t strategy, int32_t s
   b->wide_kev = events_per_thread;
   if (cudaSetDevice(b->device) != cudaSuccess) return HIST_ERR_CUDA;
   if (b->have_done && cudaEventSynchronize(b->done) != cudaSuccess) return HIST_ERR_CUDA;
-  const int rc = strategy == 0 ? batch_configure(b, smem_bytes) : slice_configure(b, smem_bytes, 0.1 * cost_cap_tenths);
+  const int rc = strategy == 0   ? batch_configure(b, smem_bytes)
+                 : strategy == 1 ? slice_configure(b, smem_bytes, 0.1 * cost_cap_tenths)
+                                 : part_configure(b, smem_bytes);
   if (rc != HIST_OK) return rc;
   if (info) batch_report(b, info);
   return HIST_OK;

@@ -282,6 +282,64 @@ struct SliceParams {
   BatchStatsSpec st;
 };
 
+// Partitioned strategy (batch_partition.cu): every member reads one column;
+// its key space is cut into ranges [S_r, S_r+1) whose slices (each member's
+// bins over the range) fit one block's shared memory together with the
+// range's merged thresholds: the distinct thresholds of all members strictly
+// inside the range, sorted, and for each position p among them (p of them
+// <= a key) every member's count of its own thresholds among the first p --
+// so one binary search gives every member's bin.  The events are partitioned
+// by range, then each work item (a range and a run of its events) fills the
+// slices in shared memory.
+constexpr int kPartBlock = 256;
+constexpr int kPartMaxMembers = 16;   // members of a partitioned batch (16-bit counts, 32-byte rows)
+constexpr int kPartMaxRanges = 2048;
+struct PartRangeDev {
+  int32_t key_base;             // its merged thresholds in the concatenated key array
+  int32_t nkeys;                // how many (M); positions p = 0 .. M
+  int32_t nbins;                // bin slots of all its slices
+  int32_t cum_base;             // its count rows (M + 1 of row_u16 each) in the concatenated count array
+};
+struct PartSliceDev {           // one member over one range
+  int32_t a;                    // first bin
+  int32_t len;                  // bins a .. a + len - 1
+  int32_t boff;                 // its first bin slot in the range's shared bins
+  int32_t pad;
+};
+struct PartItem {
+  long long e0, e1;             // events [e0, e1) of the partitioned column
+  int32_t r;                    // their range
+  int32_t pad;
+};
+struct PartParams {
+  const double* col;            // the column
+  const double* w;              // weights or nullptr
+  double* px;                   // [n] the column partitioned by range
+  double* pw;                   // [n] the weights alike (weighted fills)
+  const long long* splits;      // [nranges - 1] split keys S_1 .. S_{nranges-1}
+  const PartRangeDev* ranges;   // [nranges]
+  const PartSliceDev* slices;   // [nranges][nh]
+  const long long* keys;        // every range's merged thresholds, back to back
+  const unsigned short* cum;    // every range's count rows, back to back
+  const BatchHistDev* hists;    // [nh] the members' accumulators (or tuning scratch)
+  unsigned* counts;             // [nranges][grid_count] events per (range, block)
+  unsigned long long* offsets;  // [nranges][grid_count] their exclusive prefix sums
+  PartItem* items;              // [max_items] the fill's work items
+  int* nitems;                  // how many
+  double* part_stats;           // [fill grid][kStatSlots][3]
+  long long n;
+  int32_t nranges, nh, grid_count, fx_elo;
+  int32_t chunk;                // events per work item at most
+  int32_t max_items;
+  int32_t max_keys, max_bins;   // the largest range's thresholds and bin slots
+  int32_t row_u16;              // u16 per count row: 8 (nh <= 8) or 16
+  BatchStatsSpec st;
+};
+size_t part_count_smem(int nranges);
+size_t part_fill_smem(int max_keys, int max_bins, int nh, int row_u16);
+int part_grids(int sm_count, int nranges, size_t fill_smem, int* count_grid, int* fill_per_sm);
+int launch_part_fill(const PartParams& p, bool unit, int fill_grid, size_t fill_smem, void* stream);
+
 int launch_slice_fill(const SliceParams& p, int block, int grid, size_t smem, void* stream);
 int slice_max_blocks_per_sm(int block, size_t smem, int* per_sm);
 size_t slice_smem_bytes(int keys, int words, int frags);

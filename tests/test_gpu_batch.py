@@ -277,3 +277,108 @@ def test_batch_rejects_mixed_precision(B):
     finally:
         h1.close()
         h2.close()
+
+
+def _one_column_batch(n, seed):
+    """Twelve axes of every kind (fixed, log-spaced, jittered, mixture
+    quantiles; ranges inside, around and beside the data) on one column of
+    values N(0.3, 3), with weights U[0.5, 1.5)."""
+    rng = np.random.default_rng(seed)
+    axes = []
+    for i in range(12):
+        kind = i % 4
+        nb = int(round(10 * 10 ** (3.3 * i / 11)))
+        if kind == 0:
+            axes.append(W.fixed(nb, -8.0 + 0.1 * i, 9.0 - 0.2 * i))
+        elif kind == 1:
+            axes.append(W.variable(W.log_edges(nb, -2.0, 1.2)))
+        elif kind == 2:
+            axes.append(W.variable(W.jittered_edges(nb, -5.0, 5.0, rng)))
+        else:
+            axes.append(W.variable(W.mixture_quantile_edges(nb)))
+    x = rng.normal(0.3, 3.0, n)
+    w = rng.uniform(0.5, 1.5, n)
+    return W.BatchWorkload("one_column", axes, [0] * len(axes), x.reshape(1, n), w, {})
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+@pytest.mark.parametrize("budget", [6 << 10, 100 << 10])
+def test_batch_partitioned_matches_oracle(B, weighted, budget):
+    """The partitioned strategy (events partitioned by coordinate range,
+    every member's bins of a range in one block's shared memory): bins and
+    statistics against the oracle, with a small shared-memory budget (many
+    ranges: every member cut at many range boundaries) and a large one."""
+    bw = _one_column_batch(300_007, 71)
+    w = bw.weights if weighted else None
+    hists = [B.Hist([ax]) for ax in bw.axes]
+    batch = None
+    try:
+        batch = B.Batch(hists, bw.col_of_hist)
+        info = batch.configure(2, budget)
+        assert info["strategy"] == 2 and info["slices"] >= (8 if budget < (10 << 10) else 1)
+        batch.fill([to_device(np.ascontiguousarray(bw.columns[0]))], to_device(w))
+        _check(bw, hists, w, f"partitioned budget={budget} w={weighted}")
+    finally:
+        if batch is not None:
+            batch.close()
+        for h in hists:
+            h.close()
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_batch_partitioned_edges_specials_and_accumulate(B, weighted):
+    """Every threshold of every member and its neighbouring doubles (so
+    every range boundary and slice boundary), signed zeros, infinities,
+    NaN, subnormals; odd weights; two fills accumulate like one of the
+    concatenation (graph replay)."""
+    rng = np.random.default_rng(72)
+    bw = _one_column_batch(10, 73)
+    pts = np.concatenate([edge_probe_values(ax, B.hist_axis_thresholds(ax), rng, nrand=300) for ax in bw.axes])
+    pts = pts[rng.permutation(pts.size)]
+    n = pts.size
+    w = rng.uniform(-2.0, 2.0, n) if weighted else None
+    if weighted:
+        w[::97] = 0.0
+        w[1::89] = 1e-5
+        w[2::83] = -3e3
+    hists = [B.Hist([ax]) for ax in bw.axes]
+    batch = None
+    try:
+        batch = B.Batch(hists, bw.col_of_hist, B.HIST_BATCH_GRAPH)
+        batch.configure(2, 8 << 10)
+        col = to_device(pts)
+        wd = to_device(w)
+        batch.fill([col], wd)
+        batch.fill([col], wd)
+        two = np.concatenate([pts, pts]).reshape(1, -1)
+        w2 = None if w is None else np.concatenate([w, w])
+        for i, (h, ax) in enumerate(zip(hists, bw.axes)):
+            bins, stats = h.result()
+            ref = oracle.fill([ax], two, w2)
+            if w2 is None:
+                assert np.array_equal(bins, ref.counts.astype(np.float64)), f"hist {i}"
+            else:
+                assert_sums_close(bins, ref.bins_acc, ref.bins_abs, RTOL, f"partitioned edges hist {i} bins")
+            assert stats[0] == ref.stats_acc[0]
+            assert_sums_close(stats[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, f"partitioned hist {i} stats")
+    finally:
+        if batch is not None:
+            batch.close()
+        for h in hists:
+            h.close()
+
+
+def test_batch_partitioned_needs_one_column(B):
+    bw = W.cfg4(n=1000)
+    hists = [B.Hist([ax]) for ax in bw.axes[:6]]
+    batch = None
+    try:
+        batch = B.Batch(hists, bw.col_of_hist[:6])
+        with pytest.raises(B.HistError) as e:
+            batch.configure(2, 64 << 10)
+        assert e.value.code == B.HIST_ERR_UNSUPPORTED
+    finally:
+        if batch is not None:
+            batch.close()
+        for h in hists:
+            h.close()

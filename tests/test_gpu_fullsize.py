@@ -150,10 +150,17 @@ def test_cfg5_full_size_locators(B, cfg5_ref, locator):
         for h in hists:
             h.reset()
         batch = B.Batch(hists, bw.col_of_hist, B.HIST_BATCH_GRAPH)
-        batch.tune([col[:8_000_000]], None)
+        rep = batch.tune([col[:8_000_000]], None)
         batch.fill([col], None)
         torch.cuda.synchronize()
-        _check_unit([h.result() for h in hists], refs, f"batch {locator}")
+        _check_unit([h.result() for h in hists], refs, f"batch {locator} (tuned strategy {rep['strategy']})")
+        # the partitioned strategy pinned (events partitioned by range)
+        for h in hists:
+            h.reset()
+        batch.configure(2, 100 << 10)
+        batch.fill([col], None)
+        torch.cuda.synchronize()
+        _check_unit([h.result() for h in hists], refs, f"partitioned batch {locator}")
     finally:
         if batch is not None:
             batch.close()
