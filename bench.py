@@ -357,7 +357,7 @@ def measure_forms(B, W, hbm: float, args) -> dict:
         for h in hists:
             h.fill(col, None)
     res["plain_default_ms"] = _timed(plain5, 2)
-    sample = [col[:8_000_000]]
+    sample = [col[:100_000_000]]  # large enough that the tuner sees each strategy's per-event cost
     batch = B.Batch(hists, lw.col_of_hist, B.HIST_BATCH_GRAPH)
     res["fused_default_tuning"] = batch.tune(sample, None)
     res["fused_default_ms"] = _timed(lambda: batch.fill([col], None), 2)

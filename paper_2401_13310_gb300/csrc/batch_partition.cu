@@ -17,9 +17,9 @@
 //    row of at most 16 members per position);
 //  * count: each block counts its grid-strided events per range (a binary
 //    search over the split keys in shared memory, two events at a time);
-//  * scan: one block turns the counts into per-(range, block) offsets and a
-//    list of work items (a range and a run of at most `chunk` of its events),
-//    a warp per range with coalesced reads;
+//  * scan: the counts become per-(range, block) offsets and a list of work
+//    items (a range and a run of at most `chunk` of its events): a warp per
+//    range with coalesced reads, and one block scanning the range totals;
 //  * scatter: each block writes its events (and weights) to their range's
 //    segment of a partitioned copy of the column, at the offsets found (the
 //    same grid-strided assignment as the count);
@@ -85,63 +85,88 @@ __global__ void __launch_bounds__(kPartBlock) k_part_count(const __grid_constant
   for (int r = threadIdx.x; r < p.nranges; r += blockDim.x) p.counts[(size_t)r * gridDim.x + blockIdx.x] = cnt[r];
 }
 
-// One block: per-range totals (a warp per range, coalesced), their exclusive
-// scan and the work items' bases (one thread: at most 4096 ranges), then the
-// per-(range, block) offsets (a warp scan per range) and the work items.
-__global__ void __launch_bounds__(1024) k_part_scan(const __grid_constant__ PartParams p) {
-  __shared__ unsigned long long rstart[kPartMaxRanges];
-  __shared__ int ibase[kPartMaxRanges + 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+// The scan, in three small launches: per-range totals (a warp per range,
+// coalesced reads of its blocks' counts); their exclusive scan and the work
+// items' bases (one block: at most kPartMaxRanges ranges); the per-(range,
+// block) offsets (a warp scan per range) and the work items.
+__global__ void __launch_bounds__(256) k_part_totals(const __grid_constant__ PartParams p) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= p.nranges) return;
   const int G = p.grid_count;
-  for (int r = warp; r < p.nranges; r += nwarps) {
-    unsigned long long s = 0;
-    for (int b = lane; b < G; b += 32) s += p.counts[(size_t)r * G + b];
+  unsigned long long s = 0;
+  for (int b = lane; b < G; b += 32) s += p.counts[(size_t)r * G + b];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) rstart[r] = s;  // the range's total, for now
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) p.rtotal[r] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_part_rscan(const __grid_constant__ PartParams p) {
+  __shared__ unsigned long long sv[1024];
+  __shared__ int si[1024];
+  // each thread scans a run of ranges; the runs' sums are scanned in turn
+  const int per = (p.nranges + blockDim.x - 1) / blockDim.x;
+  const int r0 = threadIdx.x * per, r1 = min(p.nranges, r0 + per);
+  unsigned long long s = 0;
+  int it = 0;
+  for (int r = r0; r < r1; ++r) {
+    const unsigned long long len = p.rtotal[r];
+    s += len;
+    it += (int)((len + (unsigned long long)p.chunk - 1) / (unsigned long long)p.chunk);
   }
+  sv[threadIdx.x] = s;
+  si[threadIdx.x] = it;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long run = 0;
-    int items = 0;
-    for (int r = 0; r < p.nranges; ++r) {
-      const unsigned long long len = rstart[r];
-      rstart[r] = run;
-      ibase[r] = items;
-      run += len;
-      items += (int)((len + (unsigned long long)p.chunk - 1) / (unsigned long long)p.chunk);
-    }
-    ibase[p.nranges] = items < p.max_items ? items : p.max_items;
-    *p.nitems = ibase[p.nranges];
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {  // inclusive Hillis-Steele scans
+    const unsigned long long a = threadIdx.x >= (unsigned)o ? sv[threadIdx.x - o] : 0ull;
+    const int b = threadIdx.x >= (unsigned)o ? si[threadIdx.x - o] : 0;
+    __syncthreads();
+    sv[threadIdx.x] += a;
+    si[threadIdx.x] += b;
+    __syncthreads();
   }
-  __syncthreads();
-  for (int r = warp; r < p.nranges; r += nwarps) {
-    unsigned long long run = rstart[r];
-    for (int b0 = 0; b0 < G; b0 += 32) {
-      const int b = b0 + lane;
-      const unsigned long long v = b < G ? p.counts[(size_t)r * G + b] : 0ull;
-      unsigned long long inc = v;
+  unsigned long long run = sv[threadIdx.x] - s;
+  int ib = si[threadIdx.x] - it;
+  for (int r = r0; r < r1; ++r) {
+    const unsigned long long len = p.rtotal[r];
+    p.rstart[r] = run;
+    p.ibase[r] = ib;
+    run += len;
+    ib += (int)((len + (unsigned long long)p.chunk - 1) / (unsigned long long)p.chunk);
+  }
+  if (threadIdx.x == blockDim.x - 1) *p.nitems = min(si[threadIdx.x], p.max_items);
+}
+
+__global__ void __launch_bounds__(256) k_part_offsets(const __grid_constant__ PartParams p) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= p.nranges) return;
+  const int G = p.grid_count;
+  unsigned long long run = p.rstart[r];
+  for (int b0 = 0; b0 < G; b0 += 32) {
+    const int b = b0 + lane;
+    const unsigned long long v = b < G ? p.counts[(size_t)r * G + b] : 0ull;
+    unsigned long long inc = v;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
-      }
-      if (b < G) p.offsets[(size_t)r * G + b] = run + inc - v;
-      run += __shfl_sync(0xffffffffu, inc, 31);
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
     }
-    const long long e0 = (long long)rstart[r];
-    const long long e1 = r + 1 < p.nranges ? (long long)rstart[r + 1] : p.n;
-    const int nch = (int)((e1 - e0 + p.chunk - 1) / p.chunk);
-    for (int k = lane; k < nch; k += 32) {
-      const int it = ibase[r] + k;
-      if (it >= p.max_items) break;
-      PartItem item;
-      item.e0 = e0 + (long long)k * p.chunk;
-      item.e1 = min(e1, item.e0 + (long long)p.chunk);
-      item.r = r;
-      item.pad = 0;
-      p.items[it] = item;
-    }
+    if (b < G) p.offsets[(size_t)r * G + b] = run + inc - v;
+    run += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  const long long e0 = (long long)p.rstart[r];
+  const long long e1 = e0 + (long long)p.rtotal[r];
+  const int nch = (int)((e1 - e0 + p.chunk - 1) / p.chunk);
+  for (int k = lane; k < nch; k += 32) {
+    const int it = p.ibase[r] + k;
+    if (it >= p.max_items) break;
+    PartItem item;
+    item.e0 = e0 + (long long)k * p.chunk;
+    item.e1 = min(e1, item.e0 + (long long)p.chunk);
+    item.r = r;
+    item.pad = 0;
+    p.items[it] = item;
   }
 }
 
@@ -346,7 +371,9 @@ int part_grids(int sm_count, int nranges, size_t fill_smem, int* count_grid, int
     least = a < least ? a : least;
   }
   if (per_sm < 1 || least < 1) return -3;
-  *count_grid = per_sm * sm_count;
+  // (at most 4 blocks per SM: fewer (range, block) segments, each longer,
+  // so the scatter's writes fill whole cache lines)
+  *count_grid = (per_sm < 4 ? per_sm : 4) * sm_count;
   *fill_per_sm = least;
   return 0;
 }
@@ -362,8 +389,11 @@ int launch_part_fill(const PartParams& p, bool unit, int fill_grid, size_t fill_
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs) != cudaSuccess ||
       cudaFuncSetAttribute(fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem) != cudaSuccess)
     return -2;
+  const int wblocks = (p.nranges + 7) / 8;  // a warp per range, 8 per block
   k_part_count<<<p.grid_count, kPartBlock, cs, s>>>(p);
-  k_part_scan<<<1, 1024, 0, s>>>(p);
+  k_part_totals<<<wblocks, 256, 0, s>>>(p);
+  k_part_rscan<<<1, 1024, 0, s>>>(p);
+  k_part_offsets<<<wblocks, 256, 0, s>>>(p);
   k_part_scatter<<<p.grid_count, kPartBlock, cs, s>>>(p);
   void* args[] = {const_cast<PartParams*>(&p)};
   if (cudaLaunchKernel(fill, dim3(fill_grid), dim3(kPartBlock), args, fill_smem, s) != cudaSuccess) return -2;

@@ -1234,6 +1234,7 @@ struct hist_batch {
   long long part_n_cap = 0, part_w_cap = 0;
   unsigned* d_counts = nullptr;
   unsigned long long* d_offsets = nullptr;
+  unsigned long long* d_rscan = nullptr;  // [2][kPartMaxRanges] range totals and starts, then item bases
   size_t counts_cap = 0;
   PartItem* d_items = nullptr;
   int* d_nitems = nullptr;
@@ -1277,6 +1278,7 @@ void batch_release(hist_batch* b) {
   cudaFree(b->d_pw);
   cudaFree(b->d_counts);
   cudaFree(b->d_offsets);
+  cudaFree(b->d_rscan);
   cudaFree(b->d_items);
   cudaFree(b->d_nitems);
   for (void* q : b->scratch) cudaFree(q);
@@ -1808,6 +1810,7 @@ int part_configure(hist_batch* b, int budget) {
     b->counts_cap = nc;
   }
   if (b->d_nitems == nullptr && (rc = dalloc(&b->d_nitems, 16)) != HIST_OK) return rc;
+  if (b->d_rscan == nullptr && (rc = dalloc(&b->d_rscan, (size_t)kPartMaxRanges * 20)) != HIST_OK) return rc;
   b->smem = fill_smem;
   b->smem_budget = budget;
   b->strategy = 2;
@@ -1920,6 +1923,9 @@ int batch_launch(const hist_batch* b, const double* const* cols, const double* w
     p.hists = tune ? b->d_desc_tune : b->d_desc;
     p.counts = b->d_counts;
     p.offsets = b->d_offsets;
+    p.rtotal = b->d_rscan;
+    p.rstart = b->d_rscan + kPartMaxRanges;
+    p.ibase = reinterpret_cast<int*>(b->d_rscan + 2 * kPartMaxRanges);
     p.items = b->d_items;
     p.nitems = b->d_nitems;
     p.part_stats = b->d_part_stats;

@@ -324,6 +324,9 @@ struct PartParams {
   const BatchHistDev* hists;    // [nh] the members' accumulators (or tuning scratch)
   unsigned* counts;             // [nranges][grid_count] events per (range, block)
   unsigned long long* offsets;  // [nranges][grid_count] their exclusive prefix sums
+  unsigned long long* rtotal;   // [nranges] events per range
+  unsigned long long* rstart;   // [nranges] first event of each range in the partitioned column
+  int* ibase;                   // [nranges] first work item of each range
   PartItem* items;              // [max_items] the fill's work items
   int* nitems;                  // how many
   double* part_stats;           // [fill grid][kStatSlots][3]
