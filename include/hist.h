@@ -241,8 +241,8 @@ int hist_kernel_time(hist_t *h, double *ms, int64_t *launches);
  * The paper's conclusion names computing several histograms from the same
  * data, and its kernels being small and launch-bound, as the next step.  A
  * batch fills up to 128 booked 1D histograms from up to 4 columns and one
- * weight column in one fused launch, with one of two privatisation
- * strategies:
+ * weight column in one fused pass over the events, with one of three
+ * privatisation strategies:
  *   wide   -- every block fills every histogram from its share of the
  *             events; small histograms keep exact per-block bins in shared
  *             memory, large ones use exact global integer atomics;
@@ -251,7 +251,18 @@ int hist_kernel_time(hist_t *h, double *ms, int64_t *launches);
  *             fills one slice from a share of the events, every bin stays
  *             in shared memory, and the slices sweep the event stream
  *             together so that each event is read from HBM once (from L2
- *             by the other slices).
+ *             by the other slices);
+ *   partitioned -- per column (at most 32 histograms each): the column's
+ *             key space is cut into ranges such that every histogram's bins
+ *             over one range, the range's merged thresholds of all its
+ *             histograms and a row of per-histogram threshold counts per
+ *             merged threshold fit one block's shared memory; the events
+ *             (and weights) are counted per range, copied into a
+ *             partitioned scratch column, and each range's events are filled
+ *             by blocks holding that range: one search over the merged
+ *             thresholds gives every histogram's bin.  Six kernels per
+ *             column, columns one after the other; scratch of 8 bytes per
+ *             event (16 weighted), kept by the batch.
  * Histograms that share a column and range share their statistics sums.
  * Results and accuracy per histogram are those of hist_fill_bulk.
  * Precision: a batch whose members are all booked with HIST_PREC_FP32C
@@ -291,8 +302,8 @@ typedef struct {
   int32_t smem_hists;      /* histograms kept in shared memory */
   double best_ms;          /* time of the chosen configuration on the sample */
   double worst_ms;         /* slowest candidate */
-  int32_t strategy;        /* chosen strategy: 0 wide, 1 sliced */
-  int32_t slices;          /* sliced: slices of the chosen plan (0 for wide) */
+  int32_t strategy;        /* chosen strategy: 0 wide, 1 sliced, 2 partitioned */
+  int32_t slices;          /* sliced: slices of the chosen plan; partitioned: ranges over all columns; 0 wide */
   int32_t replicas;        /* sliced: blocks per slice */
   int32_t cost_cap_tenths; /* sliced: work cap per slice of the chosen plan, tenths of one histogram */
   int32_t events_per_thread; /* events each thread holds per pass over the histograms */
@@ -308,8 +319,9 @@ typedef struct {
 int hist_batch_tune(hist_batch_t *b, const double *const *cols, int ncols, const double *weights, int64_t n,
                     hist_batch_tuning_t *report);
 
-/* Pin the batch's configuration instead of tuning it: strategy 0 (wide) or
- * 1 (sliced), the shared-memory budget per block in bytes; for the sliced
+/* Pin the batch's configuration instead of tuning it: strategy 0 (wide),
+ * 1 (sliced) or 2 (partitioned), the shared-memory budget per block in
+ * bytes (partitioned: per range); for the sliced
  * strategy the work cap per slice in tenths of one histogram's
  * locate-and-add and the pacing window in tiles of 2048 events (-1 the
  * default, 0 no pacing); for the wide strategy the blocks per SM the kernel
@@ -317,7 +329,9 @@ int hist_batch_tune(hist_batch_t *b, const double *const *cols, int ncols, const
  * holds (2 or 4).  info (may be NULL) receives the resulting plan (with
  * best_ms = worst_ms = 0).  Waits for the batch's earlier fills.  Errors:
  * HIST_ERR_ARG, HIST_ERR_UNSUPPORTED (the plan does not fit one block's
- * shared memory), HIST_ERR_OOM, HIST_ERR_CUDA. */
+ * shared memory; partitioned: more than 32 histograms on a column, more
+ * than 2048 ranges on a column, or an FP32C batch; sliced: an FP32C
+ * batch), HIST_ERR_OOM, HIST_ERR_CUDA. */
 int hist_batch_configure(hist_batch_t *b, int32_t strategy, int32_t smem_bytes, int32_t cost_cap_tenths,
                          int32_t pace_tiles, int32_t blocks_per_sm, int32_t events_per_thread,
                          hist_batch_tuning_t *info);

@@ -1,7 +1,9 @@
-// batch_partition.cu -- the partitioned strategy of the batched fill, for
-// batches whose histograms all read one column (many binnings of the same
-// quantity, such as the eight mixture-quantile axes of the learned-locator
-// workload).
+// batch_partition.cu -- the partitioned strategy of the batched fill: many
+// binnings of the same quantity (the eight mixture-quantile axes of the
+// learned-locator workload, or the ~21 histograms of each of pT, phi and eta
+// in the 64-histogram workload).  Each column's members are filled by one
+// run of the kernels below; a batch over several columns runs them once per
+// column, one after the other.
 //
 // A member with 1e4 .. 1e6 bins cannot keep block-private bins, so the wide
 // strategy adds its events with global atomics and looks its bin up in
@@ -14,7 +16,7 @@
 //    thresholds -- the distinct thresholds of all members strictly inside
 //    the range, sorted -- and, for every position p among them, each
 //    member's count of its own thresholds among the first p (16-bit, one
-//    row of at most 16 members per position);
+//    row of at most 32 members per position, padded to a multiple of 8);
 //  * count: each block counts its grid-strided events per range (a binary
 //    search over the split keys in shared memory, two events at a time);
 //  * scan: the counts become per-(range, block) offsets and a list of work
@@ -26,7 +28,7 @@
 //  * fill: each work item's block stages its range -- merged thresholds,
 //    count rows, zeroed bins -- in shared memory, reads its run of events
 //    coalesced, two per thread at a time; one binary search over the merged
-//    thresholds gives the position p of an event, one 16- or 32-byte load
+//    thresholds gives the position p of an event, one to four 16-byte loads
 //    its row, and member h's bin is a_h + row[h]: one add to the shared bins
 //    per member (u32 counters, or the exact fixed-point words with carries
 //    of the other strategies).  At the end the block adds its bins into the
@@ -39,6 +41,7 @@
 
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstdint>
 
 #include "batch_stats.cuh"
@@ -48,38 +51,93 @@
 namespace hgb {
 namespace {
 
-// Number of the n sorted keys K[0..n) that are <= key (two keys at once:
-// their search steps interleave).
-__device__ __forceinline__ void count_le2(const long long* K, int n, long long k0, long long k1, int& j0, int& j1) {
-  int a = 0, b = 0, len = n + 1;  // answers in [0, n]
-  while (len > 1) {
-    const int half = len >> 1;
-    const long long t0 = K[a + half - 1], t1 = K[b + half - 1];
-    a = (t0 <= k0) ? a + half : a;
-    b = (t1 <= k1) ? b + half : b;
-    len -= half;
+// Merged position (how many of the range's M merged thresholds are <= the
+// key) of two keys at once: the bounds first, then the range's bucket map
+// and a search of the bucket's thresholds, the two keys' steps interleaved.
+struct PartLocator {
+  const long long* keys;       // the range's merged thresholds (shared)
+  const unsigned short* bcnt;  // its bucket counts (shared)
+  long long lo, hi, kbase;
+  float scale, offset;
+  int m, nbk, key_map, shift, top;
+
+  __device__ __forceinline__ int bucket(long long key, unsigned long long xb) const {
+    int b;
+    if (key_map) {
+      const long long q = (key >> shift) - kbase;
+      b = (int)(q < 0 ? 0 : (q > nbk - 1 ? nbk - 1 : q));
+    } else {
+      const float t = fminf(fmaxf(__fmaf_rn(est_float(xb), scale, offset), -1.0f), (float)nbk);
+      b = min(max(__float2int_rd(t), 0), nbk - 1);
+    }
+    return b;
   }
-  j0 = a;
-  j1 = b;
+
+  __device__ __forceinline__ void locate2(long long k0, unsigned long long x0, long long k1, unsigned long long x1,
+                                          int& j0, int& j1) const {
+    const bool in0 = k0 >= lo && k0 < hi, in1 = k1 >= lo && k1 < hi;
+    const int b0 = in0 ? bucket(k0, x0) : 0, b1 = in1 ? bucket(k1, x1) : 0;
+    const int c0 = in0 ? (int)bcnt[b0] : 0, c1 = in1 ? (int)bcnt[b1] : 0;
+    const int n0 = in0 ? (int)bcnt[b0 + 1] - c0 : 0, n1 = in1 ? (int)bcnt[b1 + 1] - c1 : 0;
+    int p0 = 0, p1 = 0;
+    for (int step = top; step > 0; step >>= 1) {
+      const int q0 = p0 + step, q1 = p1 + step;
+      const long long t0 = q0 <= n0 ? keys[c0 + q0 - 1] : LLONG_MAX;
+      const long long t1 = q1 <= n1 ? keys[c1 + q1 - 1] : LLONG_MAX;
+      p0 = t0 <= k0 ? q0 : p0;
+      p1 = t1 <= k1 ? q1 : p1;
+    }
+    j0 = k0 < lo ? 0 : (k0 >= hi ? m : c0 + p0);
+    j1 = k1 < lo ? 0 : (k1 >= hi ? m : c1 + p1);
+  }
+};
+
+// The split keys' locator over their shared copy: the range of a key is its
+// position among the nranges - 1 splits.
+__device__ __forceinline__ PartLocator split_locator(const PartParams& p, const long long* splits,
+                                                     const unsigned short* sbc) {
+  const PartRangeDev& m = p.split_map;
+  return PartLocator{splits, sbc, m.lo_key, m.hi_key, m.kbase, m.scale, m.offset, m.nkeys, m.nbk, m.key_map,
+                     m.shift, m.top};
 }
 
+// Stage the split keys and their bucket counts: [splits][bucket counts].
+__device__ __forceinline__ void stage_splits(const PartParams& p, unsigned char* smem, long long*& splits,
+                                             unsigned short*& sbc, size_t& used) {
+  splits = reinterpret_cast<long long*>(smem);
+  const size_t sb = (((size_t)(p.nranges - 1) * 8) + 15) & ~(size_t)15;
+  sbc = reinterpret_cast<unsigned short*>(smem + sb);
+  used = sb + ((((size_t)p.split_map.nbk + 1) * 2 + 15) & ~(size_t)15);
+  for (int i = threadIdx.x; i < p.nranges - 1; i += blockDim.x) splits[i] = p.splits[i];
+  for (int i = threadIdx.x; i <= p.split_map.nbk && p.split_map.nbk > 0; i += blockDim.x) sbc[i] = p.sbcnt[i];
+}
+
+// Count: block b takes tiles b, b + G, b + 2G, ... of kPartTile consecutive
+// events (thread t events t, t + 256, ... of a tile) and counts them per
+// range; the scatter takes the same events in the same blocks.
 __global__ void __launch_bounds__(kPartBlock) k_part_count(const __grid_constant__ PartParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  long long* splits = reinterpret_cast<long long*>(smem_raw);
-  unsigned* cnt = reinterpret_cast<unsigned*>(smem_raw + (size_t)p.nranges * 8);
-  for (int i = threadIdx.x; i < p.nranges - 1; i += blockDim.x) splits[i] = p.splits[i];
+  long long* splits;
+  unsigned short* sbc;
+  size_t used;
+  stage_splits(p, smem_raw, splits, sbc, used);
+  unsigned* cnt = reinterpret_cast<unsigned*>(smem_raw + used);
   for (int i = threadIdx.x; i < p.nranges; i += blockDim.x) cnt[i] = 0u;
   __syncthreads();
+  const PartLocator L = split_locator(p, splits, sbc);
   const unsigned long long* xq = reinterpret_cast<const unsigned long long*>(p.col);
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.n; i += 2 * stride) {
-    const bool two = i + stride < p.n;
-    const long long k0 = key_of(__ldcs(xq + i));
-    const long long k1 = two ? key_of(__ldcs(xq + i + stride)) : k0;
-    int r0, r1;
-    count_le2(splits, p.nranges - 1, k0, k1, r0, r1);
-    atomicAdd(&cnt[r0], 1u);
-    if (two) atomicAdd(&cnt[r1], 1u);
+  constexpr int kPer = kPartTile / kPartBlock;
+  for (long long base = (long long)blockIdx.x * kPartTile; base < p.n; base += (long long)gridDim.x * kPartTile) {
+#pragma unroll
+    for (int k = 0; k < kPer; k += 2) {
+      const long long i0 = base + threadIdx.x + (long long)k * kPartBlock, i1 = i0 + kPartBlock;
+      const bool v0 = i0 < p.n, v1 = i1 < p.n;
+      const unsigned long long x0 = v0 ? __ldcs(xq + i0) : 0ull, x1 = v1 ? __ldcs(xq + i1) : 0ull;
+      int r0, r1;
+      L.locate2(key_of(x0), x0, key_of(x1), x1, r0, r1);
+      if (v0) atomicAdd(&cnt[r0], 1u);
+      if (v1) atomicAdd(&cnt[r1], 1u);
+    }
   }
   __syncthreads();
   for (int r = threadIdx.x; r < p.nranges; r += blockDim.x) p.counts[(size_t)r * gridDim.x + blockIdx.x] = cnt[r];
@@ -170,37 +228,112 @@ __global__ void __launch_bounds__(256) k_part_offsets(const __grid_constant__ Pa
   }
 }
 
+// Exclusive scan of v[0 .. n) into out (n <= kPartMaxRanges; every thread
+// of the block calls it): each thread scans a run of consecutive entries,
+// the runs' sums are scanned by warp shuffles and the warps' totals.
+__device__ __forceinline__ void block_exclusive_scan(const unsigned* v, unsigned* out, int n, unsigned* wsum) {
+  const int per = (n + kPartBlock - 1) / kPartBlock;
+  const int i0 = threadIdx.x * per, i1 = min(n, i0 + per);
+  unsigned own = 0;
+  for (int i = i0; i < i1; ++i) own += v[i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned inc = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  unsigned run = inc - own;
+  for (int w = 0; w < warp; ++w) run += wsum[w];
+  for (int i = i0; i < i1; ++i) {
+    out[i] = run;
+    run += v[i];
+  }
+}
+
+// Scatter, a tile at a time (the count's tiles): the tile's events are
+// ranked within their ranges by shared atomics, placed in range order in
+// shared memory, and written out so that consecutive threads write the
+// consecutive events of one range -- each range's run of the tile is one
+// contiguous piece of its segment.
+template <bool WEIGHTED>
 __global__ void __launch_bounds__(kPartBlock) k_part_scatter(const __grid_constant__ PartParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  long long* splits = reinterpret_cast<long long*>(smem_raw);
-  unsigned long long* base = reinterpret_cast<unsigned long long*>(smem_raw + (size_t)p.nranges * 8);
-  unsigned* cursor = reinterpret_cast<unsigned*>(smem_raw + (size_t)p.nranges * 16);
-  for (int i = threadIdx.x; i < p.nranges - 1; i += blockDim.x) splits[i] = p.splits[i];
-  for (int r = threadIdx.x; r < p.nranges; r += blockDim.x) {
-    base[r] = p.offsets[(size_t)r * gridDim.x + blockIdx.x];
-    cursor[r] = 0u;
+  long long* splits;
+  unsigned short* sbc;
+  size_t used;
+  stage_splits(p, smem_raw, splits, sbc, used);
+  const int nr = p.nranges;
+  // [.. splits][next (u64)][tcnt (u32)][tstart (u32)][buf_x][buf_w][buf_r (u16)]
+  unsigned long long* next = reinterpret_cast<unsigned long long*>(smem_raw + used);
+  unsigned* tcnt = reinterpret_cast<unsigned*>(smem_raw + used + (size_t)nr * 8);
+  unsigned* tstart = tcnt + nr;
+  const size_t bx = (used + (size_t)nr * 16 + 15) & ~(size_t)15;
+  unsigned long long* buf_x = reinterpret_cast<unsigned long long*>(smem_raw + bx);
+  unsigned long long* buf_w = buf_x + kPartTile;
+  unsigned short* buf_r = reinterpret_cast<unsigned short*>(buf_x + (WEIGHTED ? 2 : 1) * kPartTile);
+  __shared__ unsigned wsum[kPartBlock / 32];
+  for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+    next[r] = p.offsets[(size_t)r * gridDim.x + blockIdx.x];
+    tcnt[r] = 0u;
   }
   __syncthreads();
+  const PartLocator L = split_locator(p, splits, sbc);
   const unsigned long long* xq = reinterpret_cast<const unsigned long long*>(p.col);
   const unsigned long long* wq = reinterpret_cast<const unsigned long long*>(p.w);
   unsigned long long* px = reinterpret_cast<unsigned long long*>(p.px);
   unsigned long long* pw = reinterpret_cast<unsigned long long*>(p.pw);
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  // the same events per block as the count pass, in the same pairs
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.n; i += 2 * stride) {
-    const bool two = i + stride < p.n;
-    const unsigned long long x0 = __ldcs(xq + i);
-    const unsigned long long x1 = two ? __ldcs(xq + i + stride) : x0;
-    int r0, r1;
-    count_le2(splits, p.nranges - 1, key_of(x0), key_of(x1), r0, r1);
-    const unsigned long long q0 = base[r0] + atomicAdd(&cursor[r0], 1u);
-    px[q0] = x0;
-    if (wq != nullptr) pw[q0] = __ldcs(wq + i);
-    if (two) {
-      const unsigned long long q1 = base[r1] + atomicAdd(&cursor[r1], 1u);
-      px[q1] = x1;
-      if (wq != nullptr) pw[q1] = __ldcs(wq + i + stride);
+  constexpr int kPer = kPartTile / kPartBlock;
+  for (long long base = (long long)blockIdx.x * kPartTile; base < p.n; base += (long long)gridDim.x * kPartTile) {
+    unsigned long long x[kPer], w[kPer];
+    int r[kPer];
+    unsigned rank[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; k += 2) {
+      const long long i0 = base + threadIdx.x + (long long)k * kPartBlock, i1 = i0 + kPartBlock;
+      const bool v0 = i0 < p.n, v1 = i1 < p.n;
+      x[k] = v0 ? __ldcs(xq + i0) : 0ull;
+      x[k + 1] = v1 ? __ldcs(xq + i1) : 0ull;
+      if (WEIGHTED) {
+        w[k] = v0 ? __ldcs(wq + i0) : 0ull;
+        w[k + 1] = v1 ? __ldcs(wq + i1) : 0ull;
+      }
+      L.locate2(key_of(x[k]), x[k], key_of(x[k + 1]), x[k + 1], r[k], r[k + 1]);
+      rank[k] = v0 ? atomicAdd(&tcnt[r[k]], 1u) : 0u;
+      rank[k + 1] = v1 ? atomicAdd(&tcnt[r[k + 1]], 1u) : 0u;
     }
+    __syncthreads();
+    block_exclusive_scan(tcnt, tstart, nr, wsum);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      if (base + threadIdx.x + (long long)k * kPartBlock < p.n) {
+        const unsigned q = tstart[r[k]] + rank[k];
+        buf_x[q] = x[k];
+        if (WEIGHTED) buf_w[q] = w[k];
+        buf_r[q] = (unsigned short)r[k];
+      }
+    }
+    __syncthreads();
+    const int tile_n = (int)min((long long)kPartTile, p.n - base);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int q = threadIdx.x + k * kPartBlock;
+      if (q < tile_n) {
+        const int rr = buf_r[q];
+        const unsigned long long pos = next[rr] + (unsigned)(q - (int)tstart[rr]);
+        px[pos] = buf_x[q];
+        if (WEIGHTED) pw[pos] = buf_w[q];
+      }
+    }
+    __syncthreads();
+    for (int rr = threadIdx.x; rr < nr; rr += blockDim.x) {
+      next[rr] += tcnt[rr];
+      tcnt[rr] = 0u;
+    }
+    __syncthreads();
   }
 }
 
@@ -219,13 +352,19 @@ __device__ __forceinline__ void part_fx_add(unsigned* a, long long* ghi, long lo
   if (top != 0) atomicAdd(reinterpret_cast<unsigned long long*>(ghi), (unsigned long long)((long long)top << 32));
 }
 
+// A member whose slice of a range has few bins would see most lanes of a
+// warp add to the same bin (the range's events all fall in those few bins),
+// and same-address shared atomics serialise.  Such a slice keeps 2^rsh
+// copies of every bin (up to 32 slots in all), lane l adding to copy
+// l mod 2^rsh; the count rows hold c << rsh for bin c, and each thread's
+// first slot is offset by its copy, so the add stays one add per member.
 template <bool UNIT, int ROW>
 struct PartFill {
   const PartParams& p;
   const unsigned short* cum;
   const PartSliceDev* sl;
   unsigned* bins;
-  int boff[ROW];  // each member's first bin slot (registers)
+  int boff[ROW];  // each member's first bin slot for this thread's copy (registers)
 
   // An event (weight wb) at merged position pos into every member's bin.
   __device__ __forceinline__ void add(int pos, unsigned long long wb) const {
@@ -243,9 +382,9 @@ struct PartFill {
       if (UNIT) {
         atomicAdd(&bins[boff[h] + j], 1u);
       } else if (!wok) {
-        atomicAdd(&p.hists[h].g_f64[sl[h].a + j], __longlong_as_double((long long)wb));
+        atomicAdd(&p.hists[h].g_f64[sl[h].a + (j >> sl[h].rsh)], __longlong_as_double((long long)wb));
       } else if (V != 0) {
-        part_fx_add(&bins[2 * (boff[h] + j)], &p.hists[h].g_hi[sl[h].a + j], V);
+        part_fx_add(&bins[2 * (boff[h] + j)], &p.hists[h].g_hi[sl[h].a + (j >> sl[h].rsh)], V);
       }
     }
   }
@@ -254,20 +393,21 @@ struct PartFill {
 template <bool UNIT, int ROW>
 __global__ void __launch_bounds__(kPartBlock) k_part_fill(const __grid_constant__ PartParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // [count rows (16-byte aligned)][merged keys][slices][bins]
+  // [count rows][bucket counts][merged keys][slices][bins], each part
+  // 16-byte aligned
   unsigned short* cum = reinterpret_cast<unsigned short*>(smem_raw);
   const size_t cum_bytes = ((size_t)(p.max_keys + 1) * ROW * 2 + 15) & ~(size_t)15;
-  long long* keys = reinterpret_cast<long long*>(smem_raw + cum_bytes);
-  PartSliceDev* sl = reinterpret_cast<PartSliceDev*>(smem_raw + cum_bytes + (size_t)p.max_keys * 8);
-  unsigned* bins = reinterpret_cast<unsigned*>(smem_raw + cum_bytes + (size_t)p.max_keys * 8 +
+  unsigned short* bcnt = reinterpret_cast<unsigned short*>(smem_raw + cum_bytes);
+  const size_t bcnt_bytes = ((size_t)(p.max_nbk + 1) * 2 + 15) & ~(size_t)15;
+  long long* keys = reinterpret_cast<long long*>(smem_raw + cum_bytes + bcnt_bytes);
+  PartSliceDev* sl = reinterpret_cast<PartSliceDev*>(smem_raw + cum_bytes + bcnt_bytes + (size_t)p.max_keys * 8);
+  unsigned* bins = reinterpret_cast<unsigned*>(smem_raw + cum_bytes + bcnt_bytes + (size_t)p.max_keys * 8 +
                                                sizeof(PartSliceDev) * p.nh);
   __shared__ double sred[(kPartBlock / 32) * kStatSlots * 3];
   __shared__ PartItem item;
   __shared__ PartRangeDev range;
 
-  double core[kBatchMaxCols][3];
-#pragma unroll
-  for (int c = 0; c < kBatchMaxCols; ++c) core[c][0] = core[c][1] = core[c][2] = 0.0;
+  double core1[3] = {0.0, 0.0, 0.0};  // the column's core sums
   double tail[kBatchMaxGroups * 3];
   for (int t = 0; t < kBatchMaxGroups * 3; ++t) tail[t] = 0.0;
 
@@ -285,85 +425,150 @@ __global__ void __launch_bounds__(kPartBlock) k_part_fill(const __grid_constant_
       const int n16 = (range.nkeys + 1) * ROW / 8;
       for (int j = threadIdx.x; j < n16; j += blockDim.x) dst[j] = src[j];
     }
+    for (int j = threadIdx.x; j <= range.nbk && range.nbk > 0; j += blockDim.x) bcnt[j] = p.bcnt[range.bk_base + j];
     for (int h = threadIdx.x; h < p.nh; h += blockDim.x) sl[h] = p.slices[(size_t)item.r * p.nh + h];
     const int nwords = (UNIT ? 1 : 2) * range.nbins;
     for (int j = threadIdx.x; j < nwords; j += blockDim.x) bins[j] = 0u;
     __syncthreads();
 
+    const PartLocator loc{keys,         bcnt,         range.lo_key, range.hi_key, range.kbase,
+                          range.scale,  range.offset, range.nkeys,  range.nbk,    range.key_map,
+                          range.shift,  range.top};
     PartFill<UNIT, ROW> f{p, cum, sl, bins, {}};
 #pragma unroll
-    for (int h = 0; h < ROW; ++h) f.boff[h] = h < p.nh ? sl[h].boff : 0;
+    for (int h = 0; h < ROW; ++h)
+      f.boff[h] = h < p.nh ? sl[h].boff + (int)(threadIdx.x & ((1u << sl[h].rsh) - 1u)) : 0;
     const unsigned long long* xq = reinterpret_cast<const unsigned long long*>(p.px);
     const unsigned long long* wq = reinterpret_cast<const unsigned long long*>(p.pw);
     const long long e1 = item.e1;
-    for (long long e = item.e0 + threadIdx.x; e < e1; e += 2 * (long long)blockDim.x) {
-      const long long e2 = e + blockDim.x;
-      const bool two = e2 < e1;
-      const unsigned long long x0 = __ldcs(xq + e);
-      const unsigned long long x1 = two ? __ldcs(xq + e2) : x0;
-      const unsigned long long w0 = UNIT ? 0x3FF0000000000000ull : __ldcs(wq + e);
-      const unsigned long long w1 = UNIT ? 0x3FF0000000000000ull : (two ? __ldcs(wq + e2) : w0);
+    const long long step = 2 * (long long)blockDim.x;
+    constexpr unsigned long long kOne = 0x3FF0000000000000ull;
+    // two events per thread at a time (e and e + blockDim.x); the next two
+    // are loaded before the current ones are processed
+    long long e = item.e0 + threadIdx.x;
+    unsigned long long x0 = 0, x1 = 0, w0 = kOne, w1 = kOne;
+    if (e < e1) {
+      const bool two = e + blockDim.x < e1;
+      x0 = __ldcs(xq + e);
+      x1 = two ? __ldcs(xq + e + blockDim.x) : x0;
+      if (!UNIT) {
+        w0 = __ldcs(wq + e);
+        w1 = two ? __ldcs(wq + e + blockDim.x) : w0;
+      }
+    }
+    for (; e < e1; e += step) {
+      const bool two = e + blockDim.x < e1;
+      const long long en = e + step;
+      unsigned long long nx0 = 0, nx1 = 0, nw0 = kOne, nw1 = kOne;
+      if (en < e1) {
+        const bool ntwo = en + blockDim.x < e1;
+        nx0 = __ldcs(xq + en);
+        nx1 = ntwo ? __ldcs(xq + en + blockDim.x) : nx0;
+        if (!UNIT) {
+          nw0 = __ldcs(wq + en);
+          nw1 = ntwo ? __ldcs(wq + en + blockDim.x) : nw0;
+        }
+      }
       const long long k0 = key_of(x0), k1 = key_of(x1);
       int j0, j1;
-      count_le2(keys, range.nkeys, k0, k1, j0, j1);
+      loc.locate2(k0, x0, k1, x1, j0, j1);
       f.add(j0, w0);
-      stat_event<UNIT>(p.st, 0, k0, x0, w0, core[0], tail);
+      stat_event<UNIT>(p.st, p.stat_col, k0, x0, w0, core1, tail);
       if (two) {
         f.add(j1, w1);
-        stat_event<UNIT>(p.st, 0, k1, x1, w1, core[0], tail);
+        stat_event<UNIT>(p.st, p.stat_col, k1, x1, w1, core1, tail);
       }
+      x0 = nx0;
+      x1 = nx1;
+      w0 = nw0;
+      w1 = nw1;
     }
     __syncthreads();
     // the range's bins into the members' exact global accumulators
+    // (a bin's copies summed first: 64-bit sums of at most 32 words)
     for (int h = 0; h < p.nh; ++h) {
       const PartSliceDev s = sl[h];
+      const int nc = 1 << s.rsh;
       const BatchHistDev& d = p.hists[h];
       for (int j = threadIdx.x; j < s.len; j += blockDim.x) {
+        const int b0 = s.boff + (j << s.rsh);
         if (UNIT) {
-          const unsigned c = bins[s.boff + j];
-          if (c) atomicAdd(&d.g_unit[s.a + j], (unsigned long long)c);
+          unsigned long long c = 0;
+          for (int r = 0; r < nc; ++r) c += bins[b0 + r];
+          if (c) atomicAdd(&d.g_unit[s.a + j], c);
         } else {
-          const unsigned a0 = bins[2 * (s.boff + j)], a1 = bins[2 * (s.boff + j) + 1];
-          if (a0) atomicAdd(&d.g_lo[s.a + j], (unsigned long long)a0);
-          if (a1) atomicAdd(reinterpret_cast<unsigned long long*>(&d.g_hi[s.a + j]), (unsigned long long)a1);
+          unsigned long long a0 = 0, a1 = 0;
+          for (int r = 0; r < nc; ++r) {
+            a0 += bins[2 * (b0 + r)];
+            a1 += bins[2 * (b0 + r) + 1];
+          }
+          if (a0) atomicAdd(&d.g_lo[s.a + j], a0);
+          if (a1) atomicAdd(reinterpret_cast<unsigned long long*>(&d.g_hi[s.a + j]), a1);
         }
       }
     }
   }
-  // every block writes its statistics partial (zeros for idle blocks)
+  // every block writes its statistics partial (zeros for idle blocks and
+  // for the other columns' slots)
+  double core[kBatchMaxCols][3];
+#pragma unroll
+  for (int c = 0; c < kBatchMaxCols; ++c)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) core[c][q] = c == p.stat_col ? core1[q] : 0.0;
   __syncthreads();
   block_stats_store(core, tail, sred, p.part_stats + (size_t)blockIdx.x * kStatSlots * 3);
 }
 
-const void* part_fill_fn(bool unit, int row) {
-  if (unit) return row == 8 ? reinterpret_cast<const void*>(&k_part_fill<true, 8>)
-                            : reinterpret_cast<const void*>(&k_part_fill<true, 16>);
-  return row == 8 ? reinterpret_cast<const void*>(&k_part_fill<false, 8>)
-                  : reinterpret_cast<const void*>(&k_part_fill<false, 16>);
+template <bool UNIT>
+const void* part_fill_row(int row) {
+  switch (row) {
+    case 8: return reinterpret_cast<const void*>(&k_part_fill<UNIT, 8>);
+    case 16: return reinterpret_cast<const void*>(&k_part_fill<UNIT, 16>);
+    case 24: return reinterpret_cast<const void*>(&k_part_fill<UNIT, 24>);
+    default: return reinterpret_cast<const void*>(&k_part_fill<UNIT, 32>);
+  }
 }
+
+// row: u16 per count row, 8, 16, 24 or 32
+const void* part_fill_fn(bool unit, int row) { return unit ? part_fill_row<true>(row) : part_fill_row<false>(row); }
 
 }  // namespace
 
-size_t part_count_smem(int nranges) { return (size_t)nranges * 16 + (size_t)nranges * 4; }
-
-size_t part_fill_smem(int max_keys, int max_bins, int nh, int row_u16) {
-  return (((size_t)(max_keys + 1) * row_u16 * 2 + 15) & ~(size_t)15) + (size_t)max_keys * 8 +
-         sizeof(PartSliceDev) * (size_t)nh + (size_t)max_bins * 8;
+size_t part_count_smem(int nranges, int split_nbk) {
+  return ((((size_t)(nranges - 1) * 8) + 15) & ~(size_t)15) + ((((size_t)split_nbk + 1) * 2 + 15) & ~(size_t)15) +
+         (size_t)nranges * 4;
 }
 
-int part_grids(int sm_count, int nranges, size_t fill_smem, int* count_grid, int* fill_per_sm) {
-  const size_t cs = part_count_smem(nranges);
+size_t part_scatter_smem(int nranges, int split_nbk, bool weighted) {
+  const size_t used =
+      ((((size_t)(nranges - 1) * 8) + 15) & ~(size_t)15) + ((((size_t)split_nbk + 1) * 2 + 15) & ~(size_t)15);
+  const size_t bx = (used + (size_t)nranges * 16 + 15) & ~(size_t)15;
+  return bx + (size_t)kPartTile * ((weighted ? 16 : 8) + 2);
+}
+
+size_t part_fill_smem(int max_keys, int max_bins, int nh, int row_u16, int max_nbk) {
+  return (((size_t)(max_keys + 1) * row_u16 * 2 + 15) & ~(size_t)15) + (((size_t)(max_nbk + 1) * 2 + 15) & ~(size_t)15) +
+         (size_t)max_keys * 8 + sizeof(PartSliceDev) * (size_t)nh + (size_t)max_bins * 8;
+}
+
+int part_grids(int sm_count, int nranges, int split_nbk, size_t fill_smem, int* count_grid, int* fill_per_sm) {
+  const size_t cs = part_count_smem(nranges, split_nbk);
+  const size_t ss = part_scatter_smem(nranges, split_nbk, true);
+  const size_t su = part_scatter_smem(nranges, split_nbk, false);
   if (cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_part_count), cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)cs) != cudaSuccess ||
-      cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_part_scatter),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs) != cudaSuccess)
+      cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_part_scatter<true>),
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss) != cudaSuccess ||
+      cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_part_scatter<false>),
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)su) != cudaSuccess)
     return -2;
   int per_sm = 0, least = 1 << 30;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(&k_part_scatter),
-                                                    kPartBlock, cs) != cudaSuccess)
+  // (the count and the scatter share a grid: the weighted scatter's occupancy)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(&k_part_scatter<true>),
+                                                    kPartBlock, ss) != cudaSuccess)
     return -2;
-  for (int v = 0; v < 4; ++v) {
-    const void* fn = part_fill_fn(v & 1, (v & 2) ? 16 : 8);
+  for (int v = 0; v < 8; ++v) {
+    const void* fn = part_fill_fn(v & 1, 8 * (1 + (v >> 1)));
     int a = 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fn, kPartBlock, fill_smem) != cudaSuccess)
@@ -371,22 +576,23 @@ int part_grids(int sm_count, int nranges, size_t fill_smem, int* count_grid, int
     least = a < least ? a : least;
   }
   if (per_sm < 1 || least < 1) return -3;
-  // (at most 4 blocks per SM: fewer (range, block) segments, each longer,
-  // so the scatter's writes fill whole cache lines)
-  *count_grid = (per_sm < 4 ? per_sm : 4) * sm_count;
+  // one resident wave of the scatter (each block its tiles in turn)
+  *count_grid = per_sm * sm_count;
   *fill_per_sm = least;
   return 0;
 }
 
 int launch_part_fill(const PartParams& p, bool unit, int fill_grid, size_t fill_smem, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t cs = part_count_smem(p.nranges);
+  const size_t cs = part_count_smem(p.nranges, p.split_map.nbk);
+  const size_t ss = part_scatter_smem(p.nranges, p.split_map.nbk, !unit);
+  const void* scatter = unit ? reinterpret_cast<const void*>(&k_part_scatter<false>)
+                             : reinterpret_cast<const void*>(&k_part_scatter<true>);
   // (the attributes are per kernel: another batch may have set others)
   const void* fill = part_fill_fn(unit, p.row_u16);
   if (cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_part_count), cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)cs) != cudaSuccess ||
-      cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_part_scatter),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs) != cudaSuccess ||
+      cudaFuncSetAttribute(scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss) != cudaSuccess ||
       cudaFuncSetAttribute(fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem) != cudaSuccess)
     return -2;
   const int wblocks = (p.nranges + 7) / 8;  // a warp per range, 8 per block
@@ -394,8 +600,8 @@ int launch_part_fill(const PartParams& p, bool unit, int fill_grid, size_t fill_
   k_part_totals<<<wblocks, 256, 0, s>>>(p);
   k_part_rscan<<<1, 1024, 0, s>>>(p);
   k_part_offsets<<<wblocks, 256, 0, s>>>(p);
-  k_part_scatter<<<p.grid_count, kPartBlock, cs, s>>>(p);
   void* args[] = {const_cast<PartParams*>(&p)};
+  if (cudaLaunchKernel(scatter, dim3(p.grid_count), dim3(kPartBlock), args, ss, s) != cudaSuccess) return -2;
   if (cudaLaunchKernel(fill, dim3(fill_grid), dim3(kPartBlock), args, fill_smem, s) != cudaSuccess) return -2;
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }

@@ -1161,6 +1161,39 @@ extern "C" int hist_train_locator(hist_t* h, int axis, const hist_locator_opts_t
 
 // ============================================================== batches ====
 
+// The partitioned strategy's plan for one column: its members (contiguous
+// in batch order), its ranges and their staged tables on the device.
+struct PartPlan {
+  int col = 0, h0 = 0, nh = 0;  // the column and its members [h0, h0 + nh)
+  int nranges = 0, max_keys = 0, max_bins = 0, max_nbk = 0, row = 8, count_grid = 0, fill_per_sm = 0;
+  size_t smem = 0;              // the fill kernel's dynamic shared memory
+  long long* d_splits = nullptr;
+  PartRangeDev* d_ranges = nullptr;
+  PartSliceDev* d_slices = nullptr;
+  long long* d_keys = nullptr;
+  unsigned short* d_cum = nullptr;
+  unsigned short* d_bcnt = nullptr;
+  unsigned short* d_sbcnt = nullptr;  // the split keys' bucket counts
+  PartRangeDev split_map{};           // ... and their bucket map
+  int items = 0, block_base = 0;  // the fill's grid and first statistics partial (set per event count)
+  void release() {
+    cudaFree(d_splits);
+    cudaFree(d_ranges);
+    cudaFree(d_slices);
+    cudaFree(d_keys);
+    cudaFree(d_cum);
+    cudaFree(d_bcnt);
+    cudaFree(d_sbcnt);
+    d_bcnt = nullptr;
+    d_sbcnt = nullptr;
+    d_splits = nullptr;
+    d_ranges = nullptr;
+    d_slices = nullptr;
+    d_keys = nullptr;
+    d_cum = nullptr;
+  }
+};
+
 struct hist_batch {
   std::vector<hist*> hs;     // member histograms, sorted by column
   std::vector<int> col;      // column of each (sorted order)
@@ -1219,16 +1252,8 @@ struct hist_batch {
   int* d_done = nullptr;
   long long done_cap = 0;
   size_t slices_cap = 0, frags_cap = 0, keys_cap = 0;
-  // partitioned plan (strategy 2; batch_partition.cu)
-  std::vector<long long> part_splits;
-  std::vector<PartRangeDev> part_range;
-  std::vector<PartSliceDev> part_slice;
-  int part_max_keys = 0, part_max_bins = 0, part_count_grid = 0, part_row = 8;
-  unsigned short* d_part_cum = nullptr;
-  long long* d_part_splits = nullptr;
-  PartRangeDev* d_part_ranges = nullptr;
-  PartSliceDev* d_part_slices = nullptr;
-  long long* d_part_keys = nullptr;
+  // partitioned plan (strategy 2; batch_partition.cu): one per column
+  std::vector<PartPlan> plans;
   double* d_px = nullptr;            // the partitioned column and weights (capacity part_n_cap events)
   double* d_pw = nullptr;
   long long part_n_cap = 0, part_w_cap = 0;
@@ -1269,11 +1294,7 @@ void batch_release(hist_batch* b) {
   cudaFree(b->d_frags_tune);
   cudaFree(b->d_slice_keys);
   cudaFree(b->d_done);
-  cudaFree(b->d_part_splits);
-  cudaFree(b->d_part_ranges);
-  cudaFree(b->d_part_slices);
-  cudaFree(b->d_part_keys);
-  cudaFree(b->d_part_cum);
+  for (PartPlan& q : b->plans) q.release();
   cudaFree(b->d_px);
   cudaFree(b->d_pw);
   cudaFree(b->d_counts);
@@ -1661,34 +1682,69 @@ int batch_configure(hist_batch* b, int budget) {
 }
 
 // ---- partitioned strategy: planning (see batch_partition.cu) ----
-constexpr int kPartChunk = 1 << 19;   // events per fill work item at most
+constexpr int kPartChunkMax = 1 << 19;  // events per fill work item at most
+constexpr int kPartChunkMin = 1 << 14;  // ... and at least (below: the staging dominates)
+constexpr int kPartWaves = 6;           // work items aimed at per resident fill block
 
 // Bin of a key on a member's thresholds (the largest k with T[k] <= key).
 int host_bin(const std::vector<int64_t>& T, long long key) {
   return (int)(std::upper_bound(T.begin(), T.end(), (int64_t)key) - T.begin()) - 1;
 }
 
-// Cut the column's key space into ranges that fit `budget` bytes of shared
-// memory: every member's thresholds sorted together; a range takes
-// thresholds until the next would pass its capacity C, the next range starts
-// at that threshold (a range's first threshold is a slice boundary, not one
-// of its interior thresholds).  A range costs, per interior threshold, one
-// bin of 8 bytes, one merged key of 8 bytes and one count row of 2 row_u16
-// bytes, plus per member 16 bytes of descriptor and one more bin.
-int part_configure(hist_batch* b, int budget) {
-  const int nh = (int)b->hs.size();
-  if (b->ncols != 1 || b->f32c || nh > kPartMaxMembers) return HIST_ERR_UNSUPPORTED;
-  int maxopt = 0;
-  if (cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess)
-    return HIST_ERR_CUDA;
-  const int limit = maxopt - 8 * 1024;  // the fill kernel's static arrays
-  if (budget > limit) budget = limit;
-  const int row = nh <= 8 ? 8 : 16;
-  const long long C = ((long long)budget - 24LL * nh - 2LL * row - 16) / (16 + 2 * row);
+// The bucket map of M sorted distinct keys (the axes' bucket map, built on
+// the pseudo-axis [-inf, keys..., +inf] with a power of two >= M buckets):
+// its fields in R, its counts appended to bcnt (R.bk_base their first).
+int part_bucket_map(const std::vector<long long>& keys, PartRangeDev* R, std::vector<uint16_t>* bcnt) {
+  const int M = (int)keys.size();
+  R->lo_key = M > 0 ? keys.front() : std::numeric_limits<long long>::max();
+  R->hi_key = M > 0 ? keys.back() : std::numeric_limits<long long>::max();
+  R->kbase = 0;
+  R->scale = R->offset = 0.0f;
+  R->bk_base = (int32_t)bcnt->size();
+  R->nbk = R->key_map = R->shift = R->top = R->pad = 0;
+  if (M < 2) return 0;
+  int nbk = 4;
+  while (nbk < M) nbk *= 2;
+  std::vector<int64_t> T(1, std::numeric_limits<int64_t>::min());
+  T.insert(T.end(), keys.begin(), keys.end());
+  T.push_back(std::numeric_limits<int64_t>::max());
+  BucketMap map;
+  std::vector<int32_t> bc;
+  if (build_bucket_map(M - 1, T.data(), nbk, &map, &bc) < 0) return -1;
+  R->kbase = map.kbase;
+  R->scale = map.scale;
+  R->offset = map.offset;
+  R->nbk = map.nbk;
+  R->key_map = map.key_map;
+  R->shift = map.shift;
+  R->top = map.top;
+  for (int q = 0; q <= nbk; ++q) bcnt->push_back((uint16_t)bc[(size_t)q]);
+  return nbk;
+}
+
+// Plan one column's members [h0, h0 + nh): cut the column's key space into
+// ranges that fit `budget` bytes of shared memory.  Every member's thresholds
+// are sorted together; a range takes thresholds until the next would pass
+// its capacity C, and the next range starts at that threshold (a range's
+// first threshold is a slice boundary, not one of its interior thresholds).
+// A range costs, per interior threshold, one bin of 8 bytes, one merged key
+// of 8 bytes, one count row of 2 row bytes and at most two bucket counts of
+// 2 bytes, plus per member 16 bytes of descriptor, one more bin and up to
+// 31 bin copies (a slice of at most 16 bins keeps 2^rsh <= 32 / len copies
+// of each bin, so that a warp's adds spread over the banks).  Each
+// range gets the axes' bucket map (build_bucket_map) over its merged
+// thresholds, with a power of two >= M buckets.  On success the plan's
+// tables are on the device.
+int part_plan_column(const hist_batch* b, int col, int h0, int nh, int budget, int limit, PartPlan* out) {
+  if (nh < 1 || nh > kPartMaxMembers) return HIST_ERR_UNSUPPORTED;
+  const int row = 8 * ((nh + 7) / 8);
+  const long long C = ((long long)budget - 280LL * nh - 2LL * row - 48) / (20 + 2 * row);
   if (C < 16) return HIST_ERR_UNSUPPORTED;
   std::vector<long long> all;
-  for (const hist* h : b->hs)
-    for (int k = 1; k <= h->nbins[0] + 1; ++k) all.push_back(h->T_host[0][k]);
+  for (int h = h0; h < h0 + nh; ++h) {
+    const hist* m = b->hs[(size_t)h];
+    for (int k = 1; k <= m->nbins[0] + 1; ++k) all.push_back(m->T_host[0][k]);
+  }
   std::sort(all.begin(), all.end());
   std::vector<long long> splits;
   long long acc = 0;
@@ -1709,9 +1765,10 @@ int part_configure(hist_batch* b, int budget) {
   std::vector<PartRangeDev> ranges(nranges);
   std::vector<PartSliceDev> slices((size_t)nranges * nh);
   std::vector<long long> keys;
-  std::vector<uint16_t> cum;
-  int max_keys = 0, max_bins = 0;
+  std::vector<uint16_t> cum, bcnt;
+  int max_keys = 0, max_bins = 0, max_nbk = 0;
   std::vector<long long> merged;
+  std::vector<int> a(nh), e(nh);
   for (int r = 0; r < nranges; ++r) {
     const long long lo = r == 0 ? std::numeric_limits<long long>::min() : splits[(size_t)r - 1];
     const long long hi_m1 = r + 1 < nranges ? splits[(size_t)r] - 1 : std::numeric_limits<long long>::max() - 1;
@@ -1719,17 +1776,17 @@ int part_configure(hist_batch* b, int budget) {
     // the members' slices and their interior thresholds, merged and distinct
     merged.clear();
     int nb = 0;
-    std::vector<int> a(nh), e(nh);
     for (int h = 0; h < nh; ++h) {
-      const std::vector<int64_t>& T = b->hs[(size_t)h]->T_host[0];
+      const std::vector<int64_t>& T = b->hs[(size_t)(h0 + h)]->T_host[0];
       a[h] = host_bin(T, lo);
       e[h] = host_bin(T, hi_m1);
       PartSliceDev& S = slices[(size_t)r * nh + h];
       S.a = a[h];
       S.len = e[h] - a[h] + 1;
       S.boff = nb;
-      S.pad = 0;
-      nb += S.len;
+      S.rsh = 0;
+      while (S.len << (S.rsh + 1) <= 32) ++S.rsh;
+      nb += S.len << S.rsh;
       for (int k = a[h] + 1; k <= e[h]; ++k) merged.push_back(T[(size_t)k]);
     }
     std::sort(merged.begin(), merged.end());
@@ -1744,62 +1801,108 @@ int part_configure(hist_batch* b, int budget) {
     const size_t row0 = cum.size();
     cum.resize(row0 + (size_t)(M + 1) * row, 0);
     for (int h = 0; h < nh; ++h) {
-      const std::vector<int64_t>& T = b->hs[(size_t)h]->T_host[0];
+      const std::vector<int64_t>& T = b->hs[(size_t)(h0 + h)]->T_host[0];
+      const int rsh = slices[(size_t)r * nh + h].rsh;
       int k = a[h] + 1, c = 0;
       for (int q = 1; q <= M; ++q) {
         while (k <= e[h] && T[(size_t)k] <= merged[(size_t)q - 1]) {
           ++k;
           ++c;
         }
-        cum[row0 + (size_t)q * row + h] = (uint16_t)c;
+        cum[row0 + (size_t)q * row + h] = (uint16_t)(c << rsh);
       }
     }
+    // the bucket map of the merged thresholds
+    const int nbk = part_bucket_map(merged, &R, &bcnt);
+    if (nbk < 0) return HIST_ERR_UNSUPPORTED;
+    max_nbk = std::max(max_nbk, nbk);
     max_keys = std::max(max_keys, M);
     max_bins = std::max(max_bins, nb);
   }
   if (keys.size() > (size_t)std::numeric_limits<int32_t>::max() ||
-      cum.size() > (size_t)std::numeric_limits<int32_t>::max())
+      cum.size() > (size_t)std::numeric_limits<int32_t>::max() ||
+      bcnt.size() > (size_t)std::numeric_limits<int32_t>::max())
     return HIST_ERR_UNSUPPORTED;
-  const size_t fill_smem = part_fill_smem(max_keys, max_bins, nh, row);
+  const size_t fill_smem = part_fill_smem(max_keys, max_bins, nh, row, max_nbk);
   if (fill_smem > (size_t)limit) return HIST_ERR_UNSUPPORTED;
-  int count_grid = 0, fill_per_sm = 0;
-  if (part_grids(b->sm_count, nranges, fill_smem, &count_grid, &fill_per_sm) != 0) return HIST_ERR_CUDA;
-  // upload the plan
-  cudaFree(b->d_part_splits);
-  cudaFree(b->d_part_ranges);
-  cudaFree(b->d_part_slices);
-  cudaFree(b->d_part_keys);
-  cudaFree(b->d_part_cum);
-  b->d_part_splits = nullptr;
-  b->d_part_ranges = nullptr;
-  b->d_part_slices = nullptr;
-  b->d_part_keys = nullptr;
-  b->d_part_cum = nullptr;
-  int rc;
-  if ((rc = dalloc(&b->d_part_splits, std::max<size_t>(splits.size(), 1) * 8)) != HIST_OK ||
-      (rc = dalloc(&b->d_part_ranges, sizeof(PartRangeDev) * ranges.size())) != HIST_OK ||
-      (rc = dalloc(&b->d_part_slices, sizeof(PartSliceDev) * slices.size())) != HIST_OK ||
-      (rc = dalloc(&b->d_part_keys, std::max<size_t>(keys.size(), 1) * 8)) != HIST_OK ||
-      (rc = dalloc(&b->d_part_cum, cum.size() * 2)) != HIST_OK)
-    return rc;
-  if ((!splits.empty() &&
-       cudaMemcpy(b->d_part_splits, splits.data(), splits.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) ||
-      cudaMemcpy(b->d_part_ranges, ranges.data(), sizeof(PartRangeDev) * ranges.size(), cudaMemcpyHostToDevice) !=
-          cudaSuccess ||
-      cudaMemcpy(b->d_part_slices, slices.data(), sizeof(PartSliceDev) * slices.size(), cudaMemcpyHostToDevice) !=
-          cudaSuccess ||
-      (!keys.empty() && cudaMemcpy(b->d_part_keys, keys.data(), keys.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) ||
-      cudaMemcpy(b->d_part_cum, cum.data(), cum.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+  PartPlan q;
+  q.col = col;
+  q.h0 = h0;
+  q.nh = nh;
+  q.nranges = nranges;
+  q.max_keys = max_keys;
+  q.max_bins = max_bins;
+  q.max_nbk = max_nbk;
+  q.row = row;
+  q.smem = fill_smem;
+  // the split keys' bucket map (the count and scatter passes' locate)
+  std::vector<uint16_t> sbcnt;
+  if (part_bucket_map(splits, &q.split_map, &sbcnt) < 0) return HIST_ERR_UNSUPPORTED;
+  q.split_map.nkeys = (int32_t)splits.size();
+  if (part_grids(b->sm_count, nranges, q.split_map.nbk, fill_smem, &q.count_grid, &q.fill_per_sm) != 0)
     return HIST_ERR_CUDA;
-  b->part_splits.swap(splits);
-  b->part_range.swap(ranges);
-  b->part_slice.swap(slices);
-  b->part_max_keys = max_keys;
-  b->part_max_bins = max_bins;
-  b->part_row = row;
-  b->part_count_grid = count_grid;
-  // the counts of the count and scatter passes, one per (range, block)
-  const size_t nc = (size_t)nranges * count_grid;
+  int rc;
+  if ((rc = dalloc(&q.d_splits, std::max<size_t>(splits.size(), 1) * 8)) != HIST_OK ||
+      (rc = dalloc(&q.d_ranges, sizeof(PartRangeDev) * ranges.size())) != HIST_OK ||
+      (rc = dalloc(&q.d_slices, sizeof(PartSliceDev) * slices.size())) != HIST_OK ||
+      (rc = dalloc(&q.d_keys, std::max<size_t>(keys.size(), 1) * 8)) != HIST_OK ||
+      (rc = dalloc(&q.d_cum, cum.size() * 2)) != HIST_OK ||
+      (rc = dalloc(&q.d_bcnt, std::max<size_t>(bcnt.size(), 8) * 2)) != HIST_OK ||
+      (rc = dalloc(&q.d_sbcnt, std::max<size_t>(sbcnt.size(), 8) * 2)) != HIST_OK) {
+    q.release();
+    return rc;
+  }
+  if ((!splits.empty() &&
+       cudaMemcpy(q.d_splits, splits.data(), splits.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(q.d_ranges, ranges.data(), sizeof(PartRangeDev) * ranges.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(q.d_slices, slices.data(), sizeof(PartSliceDev) * slices.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      (!keys.empty() && cudaMemcpy(q.d_keys, keys.data(), keys.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(q.d_cum, cum.data(), cum.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (!bcnt.empty() && cudaMemcpy(q.d_bcnt, bcnt.data(), bcnt.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      (!sbcnt.empty() &&
+       cudaMemcpy(q.d_sbcnt, sbcnt.data(), sbcnt.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)) {
+    q.release();
+    return HIST_ERR_CUDA;
+  }
+  *out = q;
+  return HIST_OK;
+}
+
+// The partitioned strategy: one plan per column (exact precision only; every
+// column at most kPartMaxMembers members).
+int part_configure(hist_batch* b, int budget) {
+  if (b->f32c) return HIST_ERR_UNSUPPORTED;
+  int maxopt = 0;
+  if (cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess)
+    return HIST_ERR_CUDA;
+  const int limit = maxopt - 8 * 1024;  // the fill kernel's static arrays
+  if (budget > limit) budget = limit;
+  for (int c = 0; c < b->ncols; ++c)
+    if (b->col_begin[c + 1] - b->col_begin[c] > kPartMaxMembers) return HIST_ERR_UNSUPPORTED;
+  std::vector<PartPlan> plans;
+  int rc = HIST_OK;
+  for (int c = 0; c < b->ncols && rc == HIST_OK; ++c) {
+    const int h0 = b->col_begin[c], nh = b->col_begin[c + 1] - h0;
+    if (nh == 0) continue;
+    PartPlan q;
+    rc = part_plan_column(b, c, h0, nh, budget, limit, &q);
+    if (rc == HIST_OK) plans.push_back(q);
+  }
+  if (rc != HIST_OK) {
+    for (PartPlan& q : plans) q.release();
+    return rc;
+  }
+  for (PartPlan& q : b->plans) q.release();
+  b->plans.swap(plans);
+  // the counts of the count and scatter passes, one per (range, block),
+  // shared by the plans (their fills run one after the other)
+  size_t nc = 0, smem = 0;
+  for (const PartPlan& q : b->plans) {
+    nc = std::max(nc, (size_t)q.nranges * q.count_grid);
+    smem = std::max(smem, q.smem);
+  }
   if (nc > b->counts_cap) {
     cudaFree(b->d_counts);
     cudaFree(b->d_offsets);
@@ -1811,10 +1914,10 @@ int part_configure(hist_batch* b, int budget) {
   }
   if (b->d_nitems == nullptr && (rc = dalloc(&b->d_nitems, 16)) != HIST_OK) return rc;
   if (b->d_rscan == nullptr && (rc = dalloc(&b->d_rscan, (size_t)kPartMaxRanges * 20)) != HIST_OK) return rc;
-  b->smem = fill_smem;
+  b->smem = smem;
   b->smem_budget = budget;
   b->strategy = 2;
-  b->grid = 0;  // the fill's grid depends on the events: batch_reserve
+  b->grid = 0;  // the fills' grids depend on the events: batch_reserve
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
@@ -1822,8 +1925,20 @@ int part_configure(hist_batch* b, int budget) {
   return HIST_OK;
 }
 
-int part_items(const hist_batch* b, int64_t n) {
-  return (int)b->part_range.size() + (int)((n + kPartChunk - 1) / kPartChunk) + 1;
+// Events per work item for a fill of n events: about kPartWaves items per
+// resident fill block (so the last wave is short), within the bounds above.
+int part_chunk(const PartPlan& q, int sm_count, int64_t n) {
+  const long long target = (long long)kPartWaves * std::max(1, q.fill_per_sm) * sm_count;
+  long long c = (n + target - 1) / target;
+  c = std::max<long long>(kPartChunkMin, std::min<long long>(kPartChunkMax, c));
+  return (int)c;
+}
+
+// Work items of a fill of n events, at most (each range's events in runs of
+// at most one chunk).
+int part_items(const PartPlan& q, int sm_count, int64_t n) {
+  const int chunk = part_chunk(q, sm_count, n);
+  return q.nranges + (int)((n + chunk - 1) / chunk) + 1;
 }
 
 int batch_check_args(const hist_batch* b, const double* const* cols, int ncols, const double* weights, int64_t n) {
@@ -1878,19 +1993,30 @@ int batch_reserve(hist_batch* b, int64_t n, bool weighted) {
       if ((rc = dalloc(&b->d_pw, (size_t)cap * 8)) != HIST_OK) return rc;
       b->part_w_cap = cap;
     }
-    const int items = part_items(b, n);
-    if (items > b->items_cap) {
+    // each column's fill: its work items and its blocks' statistics
+    // partials (after the previous columns')
+    int total = 0, most = 0;
+    bool changed = false;
+    for (PartPlan& q : b->plans) {
+      const int items = part_items(q, b->sm_count, n);
+      changed = changed || items != q.items || total != q.block_base;
+      q.items = items;
+      q.block_base = total;
+      total += items;
+      most = std::max(most, items);
+    }
+    if (most > b->items_cap) {
       cudaFree(b->d_items);
       b->d_items = nullptr;
       b->items_cap = 0;
-      if ((rc = dalloc(&b->d_items, sizeof(PartItem) * (size_t)items)) != HIST_OK) return rc;
-      b->items_cap = items;
+      if ((rc = dalloc(&b->d_items, sizeof(PartItem) * (size_t)most)) != HIST_OK) return rc;
+      b->items_cap = most;
     }
-    if (items != b->grid && b->exec) {  // a captured fill launched another grid
+    if ((changed || total != b->grid) && b->exec) {  // a captured fill launched other grids
       cudaGraphExecDestroy(b->exec);
       b->exec = nullptr;
     }
-    b->grid = items;
+    b->grid = total;
     return batch_part_stats(b);
   }
   if (b->strategy != 1) return HIST_OK;
@@ -1908,40 +2034,51 @@ int batch_reserve(hist_batch* b, int64_t n, bool weighted) {
 int batch_launch(const hist_batch* b, const double* const* cols, const double* weights, int64_t n, bool tune,
                  cudaStream_t s) {
   if (b->strategy == 2) {
-    PartParams p;
-    std::memset(&p, 0, sizeof(p));
-    p.col = cols[0];
-    p.w = weights;
-    p.px = b->d_px;
-    p.pw = weights != nullptr ? b->d_pw : nullptr;
-    p.splits = b->d_part_splits;
-    p.ranges = b->d_part_ranges;
-    p.slices = b->d_part_slices;
-    p.keys = b->d_part_keys;
-    p.cum = b->d_part_cum;
-    p.row_u16 = b->part_row;
-    p.hists = tune ? b->d_desc_tune : b->d_desc;
-    p.counts = b->d_counts;
-    p.offsets = b->d_offsets;
-    p.rtotal = b->d_rscan;
-    p.rstart = b->d_rscan + kPartMaxRanges;
-    p.ibase = reinterpret_cast<int*>(b->d_rscan + 2 * kPartMaxRanges);
-    p.items = b->d_items;
-    p.nitems = b->d_nitems;
-    p.part_stats = b->d_part_stats;
-    p.n = n;
-    p.nranges = (int)b->part_range.size();
-    p.nh = (int)b->hs.size();
-    p.grid_count = b->part_count_grid;
-    p.fx_elo = kDefaultFxElo;
-    p.chunk = kPartChunk;
-    p.max_items = b->grid;
-    p.max_keys = b->part_max_keys;
-    p.max_bins = b->part_max_bins;
-    p.st = b->st;
-    if (p.max_items != part_items(b, n) || (weights != nullptr && b->part_w_cap < n) || b->part_n_cap < n)
-      return HIST_ERR_CUDA;  // batch_reserve sized the scratch for these events
-    if (launch_part_fill(p, weights == nullptr, b->grid, b->smem, s) != 0) return HIST_ERR_CUDA;
+    if ((weights != nullptr && b->part_w_cap < n) || b->part_n_cap < n) return HIST_ERR_CUDA;
+    // one column after the other: they share the partitioned copy, the
+    // counts and the work items
+    for (const PartPlan& q : b->plans) {
+      PartParams p;
+      std::memset(&p, 0, sizeof(p));
+      p.col = cols[q.col];
+      p.w = weights;
+      p.px = b->d_px;
+      p.pw = weights != nullptr ? b->d_pw : nullptr;
+      p.splits = q.d_splits;
+      p.ranges = q.d_ranges;
+      p.slices = q.d_slices;
+      p.keys = q.d_keys;
+      p.cum = q.d_cum;
+      p.bcnt = q.d_bcnt;
+      p.sbcnt = q.d_sbcnt;
+      p.split_map = q.split_map;
+      p.row_u16 = q.row;
+      p.hists = (tune ? b->d_desc_tune : b->d_desc) + q.h0;
+      p.counts = b->d_counts;
+      p.offsets = b->d_offsets;
+      p.rtotal = b->d_rscan;
+      p.rstart = b->d_rscan + kPartMaxRanges;
+      p.ibase = reinterpret_cast<int*>(b->d_rscan + 2 * kPartMaxRanges);
+      p.items = b->d_items;
+      p.nitems = b->d_nitems;
+      p.part_stats = b->d_part_stats + (size_t)q.block_base * kStatSlots * 3;
+      p.n = n;
+      p.nranges = q.nranges;
+      p.nh = q.nh;
+      p.grid_count = q.count_grid;
+      p.fx_elo = kDefaultFxElo;
+      p.chunk = part_chunk(q, b->sm_count, n);
+      p.max_items = q.items;
+      p.max_keys = q.max_keys;
+      p.max_bins = q.max_bins;
+      p.max_nbk = q.max_nbk;
+      p.stat_col = q.col;
+      p.st = b->st;
+      if (q.items != part_items(q, b->sm_count, n) || q.items > b->items_cap ||
+          (size_t)q.nranges * q.count_grid > b->counts_cap || q.block_base + q.items > b->part_blocks)
+        return HIST_ERR_CUDA;  // batch_reserve sized the scratch for these events
+      if (launch_part_fill(p, weights == nullptr, q.items, q.smem, s) != 0) return HIST_ERR_CUDA;
+    }
   } else if (b->strategy == 1) {
     SliceParams p;
     std::memset(&p, 0, sizeof(p));
@@ -2229,8 +2366,8 @@ void batch_report(const hist_batch* b, hist_batch_tuning_t* r) {
   } else if (b->strategy == 1) {
     slice_max_blocks_per_sm(kSliceBlock, b->smem, &per_sm);
   } else {
-    int cg = 0;
-    part_grids(b->sm_count, (int)b->part_range.size(), b->smem, &cg, &per_sm);
+    per_sm = 1 << 30;
+    for (const PartPlan& q : b->plans) per_sm = std::min(per_sm, q.fill_per_sm);
   }
   r->blocks_per_sm = per_sm;
   int nsm = 0;
@@ -2240,7 +2377,9 @@ void batch_report(const hist_batch* b, hist_batch_tuning_t* r) {
     nsm = (int)b->hs.size();
   r->smem_hists = nsm;
   r->strategy = b->strategy;
-  r->slices = b->strategy == 1 ? (int)b->slices.size() : (b->strategy == 2 ? (int)b->part_range.size() : 0);
+  int nranges = 0;
+  for (const PartPlan& q : b->plans) nranges += q.nranges;
+  r->slices = b->strategy == 1 ? (int)b->slices.size() : (b->strategy == 2 ? nranges : 0);
   r->replicas = b->strategy == 1 ? b->slice_replicas : 0;
   r->cost_cap_tenths = b->strategy == 1 ? (int)(10.0 * b->slice_cap + 0.5) : 0;
   r->events_per_thread = b->strategy == 0 ? b->wide_kev : 4;
@@ -2272,7 +2411,7 @@ extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int n
   if (!(b->flags & HIST_BATCH_WIDE))
     for (int kb : {96, 200})
       for (double cap : {3.0, 12.0}) cands.push_back({1, kb * 1024, cap, 2, 4});
-  if (!(b->flags & (HIST_BATCH_WIDE | HIST_BATCH_SLICED)) && b->ncols == 1 && !b->f32c)
+  if (!(b->flags & (HIST_BATCH_WIDE | HIST_BATCH_SLICED)) && !b->f32c)
     for (int kb : {48, 100, 200}) cands.push_back({2, kb * 1024, 0.0, 2, 4});
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HIST_ERR_CUDA;

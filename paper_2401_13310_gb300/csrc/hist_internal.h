@@ -292,19 +292,32 @@ struct SliceParams {
 // by range, then each work item (a range and a run of its events) fills the
 // slices in shared memory.
 constexpr int kPartBlock = 256;
-constexpr int kPartMaxMembers = 16;   // members of a partitioned batch (16-bit counts, 32-byte rows)
+constexpr int kPartMaxMembers = 32;   // members per column of a partitioned batch (16-bit counts, rows <= 64 bytes)
 constexpr int kPartMaxRanges = 2048;
+constexpr int kPartTile = 2048;       // events per tile of the count and scatter passes (8 per thread)
 struct PartRangeDev {
   int32_t key_base;             // its merged thresholds in the concatenated key array
   int32_t nkeys;                // how many (M); positions p = 0 .. M
   int32_t nbins;                // bin slots of all its slices
   int32_t cum_base;             // its count rows (M + 1 of row_u16 each) in the concatenated count array
+  // bucket map of the merged thresholds (the axes' bucket map, on them):
+  // keys below lo_key have position 0, keys from hi_key on position M; a
+  // key in between lies in bucket b, whose thresholds are merged positions
+  // bcnt[b] .. bcnt[b + 1] - 1
+  int64_t lo_key, hi_key;       // first and last merged threshold (M >= 1; M = 0: both INT64_MAX)
+  int64_t kbase;                // key map: bucket = (key >> shift) - kbase
+  float scale, offset;          // linear map of the truncated coordinate
+  int32_t bk_base;              // its bucket counts ([nbk + 1] u16) in the concatenated bucket array
+  int32_t nbk;                  // buckets (0: M <= 1, the bounds decide)
+  int32_t key_map, shift;
+  int32_t top;                  // largest power of two <= the most thresholds in one bucket (0: none)
+  int32_t pad;
 };
 struct PartSliceDev {           // one member over one range
   int32_t a;                    // first bin
   int32_t len;                  // bins a .. a + len - 1
   int32_t boff;                 // its first bin slot in the range's shared bins
-  int32_t pad;
+  int32_t rsh;                  // log2 of its copies per bin: bin a + c has slots boff + (c << rsh) + (lane & (2^rsh - 1))
 };
 struct PartItem {
   long long e0, e1;             // events [e0, e1) of the partitioned column
@@ -321,6 +334,9 @@ struct PartParams {
   const PartSliceDev* slices;   // [nranges][nh]
   const long long* keys;        // every range's merged thresholds, back to back
   const unsigned short* cum;    // every range's count rows, back to back
+  const unsigned short* bcnt;   // every range's bucket counts, back to back
+  const unsigned short* sbcnt;  // the split keys' bucket counts ([split_map.nbk + 1])
+  PartRangeDev split_map;       // the bucket map of the split keys (nkeys = nranges - 1)
   const BatchHistDev* hists;    // [nh] the members' accumulators (or tuning scratch)
   unsigned* counts;             // [nranges][grid_count] events per (range, block)
   unsigned long long* offsets;  // [nranges][grid_count] their exclusive prefix sums
@@ -335,12 +351,15 @@ struct PartParams {
   int32_t chunk;                // events per work item at most
   int32_t max_items;
   int32_t max_keys, max_bins;   // the largest range's thresholds and bin slots
-  int32_t row_u16;              // u16 per count row: 8 (nh <= 8) or 16
+  int32_t max_nbk;              // the most buckets of a range
+  int32_t row_u16;              // u16 per count row: nh rounded up to 8, 16, 24 or 32
+  int32_t stat_col;             // the column's index among the batch's columns (its statistics slots)
   BatchStatsSpec st;
 };
-size_t part_count_smem(int nranges);
-size_t part_fill_smem(int max_keys, int max_bins, int nh, int row_u16);
-int part_grids(int sm_count, int nranges, size_t fill_smem, int* count_grid, int* fill_per_sm);
+size_t part_count_smem(int nranges, int split_nbk);
+size_t part_scatter_smem(int nranges, int split_nbk, bool weighted);
+size_t part_fill_smem(int max_keys, int max_bins, int nh, int row_u16, int max_nbk);
+int part_grids(int sm_count, int nranges, int split_nbk, size_t fill_smem, int* count_grid, int* fill_per_sm);
 int launch_part_fill(const PartParams& p, bool unit, int fill_grid, size_t fill_smem, void* stream);
 
 int launch_slice_fill(const SliceParams& p, int block, int grid, size_t smem, void* stream);

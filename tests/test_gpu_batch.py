@@ -1,9 +1,11 @@
 """The batched fill: every histogram of a batch filled from one event stream
 in one launch must match the CPU oracle filled one histogram at a time
-(counts exact, sums within 1e-12 of sum |term|), under both privatisation
-strategies (wide: per-block shared bins for the small histograms, global
+(counts exact, sums within 1e-12 of sum |term|), under each privatisation
+strategy (wide: per-block shared bins for the small histograms, global
 atomics for the rest; sliced: every bin in shared memory, large histograms
-cut into fragments across blocks)."""
+cut into fragments across blocks; partitioned: each column's events
+partitioned by coordinate range, every member's bins of a range in one
+block's shared memory)."""
 import numpy as np
 import pytest
 
@@ -325,17 +327,22 @@ def test_batch_partitioned_matches_oracle(B, weighted, budget):
             h.close()
 
 
+@pytest.mark.parametrize("ncols", [1, 2])
 @pytest.mark.parametrize("weighted", [False, True])
-def test_batch_partitioned_edges_specials_and_accumulate(B, weighted):
+def test_batch_partitioned_edges_specials_and_accumulate(B, weighted, ncols):
     """Every threshold of every member and its neighbouring doubles (so
     every range boundary and slice boundary), signed zeros, infinities,
     NaN, subnormals; odd weights; two fills accumulate like one of the
-    concatenation (graph replay)."""
+    concatenation (graph replay).  With two columns the members alternate
+    between the probe points and the same points reversed: each column is
+    partitioned and filled on its own, its statistics in its own slots."""
     rng = np.random.default_rng(72)
     bw = _one_column_batch(10, 73)
     pts = np.concatenate([edge_probe_values(ax, B.hist_axis_thresholds(ax), rng, nrand=300) for ax in bw.axes])
     pts = pts[rng.permutation(pts.size)]
     n = pts.size
+    columns = [pts, pts[::-1].copy()][:ncols]
+    col_of_hist = [i % ncols for i in range(len(bw.axes))]
     w = rng.uniform(-2.0, 2.0, n) if weighted else None
     if weighted:
         w[::97] = 0.0
@@ -344,17 +351,18 @@ def test_batch_partitioned_edges_specials_and_accumulate(B, weighted):
     hists = [B.Hist([ax]) for ax in bw.axes]
     batch = None
     try:
-        batch = B.Batch(hists, bw.col_of_hist, B.HIST_BATCH_GRAPH)
-        batch.configure(2, 8 << 10)
-        col = to_device(pts)
+        batch = B.Batch(hists, col_of_hist, B.HIST_BATCH_GRAPH)
+        info = batch.configure(2, 8 << 10)
+        assert info["strategy"] == 2
+        cols = [to_device(c) for c in columns]
         wd = to_device(w)
-        batch.fill([col], wd)
-        batch.fill([col], wd)
-        two = np.concatenate([pts, pts]).reshape(1, -1)
+        batch.fill(cols, wd)
+        batch.fill(cols, wd)
         w2 = None if w is None else np.concatenate([w, w])
         for i, (h, ax) in enumerate(zip(hists, bw.axes)):
             bins, stats = h.result()
-            ref = oracle.fill([ax], two, w2)
+            c = columns[col_of_hist[i]]
+            ref = oracle.fill([ax], np.concatenate([c, c]).reshape(1, -1), w2)
             if w2 is None:
                 assert np.array_equal(bins, ref.counts.astype(np.float64)), f"hist {i}"
             else:
@@ -368,17 +376,48 @@ def test_batch_partitioned_edges_specials_and_accumulate(B, weighted):
             h.close()
 
 
-def test_batch_partitioned_needs_one_column(B):
-    bw = W.cfg4(n=1000)
-    hists = [B.Hist([ax]) for ax in bw.axes[:6]]
+@pytest.mark.parametrize("weighted", [True, False])
+@pytest.mark.parametrize("budget", [48 << 10, 100 << 10])
+def test_batch_partitioned_several_columns(B, weighted, budget):
+    """The 64-histogram batch (three columns of 22, 21 and 21 members, rows
+    of 24 counts) with the partitioned strategy pinned: each column's
+    members partitioned and filled in turn, against the oracle."""
+    bw = W.cfg4(n=200_003)
+    hists = [B.Hist([ax]) for ax in bw.axes]
     batch = None
     try:
-        batch = B.Batch(hists, bw.col_of_hist[:6])
-        with pytest.raises(B.HistError) as e:
-            batch.configure(2, 64 << 10)
-        assert e.value.code == B.HIST_ERR_UNSUPPORTED
+        batch = B.Batch(hists, bw.col_of_hist)
+        info = batch.configure(2, budget)
+        assert info["strategy"] == 2 and info["slices"] >= 3
+        cols = [to_device(np.ascontiguousarray(bw.columns[c])) for c in range(3)]
+        w = bw.weights if weighted else None
+        batch.fill(cols, to_device(w))
+        _check(bw, hists, w, f"partitioned 3 columns budget={budget} w={weighted}")
     finally:
         if batch is not None:
             batch.close()
+        for h in hists:
+            h.close()
+
+
+def test_batch_partitioned_member_limit_per_column(B):
+    """At most 32 members per column: 32 on one column and 33 split over
+    two columns are accepted; 33 on one column are not."""
+    axes = [W.fixed(10 + i, -1.0, 1.0) for i in range(33)]  # (one range: one statistics group per column)
+    hists = [B.Hist([ax]) for ax in axes]
+    try:
+        for members, cols, ok in ((32, [0] * 32, True), (33, [i % 2 for i in range(33)], True),
+                                  (33, [0] * 33, False)):
+            batch = B.Batch(hists[:members], cols)
+            try:
+                if ok:
+                    assert batch.configure(2, 64 << 10)["strategy"] == 2
+                else:
+                    with pytest.raises(B.HistError) as e:
+                        batch.configure(2, 64 << 10)
+                    assert e.value.code == B.HIST_ERR_UNSUPPORTED
+            finally:
+                batch.close()
+    finally:
         for h in hists:
             h.close()

@@ -66,8 +66,8 @@ def _check_weighted(results, bw, refs, what, counts=None, rtol_bins=RTOL):
 
 def test_cfg4_full_size_plain_and_batched(B, cfg4_ref):
     """64 histograms x 5e7 events: the 64 plain fills (with per-bin counts),
-    the batch after tuning on a 4e6-event sample, and the wide and sliced
-    strategies pinned -- each against the oracle."""
+    the batch after tuning on a 4e6-event sample, and the wide, sliced and
+    partitioned strategies pinned -- each against the oracle."""
     import torch
     bw, refs = cfg4_ref
     cols = [to_device(np.ascontiguousarray(bw.columns[c])) for c in range(3)]
@@ -84,7 +84,8 @@ def test_cfg4_full_size_plain_and_batched(B, cfg4_ref):
             h.close()
     # batched: tuned, then each strategy pinned; the FP32 compensated batch
     plans = [("tuned", None, 0), ("wide", (0, 48 << 10, 30, -1, 2, 2), 0),
-             ("sliced", (1, 200 << 10, 30, -1, 2, 4), 0), ("fp32c tuned", None, B.HIST_PREC_FP32C)]
+             ("sliced", (1, 200 << 10, 30, -1, 2, 4), 0), ("partitioned", (2, 100 << 10, 30, -1, 2, 4), 0),
+             ("fp32c tuned", None, B.HIST_PREC_FP32C)]
     for name, cfg, prec in plans:
         hists = [B.Hist([ax], prec) for ax in bw.axes]
         batch = None
