@@ -128,15 +128,20 @@ __global__ void __launch_bounds__(kPartBlock) k_part_count(const __grid_constant
   const unsigned long long* xq = reinterpret_cast<const unsigned long long*>(p.col);
   constexpr int kPer = kPartTile / kPartBlock;
   for (long long base = (long long)blockIdx.x * kPartTile; base < p.n; base += (long long)gridDim.x * kPartTile) {
+    // the tile's loads first (all in flight together), then the locates
+    unsigned long long x[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const long long i = base + threadIdx.x + (long long)k * kPartBlock;
+      x[k] = i < p.n ? __ldcs(xq + i) : 0ull;
+    }
 #pragma unroll
     for (int k = 0; k < kPer; k += 2) {
       const long long i0 = base + threadIdx.x + (long long)k * kPartBlock, i1 = i0 + kPartBlock;
-      const bool v0 = i0 < p.n, v1 = i1 < p.n;
-      const unsigned long long x0 = v0 ? __ldcs(xq + i0) : 0ull, x1 = v1 ? __ldcs(xq + i1) : 0ull;
       int r0, r1;
-      L.locate2(key_of(x0), x0, key_of(x1), x1, r0, r1);
-      if (v0) atomicAdd(&cnt[r0], 1u);
-      if (v1) atomicAdd(&cnt[r1], 1u);
+      L.locate2(key_of(x[k]), x[k], key_of(x[k + 1]), x[k + 1], r0, r1);
+      if (i0 < p.n) atomicAdd(&cnt[r0], 1u);
+      if (i1 < p.n) atomicAdd(&cnt[r1], 1u);
     }
   }
   __syncthreads();
@@ -290,19 +295,19 @@ __global__ void __launch_bounds__(kPartBlock) k_part_scatter(const __grid_consta
     unsigned long long x[kPer], w[kPer];
     int r[kPer];
     unsigned rank[kPer];
+    // the tile's loads first (all in flight together), then the locates
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const long long i = base + threadIdx.x + (long long)k * kPartBlock;
+      x[k] = i < p.n ? __ldcs(xq + i) : 0ull;
+      if (WEIGHTED) w[k] = i < p.n ? __ldcs(wq + i) : 0ull;
+    }
 #pragma unroll
     for (int k = 0; k < kPer; k += 2) {
       const long long i0 = base + threadIdx.x + (long long)k * kPartBlock, i1 = i0 + kPartBlock;
-      const bool v0 = i0 < p.n, v1 = i1 < p.n;
-      x[k] = v0 ? __ldcs(xq + i0) : 0ull;
-      x[k + 1] = v1 ? __ldcs(xq + i1) : 0ull;
-      if (WEIGHTED) {
-        w[k] = v0 ? __ldcs(wq + i0) : 0ull;
-        w[k + 1] = v1 ? __ldcs(wq + i1) : 0ull;
-      }
       L.locate2(key_of(x[k]), x[k], key_of(x[k + 1]), x[k + 1], r[k], r[k + 1]);
-      rank[k] = v0 ? atomicAdd(&tcnt[r[k]], 1u) : 0u;
-      rank[k + 1] = v1 ? atomicAdd(&tcnt[r[k + 1]], 1u) : 0u;
+      rank[k] = i0 < p.n ? atomicAdd(&tcnt[r[k]], 1u) : 0u;
+      rank[k + 1] = i1 < p.n ? atomicAdd(&tcnt[r[k + 1]], 1u) : 0u;
     }
     __syncthreads();
     block_exclusive_scan(tcnt, tstart, nr, wsum);
@@ -337,9 +342,11 @@ __global__ void __launch_bounds__(kPartBlock) k_part_scatter(const __grid_consta
   }
 }
 
-// Signed fixed-point value V into a shared bin's two u32 words with carries;
-// the rare change of the top (a carry out of bit 63, or a negative addend's
-// sign) goes to the global high word in units of 2^32.
+// Signed fixed-point value V into a shared bin's two u32 words with carries
+// (two 32-bit atomics that return the old value: one 64-bit shared atomic
+// measured 1.5x slower on the 64-histogram workload); the rare change of
+// the top (a carry out of bit 63, or a negative addend's sign) goes to the
+// global high word in units of 2^32.
 __device__ __forceinline__ void part_fx_add(unsigned* a, long long* ghi, long long V) {
   const unsigned v0 = (unsigned)V;
   const unsigned o0 = atomicAdd(a, v0);
@@ -390,8 +397,19 @@ struct PartFill {
   }
 };
 
+// Threads per fill block (256), and the blocks per SM its registers are
+// sized for: weighted fills three (80 registers, so that the small ranges of
+// a 48 KB budget run three blocks per SM -- the fill waits mostly on
+// shared-memory latency, so resident warps set its pace), unit-weight fills
+// two (their 64 registers fit three anyway; 512-thread blocks measured 4 %
+// slower on the 8-axis workload).
+template <bool UNIT>
+__host__ __device__ constexpr int part_fill_block() {
+  return 256;
+}
+
 template <bool UNIT, int ROW>
-__global__ void __launch_bounds__(kPartBlock) k_part_fill(const __grid_constant__ PartParams p) {
+__global__ void __launch_bounds__(part_fill_block<UNIT>(), UNIT ? 4 : 3) k_part_fill(const __grid_constant__ PartParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // [count rows][bucket counts][merged keys][slices][bins], each part
   // 16-byte aligned
@@ -403,7 +421,7 @@ __global__ void __launch_bounds__(kPartBlock) k_part_fill(const __grid_constant_
   PartSliceDev* sl = reinterpret_cast<PartSliceDev*>(smem_raw + cum_bytes + bcnt_bytes + (size_t)p.max_keys * 8);
   unsigned* bins = reinterpret_cast<unsigned*>(smem_raw + cum_bytes + bcnt_bytes + (size_t)p.max_keys * 8 +
                                                sizeof(PartSliceDev) * p.nh);
-  __shared__ double sred[(kPartBlock / 32) * kStatSlots * 3];
+  __shared__ double sred[(part_fill_block<UNIT>() / 32) * kStatSlots * 3];
   __shared__ PartItem item;
   __shared__ PartRangeDev range;
 
@@ -532,6 +550,8 @@ const void* part_fill_row(int row) {
 // row: u16 per count row, 8, 16, 24 or 32
 const void* part_fill_fn(bool unit, int row) { return unit ? part_fill_row<true>(row) : part_fill_row<false>(row); }
 
+int part_fill_threads(bool unit) { return unit ? part_fill_block<true>() : part_fill_block<false>(); }
+
 }  // namespace
 
 size_t part_count_smem(int nranges, int split_nbk) {
@@ -568,10 +588,11 @@ int part_grids(int sm_count, int nranges, int split_nbk, size_t fill_smem, int* 
                                                     kPartBlock, ss) != cudaSuccess)
     return -2;
   for (int v = 0; v < 8; ++v) {
-    const void* fn = part_fill_fn(v & 1, 8 * (1 + (v >> 1)));
+    const bool unit = v & 1;
+    const void* fn = part_fill_fn(unit, 8 * (1 + (v >> 1)));
     int a = 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fn, kPartBlock, fill_smem) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fn, part_fill_threads(unit), fill_smem) != cudaSuccess)
       return -2;
     least = a < least ? a : least;
   }
@@ -602,7 +623,8 @@ int launch_part_fill(const PartParams& p, bool unit, int fill_grid, size_t fill_
   k_part_offsets<<<wblocks, 256, 0, s>>>(p);
   void* args[] = {const_cast<PartParams*>(&p)};
   if (cudaLaunchKernel(scatter, dim3(p.grid_count), dim3(kPartBlock), args, ss, s) != cudaSuccess) return -2;
-  if (cudaLaunchKernel(fill, dim3(fill_grid), dim3(kPartBlock), args, fill_smem, s) != cudaSuccess) return -2;
+  if (cudaLaunchKernel(fill, dim3(fill_grid), dim3(part_fill_threads(unit)), args, fill_smem, s) != cudaSuccess)
+    return -2;
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -1877,7 +1877,7 @@ int part_configure(hist_batch* b, int budget) {
   int maxopt = 0;
   if (cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess)
     return HIST_ERR_CUDA;
-  const int limit = maxopt - 8 * 1024;  // the fill kernel's static arrays
+  const int limit = maxopt - 10 * 1024;  // the fill kernel's static arrays
   if (budget > limit) budget = limit;
   for (int c = 0; c < b->ncols; ++c)
     if (b->col_begin[c + 1] - b->col_begin[c] > kPartMaxMembers) return HIST_ERR_UNSUPPORTED;

@@ -170,13 +170,14 @@ def test_batch_unit_weights_many_edges_tuned(B):
 
 def test_batch_configurations_agree_exactly(B):
     """Pinned configurations (wide at two register budgets and events per
-    thread, sliced at two slice sizes): the exact fixed-point bins are
-    bit-identical whatever the configuration; statistics within tolerance."""
+    thread, sliced at two slice sizes, partitioned at two range sizes): the
+    exact fixed-point bins are bit-identical whatever the configuration;
+    statistics within tolerance."""
     bw = W.cfg4(n=150_001)
     cols = [to_device(np.ascontiguousarray(bw.columns[c])) for c in range(3)]
     w = to_device(bw.weights)
     configs = [(0, 48 << 10, 30, -1, 2, 4), (0, 96 << 10, 30, -1, 4, 2), (1, 96 << 10, 30, -1, 2, 4),
-               (1, 200 << 10, 120, 0, 2, 4)]
+               (1, 200 << 10, 120, 0, 2, 4), (2, 24 << 10, 30, -1, 2, 4), (2, 100 << 10, 30, -1, 2, 4)]
     results = []
     for cfg in configs:
         hists = [B.Hist([ax]) for ax in bw.axes]
@@ -197,6 +198,48 @@ def test_batch_configurations_agree_exactly(B):
             assert np.array_equal(b0, b1), f"hist {i} bins differ between configurations"
             ref = oracle.fill([bw.axes[i]], bw.columns[bw.col_of_hist[i]].reshape(1, -1), bw.weights)
             assert_sums_close(s1[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, f"hist {i} stats")
+
+
+def test_batch_sliced_pacing_window_does_not_change_bins(B):
+    """The sliced strategy's blocks pace themselves (a bounded wait every 16
+    tiles until every slice has passed the tile a window back; the waits of
+    one block in one launch are capped in total).  The tightest window the
+    configuration allows, on a fill long enough (8e6 events, ~3900 tiles)
+    for the cap to be spent, the default window and no pacing at all give
+    bit-identical exact bins, equal to the oracle's for unit weights: the
+    pacing only orders work for L2 locality."""
+    import torch
+    rng = np.random.default_rng(81)
+    bw = W.cfg4(n=10)
+    n = 8_000_000
+    cols_h = [rng.exponential(30.0, n), rng.uniform(-np.pi, np.pi, n), rng.normal(0.0, 2.5, n)]
+    cols = [to_device(c) for c in cols_h]
+    w = rng.uniform(0.5, 1.5, n)
+    wd = to_device(w)
+    results = {}
+    for pace in (1, -1, 0):
+        for weighted in (False, True):
+            hists = [B.Hist([ax]) for ax in bw.axes]
+            batch = None
+            try:
+                batch = B.Batch(hists, bw.col_of_hist)
+                assert batch.configure(1, 96 << 10, 30, pace, 2, 4)["strategy"] == 1
+                batch.fill(cols, wd if weighted else None)
+                torch.cuda.synchronize()
+                results[(pace, weighted)] = [h.result()[0] for h in hists]
+            finally:
+                if batch is not None:
+                    batch.close()
+                for h in hists:
+                    h.close()
+    for weighted in (False, True):
+        base = results[(0, weighted)]
+        for pace in (1, -1):
+            for i, (a, b) in enumerate(zip(base, results[(pace, weighted)])):
+                assert np.array_equal(a, b), f"hist {i}: pace {pace} changed the bins (weighted={weighted})"
+    for i in (0, 21, 42, 63):  # unit-weight bins against the oracle
+        ref = oracle.fill([bw.axes[i]], cols_h[bw.col_of_hist[i]].reshape(1, -1), None)
+        assert np.array_equal(results[(1, False)][i], ref.counts.astype(np.float64)), f"hist {i}"
 
 
 def test_batch_tuned_for_unit_then_weighted_fill(B):
