@@ -301,7 +301,10 @@ def measure_forms(B, W, hbm: float, args) -> dict:
             h.fill(cols[c], w)
     t_plain = _timed(plain4, 3)
     batch = B.Batch(hists, bw.col_of_hist, B.HIST_BATCH_GRAPH)
-    tune = batch.tune([c[:4_000_000] for c in cols], w[:4_000_000])
+    # (the tuning sample must be large enough for the partitioned strategy's
+    # per-range staging to amortise as it does on the full fill)
+    ns = min(n4, 20_000_000)
+    tune = batch.tune([c[:ns] for c in cols], w[:ns])
     for h in hists:
         h.reset()
     batch.fill(cols, w)
@@ -314,7 +317,7 @@ def measure_forms(B, W, hbm: float, args) -> dict:
     # the same batch with FP32 compensated shared-memory partials
     hists = [B.Hist([ax], B.HIST_PREC_FP32C) for ax in bw.axes]
     batch = B.Batch(hists, bw.col_of_hist, B.HIST_BATCH_GRAPH)
-    tune_c = batch.tune([c[:4_000_000] for c in cols], w[:4_000_000])
+    tune_c = batch.tune([c[:ns] for c in cols], w[:ns])
     for h in hists:
         h.reset()
     batch.fill(cols, w)
@@ -619,12 +622,12 @@ def profile_run(args) -> int:
             batch.fill([col], None)
     elif args.profile == "batched64":
         # the 64-histogram batch pinned to the partitioned strategy at a
-        # 100 KB budget (the tuner's choice on this workload)
+        # 48 KB budget (the tuner's choice on this workload)
         bw = W.cfg4(n=args.batch_events, device="cuda")
         cols = [bw.columns[c].contiguous() for c in range(3)]
         hists = [B.Hist([ax]) for ax in bw.axes]
         batch = B.Batch(hists, bw.col_of_hist)
-        batch.configure(2, 100 << 10)
+        batch.configure(2, 48 << 10)
         for _ in range(2):
             batch.fill(cols, bw.weights)
     else:  # "nd": the 2D fill of configuration 3a, then the 3D fill of 3b

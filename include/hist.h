@@ -266,10 +266,11 @@ int hist_kernel_time(hist_t *h, double *ms, int64_t *launches);
  * Histograms that share a column and range share their statistics sums.
  * Results and accuracy per histogram are those of hist_fill_bulk.
  * Precision: a batch whose members are all booked with HIST_PREC_FP32C
- * runs the FP32 compensated form (wide strategy only): small histograms
- * keep per-block FP32 (hi, lo) bins with TwoSum on the atomic's old value,
- * flushed in binary64; large ones take binary64 atomics.  Every other batch
- * keeps exact fixed-point bins (as HIST_PREC_FP64). */
+ * runs the FP32 compensated form (wide or partitioned strategy): bins in
+ * shared memory are FP32 (hi, lo) pairs with TwoSum on the atomic's old
+ * value, flushed in binary64 (wide: the small histograms, the large ones
+ * take binary64 atomics; partitioned: every histogram's slice of a range).
+ * Every other batch keeps exact fixed-point bins (as HIST_PREC_FP64). */
 typedef struct hist_batch hist_batch_t;
 
 #define HIST_BATCH_GRAPH (1u << 0)  /* replay the fill's launches as a cached CUDA graph */
@@ -313,9 +314,13 @@ typedef struct {
  * the wide strategy keep one word per shared bin, which a later weighted
  * fill widens again): time the candidate strategies, shared-memory budgets
  * (which histograms keep shared-memory bins; the slice size), blocks per SM,
- * events per thread and work caps per slice on the given sample of events, writing into scratch accumulators (the member histograms are not
- * changed), and keep the fastest for later fills.  Synchronous.  report may
- * be NULL.  Errors: as hist_batch_fill. */
+ * events per thread and work caps per slice on the given sample of events,
+ * writing into scratch accumulators (the member histograms are not
+ * changed), and keep the fastest for later fills.  The sample should be
+ * like the later fills in size too: the partitioned strategy stages each
+ * range's tables once per work item, a cost that small samples overweight
+ * (about 1e7 events per column suffice).  Synchronous.  report may be
+ * NULL.  Errors: as hist_batch_fill. */
 int hist_batch_tune(hist_batch_t *b, const double *const *cols, int ncols, const double *weights, int64_t n,
                     hist_batch_tuning_t *report);
 
@@ -329,9 +334,9 @@ int hist_batch_tune(hist_batch_t *b, const double *const *cols, int ncols, const
  * holds (2 or 4).  info (may be NULL) receives the resulting plan (with
  * best_ms = worst_ms = 0).  Waits for the batch's earlier fills.  Errors:
  * HIST_ERR_ARG, HIST_ERR_UNSUPPORTED (the plan does not fit one block's
- * shared memory; partitioned: more than 32 histograms on a column, more
- * than 2048 ranges on a column, or an FP32C batch; sliced: an FP32C
- * batch), HIST_ERR_OOM, HIST_ERR_CUDA. */
+ * shared memory; partitioned: more than 32 histograms on a column, or
+ * more than 2048 ranges on a column; sliced: an FP32C batch), HIST_ERR_OOM,
+ * HIST_ERR_CUDA. */
 int hist_batch_configure(hist_batch_t *b, int32_t strategy, int32_t smem_bytes, int32_t cost_cap_tenths,
                          int32_t pace_tiles, int32_t blocks_per_sm, int32_t events_per_thread,
                          hist_batch_tuning_t *info);

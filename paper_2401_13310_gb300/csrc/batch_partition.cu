@@ -127,13 +127,22 @@ __global__ void __launch_bounds__(kPartBlock) k_part_count(const __grid_constant
   const PartLocator L = split_locator(p, splits, sbc);
   const unsigned long long* xq = reinterpret_cast<const unsigned long long*>(p.col);
   constexpr int kPer = kPartTile / kPartBlock;
-  for (long long base = (long long)blockIdx.x * kPartTile; base < p.n; base += (long long)gridDim.x * kPartTile) {
-    // the tile's loads first (all in flight together), then the locates
-    unsigned long long x[kPer];
+  const long long gstep = (long long)gridDim.x * kPartTile;
+  // the tile's loads all in flight together, and the next tile's issued
+  // before this one is located
+  unsigned long long x[kPer];
+  long long base = (long long)blockIdx.x * kPartTile;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const long long i = base + threadIdx.x + (long long)k * kPartBlock;
+    x[k] = i < p.n ? __ldcs(xq + i) : 0ull;
+  }
+  for (; base < p.n; base += gstep) {
+    unsigned long long nx[kPer];
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
-      const long long i = base + threadIdx.x + (long long)k * kPartBlock;
-      x[k] = i < p.n ? __ldcs(xq + i) : 0ull;
+      const long long i = base + gstep + threadIdx.x + (long long)k * kPartBlock;
+      nx[k] = i < p.n ? __ldcs(xq + i) : 0ull;
     }
 #pragma unroll
     for (int k = 0; k < kPer; k += 2) {
@@ -143,6 +152,8 @@ __global__ void __launch_bounds__(kPartBlock) k_part_count(const __grid_constant
       if (i0 < p.n) atomicAdd(&cnt[r0], 1u);
       if (i1 < p.n) atomicAdd(&cnt[r1], 1u);
     }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) x[k] = nx[k];
   }
   __syncthreads();
   for (int r = threadIdx.x; r < p.nranges; r += blockDim.x) p.counts[(size_t)r * gridDim.x + blockIdx.x] = cnt[r];
@@ -291,16 +302,26 @@ __global__ void __launch_bounds__(kPartBlock) k_part_scatter(const __grid_consta
   unsigned long long* px = reinterpret_cast<unsigned long long*>(p.px);
   unsigned long long* pw = reinterpret_cast<unsigned long long*>(p.pw);
   constexpr int kPer = kPartTile / kPartBlock;
-  for (long long base = (long long)blockIdx.x * kPartTile; base < p.n; base += (long long)gridDim.x * kPartTile) {
-    unsigned long long x[kPer], w[kPer];
+  const long long gstep = (long long)gridDim.x * kPartTile;
+  // the tile's coordinates all in flight together, and the next tile's
+  // issued before this one is placed
+  unsigned long long x[kPer];
+  long long base = (long long)blockIdx.x * kPartTile;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const long long i = base + threadIdx.x + (long long)k * kPartBlock;
+    x[k] = i < p.n ? __ldcs(xq + i) : 0ull;
+  }
+  for (; base < p.n; base += gstep) {
+    unsigned long long w[kPer], nx[kPer];
     int r[kPer];
     unsigned rank[kPer];
-    // the tile's loads first (all in flight together), then the locates
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const long long i = base + threadIdx.x + (long long)k * kPartBlock;
-      x[k] = i < p.n ? __ldcs(xq + i) : 0ull;
       if (WEIGHTED) w[k] = i < p.n ? __ldcs(wq + i) : 0ull;
+      const long long in = i + gstep;
+      nx[k] = in < p.n ? __ldcs(xq + in) : 0ull;
     }
 #pragma unroll
     for (int k = 0; k < kPer; k += 2) {
@@ -338,6 +359,8 @@ __global__ void __launch_bounds__(kPartBlock) k_part_scatter(const __grid_consta
       next[rr] += tcnt[rr];
       tcnt[rr] = 0u;
     }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) x[k] = nx[k];
     __syncthreads();
   }
 }
@@ -347,13 +370,15 @@ __global__ void __launch_bounds__(kPartBlock) k_part_scatter(const __grid_consta
 // measured 1.5x slower on the 64-histogram workload); the rare change of
 // the top (a carry out of bit 63, or a negative addend's sign) goes to the
 // global high word in units of 2^32.
-__device__ __forceinline__ void part_fx_add(unsigned* a, long long* ghi, long long V) {
+// The low words of a range's bins are one array and the high words another
+// (lanes adding to consecutive slots touch consecutive banks).
+__device__ __forceinline__ void part_fx_add(unsigned* lo, unsigned* hi, long long* ghi, long long V) {
   const unsigned v0 = (unsigned)V;
-  const unsigned o0 = atomicAdd(a, v0);
+  const unsigned o0 = atomicAdd(lo, v0);
   const unsigned c0 = (o0 + v0 < o0) ? 1u : 0u;
   const unsigned a1 = (unsigned)((unsigned long long)V >> 32) + c0;
   const unsigned c1a = (a1 < c0) ? 1u : 0u;
-  const unsigned o1 = atomicAdd(a + 1, a1);
+  const unsigned o1 = atomicAdd(hi, a1);
   const unsigned c1 = c1a | ((o1 + a1 < o1) ? 1u : 0u);
   const int top = (int)(V >> 63) + (int)c1;
   if (top != 0) atomicAdd(reinterpret_cast<unsigned long long*>(ghi), (unsigned long long)((long long)top << 32));
@@ -362,15 +387,35 @@ __device__ __forceinline__ void part_fx_add(unsigned* a, long long* ghi, long lo
 // A member whose slice of a range has few bins would see most lanes of a
 // warp add to the same bin (the range's events all fall in those few bins),
 // and same-address shared atomics serialise.  Such a slice keeps 2^rsh
-// copies of every bin (up to 32 slots in all), lane l adding to copy
-// l mod 2^rsh; the count rows hold c << rsh for bin c, and each thread's
+// copies of every bin (as many as fit 32 slots, one bank each: 64 slots
+// measured 20 % slower on the 8-axis workload, two slots then sharing a
+// bank), lane l adding to copy l mod 2^rsh; the count rows hold c << rsh
+// for bin c, and each thread's
 // first slot is offset by its copy, so the add stays one add per member.
-template <bool UNIT, int ROW>
+// F32C: FP32 compensated bins (HIST_PREC_FP32C batches) -- the weight as
+// FP32 hi + lo; hi is added to the slot's sum word by an atomic whose
+// returned old value gives the addition's rounding error exactly (TwoSum);
+// that error plus lo (their sum's own rounding error recovered by TwoSum) is
+// added the same way to a compensation word, whose rounding errors go to a
+// third word.  Three planes: sums, compensations, second compensations.
+// A range's events can all fall in one bin of a coarse member, so a bin copy
+// may collect ~2^14 entries in one work item: with one compensation word
+// its own rounding (~m 2^-48 of the bin) would exceed 1e-11; the third word
+// leaves ~m^2 2^-72.
+// The rounding error of fl(a + b), exactly (Knuth's TwoSum).
+__device__ __forceinline__ float two_sum_err(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  return __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+
+template <bool UNIT, bool F32C, int ROW>
 struct PartFill {
   const PartParams& p;
   const unsigned short* cum;
   const PartSliceDev* sl;
-  unsigned* bins;
+  unsigned* bins;  // [nslots] counters; [nslots] low then high words; or three FP32 planes
+  int nslots;
   int boff[ROW];  // each member's first bin slot for this thread's copy (registers)
 
   // An event (weight wb) at merged position pos into every member's bin.
@@ -380,7 +425,14 @@ struct PartFill {
 #pragma unroll
     for (int k = 0; k < ROW / 8; ++k) q[k] = rp[k];
     long long V = 0;
-    const bool wok = UNIT ? true : fx_of(wb, p.fx_elo, &V);
+    FF W{0.0f, 0.0f};
+    bool wok = true;
+    if (F32C) {
+      wok = in_ff(exp_field(wb));
+      if (wok) W = ff_split(wb, hi24(wb));
+    } else if (!UNIT) {
+      wok = fx_of(wb, p.fx_elo, &V);
+    }
 #pragma unroll
     for (int h = 0; h < ROW; ++h) {
       if (h >= p.nh) break;
@@ -388,10 +440,18 @@ struct PartFill {
       const int j = (int)((h & 1) ? (w32 >> 16) : (w32 & 0xFFFFu));
       if (UNIT) {
         atomicAdd(&bins[boff[h] + j], 1u);
+      } else if (F32C && wok) {
+        float* f = reinterpret_cast<float*>(bins) + boff[h] + j;
+        const float e0 = two_sum_err(atomicAdd(f, W.hi), W.hi);
+        const float t = __fadd_rn(e0, W.lo);
+        const float d = two_sum_err(e0, W.lo);
+        const float e1 = two_sum_err(atomicAdd(f + nslots, t), t);
+        atomicAdd(f + 2 * nslots, __fadd_rn(e1, d));
       } else if (!wok) {
         atomicAdd(&p.hists[h].g_f64[sl[h].a + (j >> sl[h].rsh)], __longlong_as_double((long long)wb));
-      } else if (V != 0) {
-        part_fx_add(&bins[2 * (boff[h] + j)], &p.hists[h].g_hi[sl[h].a + (j >> sl[h].rsh)], V);
+      } else if (!F32C && V != 0) {
+        part_fx_add(&bins[boff[h] + j], &bins[nslots + boff[h] + j], &p.hists[h].g_hi[sl[h].a + (j >> sl[h].rsh)],
+                    V);
       }
     }
   }
@@ -408,7 +468,7 @@ __host__ __device__ constexpr int part_fill_block() {
   return 256;
 }
 
-template <bool UNIT, int ROW>
+template <bool UNIT, bool F32C, int ROW>
 __global__ void __launch_bounds__(part_fill_block<UNIT>(), UNIT ? 4 : 3) k_part_fill(const __grid_constant__ PartParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // [count rows][bucket counts][merged keys][slices][bins], each part
@@ -445,14 +505,14 @@ __global__ void __launch_bounds__(part_fill_block<UNIT>(), UNIT ? 4 : 3) k_part_
     }
     for (int j = threadIdx.x; j <= range.nbk && range.nbk > 0; j += blockDim.x) bcnt[j] = p.bcnt[range.bk_base + j];
     for (int h = threadIdx.x; h < p.nh; h += blockDim.x) sl[h] = p.slices[(size_t)item.r * p.nh + h];
-    const int nwords = (UNIT ? 1 : 2) * range.nbins;
+    const int nwords = (UNIT ? 1 : (F32C ? 3 : 2)) * range.nbins;
     for (int j = threadIdx.x; j < nwords; j += blockDim.x) bins[j] = 0u;
     __syncthreads();
 
     const PartLocator loc{keys,         bcnt,         range.lo_key, range.hi_key, range.kbase,
                           range.scale,  range.offset, range.nkeys,  range.nbk,    range.key_map,
                           range.shift,  range.top};
-    PartFill<UNIT, ROW> f{p, cum, sl, bins, {}};
+    PartFill<UNIT, F32C, ROW> f{p, cum, sl, bins, range.nbins, {}};
 #pragma unroll
     for (int h = 0; h < ROW; ++h)
       f.boff[h] = h < p.nh ? sl[h].boff + (int)(threadIdx.x & ((1u << sl[h].rsh) - 1u)) : 0;
@@ -514,11 +574,18 @@ __global__ void __launch_bounds__(part_fill_block<UNIT>(), UNIT ? 4 : 3) k_part_
           unsigned long long c = 0;
           for (int r = 0; r < nc; ++r) c += bins[b0 + r];
           if (c) atomicAdd(&d.g_unit[s.a + j], c);
+        } else if (F32C) {
+          const float* f = reinterpret_cast<const float*>(bins);
+          const int nb = range.nbins;
+          double v = 0.0;
+          for (int r = 0; r < nc; ++r)
+            v = __dadd_rn(v, __dadd_rn((double)f[b0 + r], __dadd_rn((double)f[nb + b0 + r], (double)f[2 * nb + b0 + r])));
+          if (v != 0.0) atomicAdd(&d.g_f64[s.a + j], v);
         } else {
           unsigned long long a0 = 0, a1 = 0;
           for (int r = 0; r < nc; ++r) {
-            a0 += bins[2 * (b0 + r)];
-            a1 += bins[2 * (b0 + r) + 1];
+            a0 += bins[b0 + r];
+            a1 += bins[range.nbins + b0 + r];
           }
           if (a0) atomicAdd(&d.g_lo[s.a + j], a0);
           if (a1) atomicAdd(reinterpret_cast<unsigned long long*>(&d.g_hi[s.a + j]), a1);
@@ -537,18 +604,22 @@ __global__ void __launch_bounds__(part_fill_block<UNIT>(), UNIT ? 4 : 3) k_part_
   block_stats_store(core, tail, sred, p.part_stats + (size_t)blockIdx.x * kStatSlots * 3);
 }
 
-template <bool UNIT>
+template <bool UNIT, bool F32C>
 const void* part_fill_row(int row) {
   switch (row) {
-    case 8: return reinterpret_cast<const void*>(&k_part_fill<UNIT, 8>);
-    case 16: return reinterpret_cast<const void*>(&k_part_fill<UNIT, 16>);
-    case 24: return reinterpret_cast<const void*>(&k_part_fill<UNIT, 24>);
-    default: return reinterpret_cast<const void*>(&k_part_fill<UNIT, 32>);
+    case 8: return reinterpret_cast<const void*>(&k_part_fill<UNIT, F32C, 8>);
+    case 16: return reinterpret_cast<const void*>(&k_part_fill<UNIT, F32C, 16>);
+    case 24: return reinterpret_cast<const void*>(&k_part_fill<UNIT, F32C, 24>);
+    default: return reinterpret_cast<const void*>(&k_part_fill<UNIT, F32C, 32>);
   }
 }
 
-// row: u16 per count row, 8, 16, 24 or 32
-const void* part_fill_fn(bool unit, int row) { return unit ? part_fill_row<true>(row) : part_fill_row<false>(row); }
+// row: u16 per count row, 8, 16, 24 or 32; f32c: FP32 compensated bins
+// (weighted fills of an FP32C batch; a unit-weight fill counts exactly)
+const void* part_fill_fn(bool unit, bool f32c, int row) {
+  if (unit) return part_fill_row<true, false>(row);
+  return f32c ? part_fill_row<false, true>(row) : part_fill_row<false, false>(row);
+}
 
 int part_fill_threads(bool unit) { return unit ? part_fill_block<true>() : part_fill_block<false>(); }
 
@@ -566,9 +637,9 @@ size_t part_scatter_smem(int nranges, int split_nbk, bool weighted) {
   return bx + (size_t)kPartTile * ((weighted ? 16 : 8) + 2);
 }
 
-size_t part_fill_smem(int max_keys, int max_bins, int nh, int row_u16, int max_nbk) {
+size_t part_fill_smem(int max_keys, int max_bins, int nh, int row_u16, int max_nbk, int slot_bytes) {
   return (((size_t)(max_keys + 1) * row_u16 * 2 + 15) & ~(size_t)15) + (((size_t)(max_nbk + 1) * 2 + 15) & ~(size_t)15) +
-         (size_t)max_keys * 8 + sizeof(PartSliceDev) * (size_t)nh + (size_t)max_bins * 8;
+         (size_t)max_keys * 8 + sizeof(PartSliceDev) * (size_t)nh + (size_t)max_bins * slot_bytes;
 }
 
 int part_grids(int sm_count, int nranges, int split_nbk, size_t fill_smem, int* count_grid, int* fill_per_sm) {
@@ -587,9 +658,9 @@ int part_grids(int sm_count, int nranges, int split_nbk, size_t fill_smem, int* 
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(&k_part_scatter<true>),
                                                     kPartBlock, ss) != cudaSuccess)
     return -2;
-  for (int v = 0; v < 8; ++v) {
-    const bool unit = v & 1;
-    const void* fn = part_fill_fn(unit, 8 * (1 + (v >> 1)));
+  for (int v = 0; v < 12; ++v) {
+    const bool unit = v % 3 == 0, f32c = v % 3 == 2;
+    const void* fn = part_fill_fn(unit, f32c, 8 * (1 + v / 3));
     int a = 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fn, part_fill_threads(unit), fill_smem) != cudaSuccess)
@@ -603,14 +674,14 @@ int part_grids(int sm_count, int nranges, int split_nbk, size_t fill_smem, int* 
   return 0;
 }
 
-int launch_part_fill(const PartParams& p, bool unit, int fill_grid, size_t fill_smem, void* stream) {
+int launch_part_fill(const PartParams& p, bool unit, bool f32c, int fill_grid, size_t fill_smem, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const size_t cs = part_count_smem(p.nranges, p.split_map.nbk);
   const size_t ss = part_scatter_smem(p.nranges, p.split_map.nbk, !unit);
   const void* scatter = unit ? reinterpret_cast<const void*>(&k_part_scatter<false>)
                              : reinterpret_cast<const void*>(&k_part_scatter<true>);
   // (the attributes are per kernel: another batch may have set others)
-  const void* fill = part_fill_fn(unit, p.row_u16);
+  const void* fill = part_fill_fn(unit, f32c, p.row_u16);
   if (cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_part_count), cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)cs) != cudaSuccess ||
       cudaFuncSetAttribute(scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss) != cudaSuccess ||

@@ -1683,6 +1683,7 @@ int batch_configure(hist_batch* b, int budget) {
 
 // ---- partitioned strategy: planning (see batch_partition.cu) ----
 constexpr int kPartChunkMax = 1 << 19;  // events per fill work item at most
+constexpr int kPartCopySlots = 32;      // bin slots a slice may take with its copies (one bank each)
 constexpr int kPartChunkMin = 1 << 14;  // ... and at least (below: the staging dominates)
 constexpr int kPartWaves = 6;           // work items aimed at per resident fill block
 
@@ -1727,18 +1728,26 @@ int part_bucket_map(const std::vector<long long>& keys, PartRangeDev* R, std::ve
 // are sorted together; a range takes thresholds until the next would pass
 // its capacity C, and the next range starts at that threshold (a range's
 // first threshold is a slice boundary, not one of its interior thresholds).
-// A range costs, per interior threshold, one bin of 8 bytes, one merged key
+// A range costs, per interior threshold, one bin slot of 8 bytes (12 in an
+// FP32C batch: three FP32 words), one merged key
 // of 8 bytes, one count row of 2 row bytes and at most two bucket counts of
 // 2 bytes, plus per member 16 bytes of descriptor, one more bin and up to
-// 31 bin copies (a slice of at most 16 bins keeps 2^rsh <= 32 / len copies
-// of each bin, so that a warp's adds spread over the banks).  Each
+// copy_slots - 1 bin copies (a slice keeps 2^rsh <= 32 copies of each bin,
+// as many as fit copy_slots slots, so that a warp's adds spread over the
+// banks; copy_slots is kPartCopySlots, halved while the copies would take
+// more than half the budget).  Each
 // range gets the axes' bucket map (build_bucket_map) over its merged
 // thresholds, with a power of two >= M buckets.  On success the plan's
 // tables are on the device.
 int part_plan_column(const hist_batch* b, int col, int h0, int nh, int budget, int limit, PartPlan* out) {
   if (nh < 1 || nh > kPartMaxMembers) return HIST_ERR_UNSUPPORTED;
   const int row = 8 * ((nh + 7) / 8);
-  const long long C = ((long long)budget - 280LL * nh - 2LL * row - 48) / (20 + 2 * row);
+  // bin copies may take up to half the budget
+  const int slot_bytes = b->f32c ? 12 : 8;  // FP32C: three FP32 words per slot
+  int copy_slots = kPartCopySlots;
+  while (copy_slots > 1 && (16LL + (long long)slot_bytes * (copy_slots + 1)) * nh > budget / 2) copy_slots /= 2;
+  const long long C = ((long long)budget - (16LL + (long long)slot_bytes * (copy_slots + 1)) * nh - 2LL * row - 48) /
+                      (12 + slot_bytes + 2 * row);
   if (C < 16) return HIST_ERR_UNSUPPORTED;
   std::vector<long long> all;
   for (int h = h0; h < h0 + nh; ++h) {
@@ -1785,7 +1794,7 @@ int part_plan_column(const hist_batch* b, int col, int h0, int nh, int budget, i
       S.len = e[h] - a[h] + 1;
       S.boff = nb;
       S.rsh = 0;
-      while (S.len << (S.rsh + 1) <= 32) ++S.rsh;
+      while (S.rsh < 5 && (S.len << (S.rsh + 1)) <= copy_slots) ++S.rsh;
       nb += S.len << S.rsh;
       for (int k = a[h] + 1; k <= e[h]; ++k) merged.push_back(T[(size_t)k]);
     }
@@ -1823,7 +1832,7 @@ int part_plan_column(const hist_batch* b, int col, int h0, int nh, int budget, i
       cum.size() > (size_t)std::numeric_limits<int32_t>::max() ||
       bcnt.size() > (size_t)std::numeric_limits<int32_t>::max())
     return HIST_ERR_UNSUPPORTED;
-  const size_t fill_smem = part_fill_smem(max_keys, max_bins, nh, row, max_nbk);
+  const size_t fill_smem = part_fill_smem(max_keys, max_bins, nh, row, max_nbk, slot_bytes);
   if (fill_smem > (size_t)limit) return HIST_ERR_UNSUPPORTED;
   PartPlan q;
   q.col = col;
@@ -1870,10 +1879,9 @@ int part_plan_column(const hist_batch* b, int col, int h0, int nh, int budget, i
   return HIST_OK;
 }
 
-// The partitioned strategy: one plan per column (exact precision only; every
-// column at most kPartMaxMembers members).
+// The partitioned strategy: one plan per column (every column at most
+// kPartMaxMembers members); exact or FP32 compensated bins.
 int part_configure(hist_batch* b, int budget) {
-  if (b->f32c) return HIST_ERR_UNSUPPORTED;
   int maxopt = 0;
   if (cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess)
     return HIST_ERR_CUDA;
@@ -2077,7 +2085,7 @@ int batch_launch(const hist_batch* b, const double* const* cols, const double* w
       if (q.items != part_items(q, b->sm_count, n) || q.items > b->items_cap ||
           (size_t)q.nranges * q.count_grid > b->counts_cap || q.block_base + q.items > b->part_blocks)
         return HIST_ERR_CUDA;  // batch_reserve sized the scratch for these events
-      if (launch_part_fill(p, weights == nullptr, q.items, q.smem, s) != 0) return HIST_ERR_CUDA;
+      if (launch_part_fill(p, weights == nullptr, b->f32c, q.items, q.smem, s) != 0) return HIST_ERR_CUDA;
     }
   } else if (b->strategy == 1) {
     SliceParams p;
@@ -2411,7 +2419,7 @@ extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int n
   if (!(b->flags & HIST_BATCH_WIDE))
     for (int kb : {96, 200})
       for (double cap : {3.0, 12.0}) cands.push_back({1, kb * 1024, cap, 2, 4});
-  if (!(b->flags & (HIST_BATCH_WIDE | HIST_BATCH_SLICED)) && !b->f32c)
+  if (!(b->flags & (HIST_BATCH_WIDE | HIST_BATCH_SLICED)))
     for (int kb : {48, 100, 200}) cands.push_back({2, kb * 1024, 0.0, 2, 4});
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HIST_ERR_CUDA;

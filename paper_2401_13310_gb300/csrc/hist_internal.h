@@ -358,9 +358,9 @@ struct PartParams {
 };
 size_t part_count_smem(int nranges, int split_nbk);
 size_t part_scatter_smem(int nranges, int split_nbk, bool weighted);
-size_t part_fill_smem(int max_keys, int max_bins, int nh, int row_u16, int max_nbk);
+size_t part_fill_smem(int max_keys, int max_bins, int nh, int row_u16, int max_nbk, int slot_bytes);
 int part_grids(int sm_count, int nranges, int split_nbk, size_t fill_smem, int* count_grid, int* fill_per_sm);
-int launch_part_fill(const PartParams& p, bool unit, int fill_grid, size_t fill_smem, void* stream);
+int launch_part_fill(const PartParams& p, bool unit, bool f32c, int fill_grid, size_t fill_smem, void* stream);
 
 int launch_slice_fill(const SliceParams& p, int block, int grid, size_t smem, void* stream);
 int slice_max_blocks_per_sm(int block, size_t smem, int* per_sm);

@@ -270,14 +270,16 @@ def test_batch_tuned_for_unit_then_weighted_fill(B):
             h.close()
 
 
+@pytest.mark.parametrize("plan", ["tuned", "wide", "partitioned"])
 @pytest.mark.parametrize("odd", [False, True])
-def test_batch_fp32c_matches_oracle(B, odd):
+def test_batch_fp32c_matches_oracle(B, odd, plan):
     """A batch whose members are all booked HIST_PREC_FP32C runs the FP32
-    compensated form (per-block FP32 hi/lo bins with TwoSum on the atomic's
-    old value, binary64 atomics for the large members): bins and statistics
-    within 1e-12 of the oracle's sum of |terms|, after tuning (the wide
-    strategy only).  With odd weights (zero, negative, tiny, huge) the
-    events outside the double-word range take the binary64 path."""
+    compensated form (shared FP32 hi/lo bins with TwoSum on the atomic's old
+    value; in the wide strategy binary64 atomics for the large members):
+    bins and statistics within 1e-12 of the oracle's sum of |terms|, after
+    tuning and with the wide and partitioned strategies pinned.  With odd
+    weights (zero, negative, tiny, huge) the events outside the double-word
+    range take the binary64 path."""
     bw = W.cfg4(n=200_003)
     w = np.array(bw.weights, copy=True)
     if odd:
@@ -294,8 +296,12 @@ def test_batch_fp32c_matches_oracle(B, odd):
         assert e.value.code == B.HIST_ERR_UNSUPPORTED
         batch = B.Batch(hists, bw.col_of_hist, B.HIST_BATCH_GRAPH)
         cols = [to_device(np.ascontiguousarray(bw.columns[c])) for c in range(3)]
-        rep = batch.tune(cols, to_device(w))
-        assert rep["strategy"] == 0
+        if plan == "tuned":
+            assert batch.tune(cols, to_device(w))["strategy"] in (0, 2)
+        elif plan == "wide":
+            assert batch.configure(0, 48 << 10, 30, -1, 2, 4)["strategy"] == 0
+        else:
+            assert batch.configure(2, 48 << 10, 30, -1, 2, 4)["strategy"] == 2
         batch.fill(cols, to_device(w))
         worst = 0.0
         for i, (h, ax, c) in enumerate(zip(hists, bw.axes, bw.col_of_hist)):

@@ -85,7 +85,8 @@ def test_cfg4_full_size_plain_and_batched(B, cfg4_ref):
     # batched: tuned, then each strategy pinned; the FP32 compensated batch
     plans = [("tuned", None, 0), ("wide", (0, 48 << 10, 30, -1, 2, 2), 0),
              ("sliced", (1, 200 << 10, 30, -1, 2, 4), 0), ("partitioned", (2, 100 << 10, 30, -1, 2, 4), 0),
-             ("fp32c tuned", None, B.HIST_PREC_FP32C)]
+             ("fp32c tuned", None, B.HIST_PREC_FP32C),
+             ("fp32c partitioned", (2, 48 << 10, 30, -1, 2, 4), B.HIST_PREC_FP32C)]
     for name, cfg, prec in plans:
         hists = [B.Hist([ax], prec) for ax in bw.axes]
         batch = None
