@@ -52,8 +52,8 @@ WORKLOAD = ("1d_weighted_1e8x2: (a) 1000 fixed bins [-5,5) x~N(0,1); "
 # DRAM bytes per event that ncu counted for the fill kernel of each fill
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 2e7
 # events), valid for the kernel sources with this digest only.
-TRAFFIC = {"digest": "b0265727d10e4ea2", "a_fixed1000": (320069632 + 6245632) / 2e7,
-           "b_var500": (320093184 + 4602880) / 2e7}
+TRAFFIC = {"digest": "42d3670f6cc04d27", "a_fixed1000": (320065536 + 6033152) / 2e7,
+           "b_var500": (320093952 + 4691968) / 2e7}
 KERNEL_SOURCES = ["fill_kernels.cu", "fill_device.cuh", "device_common.cuh", "learned_eval.cuh"]
 
 
@@ -630,6 +630,17 @@ def profile_run(args) -> int:
         batch.configure(2, 48 << 10)
         for _ in range(2):
             batch.fill(cols, bw.weights)
+    elif args.profile == "histo1d":
+        # the paper's Histo1D shape on the device: 1000 fixed bins on [0,1],
+        # values uniform on [0,1], unit weights, three fills
+        g = torch.Generator(device="cuda")
+        g.manual_seed(21)
+        x = torch.rand(args.events, dtype=torch.float64, device="cuda", generator=g)
+        h = B.Hist([W.fixed(1000, 0.0, 1.0)])
+        for _ in range(3):
+            h.fill(x)
+        torch.cuda.synchronize()
+        h.close()
     else:  # "nd": the 2D fill of configuration 3a, then the 3D fill of 3b
         for cfg in (W.cfg3a, W.cfg3b):
             wl = cfg(n=args.events, device="cuda")
@@ -660,7 +671,7 @@ def main():
     ap.add_argument("--bulk", type=int, default=1 << 24)
     ap.add_argument("--batch-events", type=int, default=50_000_000)
     ap.add_argument("--learned-events", type=int, default=1_000_000_000)
-    ap.add_argument("--profile", choices=["partitioned8", "batched64", "nd"], default=None,
+    ap.add_argument("--profile", choices=["partitioned8", "batched64", "nd", "histo1d"], default=None,
                     help="run a short launch sequence of one form for a profiler, then exit")
     args = ap.parse_args()
     if args.profile is not None:
