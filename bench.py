@@ -630,6 +630,19 @@ def profile_run(args) -> int:
         batch.configure(2, 48 << 10)
         for _ in range(2):
             batch.fill(cols, bw.weights)
+    elif args.profile == "locators1e6":
+        # the largest mixture-quantile axis (1e6 edges): a plain fill through
+        # its bucket map, then a plain fill through the trained learned locator
+        lw = W.cfg5(n=args.learned_events, device="cuda")
+        col = lw.columns[0].contiguous()
+        ax = lw.axes[-1]
+        hb = B.Hist([ax])
+        hl = B.Hist([ax], B.HIST_LOCATOR_LEARNED)
+        hl.train_locator(0)
+        for h in (hb, hl):
+            h.fill(col)
+            torch.cuda.synchronize()
+            h.close()
     elif args.profile == "histo1d":
         # the paper's Histo1D shape on the device: 1000 fixed bins on [0,1],
         # values uniform on [0,1], unit weights, three fills
@@ -671,7 +684,7 @@ def main():
     ap.add_argument("--bulk", type=int, default=1 << 24)
     ap.add_argument("--batch-events", type=int, default=50_000_000)
     ap.add_argument("--learned-events", type=int, default=1_000_000_000)
-    ap.add_argument("--profile", choices=["partitioned8", "batched64", "nd", "histo1d"], default=None,
+    ap.add_argument("--profile", choices=["partitioned8", "batched64", "nd", "histo1d", "locators1e6"], default=None,
                     help="run a short launch sequence of one form for a profiler, then exit")
     args = ap.parse_args()
     if args.profile is not None:
