@@ -468,8 +468,13 @@ __host__ __device__ constexpr int part_fill_block() {
   return 256;
 }
 
-template <bool UNIT, bool F32C, int ROW>
-__global__ void __launch_bounds__(part_fill_block<UNIT>(), UNIT ? 4 : 3) k_part_fill(const __grid_constant__ PartParams p) {
+// EV: events a thread takes at a time, 2 or 4.  Four (unit weights only,
+// two blocks per SM, up to 128 registers) serve the ranges whose tables
+// already hold the fill to two blocks per SM: the dependent shared-memory
+// lookups of four events are in flight together.
+template <bool UNIT, bool F32C, int ROW, int EV = 2>
+__global__ void __launch_bounds__(part_fill_block<UNIT>(), EV == 4 ? 2 : (UNIT ? 4 : 3))
+    k_part_fill(const __grid_constant__ PartParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // [count rows][bucket counts][merged keys][slices][bins], each part
   // 16-byte aligned
@@ -519,8 +524,40 @@ __global__ void __launch_bounds__(part_fill_block<UNIT>(), UNIT ? 4 : 3) k_part_
     const unsigned long long* xq = reinterpret_cast<const unsigned long long*>(p.px);
     const unsigned long long* wq = reinterpret_cast<const unsigned long long*>(p.pw);
     const long long e1 = item.e1;
-    const long long step = 2 * (long long)blockDim.x;
     constexpr unsigned long long kOne = 0x3FF0000000000000ull;
+    if constexpr (EV == 4) {
+      // events e, e + B, e + 2B, e + 3B (B threads), the next four loaded
+      // before the current ones are processed; unit weights
+      const long long B = blockDim.x;
+      long long e = item.e0 + threadIdx.x;
+      unsigned long long x[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (e + i * B < e1) x[i] = __ldcs(xq + e + i * B);
+      for (; e < e1; e += 4 * B) {
+        const long long en = e + 4 * B;
+        unsigned long long nx[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (en + i * B < e1) nx[i] = __ldcs(xq + en + i * B);
+        long long k[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) k[i] = key_of(x[i]);
+        int j[4];
+        loc.locate2(k[0], x[0], k[1], x[1], j[0], j[1]);
+        loc.locate2(k[2], x[2], k[3], x[3], j[2], j[3]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (e + i * B < e1) {
+            f.add(j[i], kOne);
+            stat_event<UNIT>(p.st, p.stat_col, k[i], x[i], kOne, core1, tail);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = nx[i];
+      }
+    } else {
+    const long long step = 2 * (long long)blockDim.x;
     // two events per thread at a time (e and e + blockDim.x); the next two
     // are loaded before the current ones are processed
     long long e = item.e0 + threadIdx.x;
@@ -560,6 +597,7 @@ __global__ void __launch_bounds__(part_fill_block<UNIT>(), UNIT ? 4 : 3) k_part_
       x1 = nx1;
       w0 = nw0;
       w1 = nw1;
+    }
     }
     __syncthreads();
     // the range's bins into the members' exact global accumulators
@@ -604,20 +642,32 @@ __global__ void __launch_bounds__(part_fill_block<UNIT>(), UNIT ? 4 : 3) k_part_
   block_stats_store(core, tail, sred, p.part_stats + (size_t)blockIdx.x * kStatSlots * 3);
 }
 
-template <bool UNIT, bool F32C>
+template <bool UNIT, bool F32C, int EV = 2>
 const void* part_fill_row(int row) {
   switch (row) {
-    case 8: return reinterpret_cast<const void*>(&k_part_fill<UNIT, F32C, 8>);
-    case 16: return reinterpret_cast<const void*>(&k_part_fill<UNIT, F32C, 16>);
-    case 24: return reinterpret_cast<const void*>(&k_part_fill<UNIT, F32C, 24>);
-    default: return reinterpret_cast<const void*>(&k_part_fill<UNIT, F32C, 32>);
+    case 8: return reinterpret_cast<const void*>(&k_part_fill<UNIT, F32C, 8, EV>);
+    case 16: return reinterpret_cast<const void*>(&k_part_fill<UNIT, F32C, 16, EV>);
+    case 24: return reinterpret_cast<const void*>(&k_part_fill<UNIT, F32C, 24, EV>);
+    default: return reinterpret_cast<const void*>(&k_part_fill<UNIT, F32C, 32, EV>);
   }
 }
 
 // row: u16 per count row, 8, 16, 24 or 32; f32c: FP32 compensated bins
-// (weighted fills of an FP32C batch; a unit-weight fill counts exactly)
-const void* part_fill_fn(bool unit, bool f32c, int row) {
-  if (unit) return part_fill_row<true, false>(row);
+// (weighted fills of an FP32C batch; a unit-weight fill counts exactly).
+// A unit-weight fill whose shared tables allow at most two blocks per SM
+// takes the four-events-at-a-time kernel.
+const void* part_fill_fn(bool unit, bool f32c, int row, size_t fill_smem) {
+  if (unit) {
+    const void* two = part_fill_row<true, false>(row);
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(two, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, two, part_fill_block<true>(), fill_smem) ==
+            cudaSuccess &&
+        per_sm >= 1 && per_sm <= 2)
+      return part_fill_row<true, false, 4>(row);
+    cudaGetLastError();
+    return two;
+  }
   return f32c ? part_fill_row<false, true>(row) : part_fill_row<false, false>(row);
 }
 
@@ -660,7 +710,7 @@ int part_grids(int sm_count, int nranges, int split_nbk, size_t fill_smem, int* 
     return -2;
   for (int v = 0; v < 12; ++v) {
     const bool unit = v % 3 == 0, f32c = v % 3 == 2;
-    const void* fn = part_fill_fn(unit, f32c, 8 * (1 + v / 3));
+    const void* fn = part_fill_fn(unit, f32c, 8 * (1 + v / 3), fill_smem);
     int a = 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fn, part_fill_threads(unit), fill_smem) != cudaSuccess)
@@ -681,7 +731,7 @@ int launch_part_fill(const PartParams& p, bool unit, bool f32c, int fill_grid, s
   const void* scatter = unit ? reinterpret_cast<const void*>(&k_part_scatter<false>)
                              : reinterpret_cast<const void*>(&k_part_scatter<true>);
   // (the attributes are per kernel: another batch may have set others)
-  const void* fill = part_fill_fn(unit, f32c, p.row_u16);
+  const void* fill = part_fill_fn(unit, f32c, p.row_u16, fill_smem);
   if (cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_part_count), cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)cs) != cudaSuccess ||
       cudaFuncSetAttribute(scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss) != cudaSuccess ||
