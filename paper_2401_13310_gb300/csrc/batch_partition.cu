@@ -468,10 +468,10 @@ __host__ __device__ constexpr int part_fill_block() {
   return 256;
 }
 
-// EV: events a thread takes at a time, 2 or 4.  Four (unit weights only,
-// two blocks per SM, up to 128 registers) serve the ranges whose tables
-// already hold the fill to two blocks per SM: the dependent shared-memory
-// lookups of four events are in flight together.
+// EV: events a thread takes at a time, 2 or 4.  Four (unit weights or exact
+// fixed point, two blocks per SM, up to 128 registers) serve the ranges
+// whose tables already hold the fill to two blocks per SM: the dependent
+// shared-memory lookups of four events are in flight together.
 template <bool UNIT, bool F32C, int ROW, int EV = 2>
 __global__ void __launch_bounds__(part_fill_block<UNIT>(), EV == 4 ? 2 : (UNIT ? 4 : 3))
     k_part_fill(const __grid_constant__ PartParams p) {
@@ -527,19 +527,25 @@ __global__ void __launch_bounds__(part_fill_block<UNIT>(), EV == 4 ? 2 : (UNIT ?
     constexpr unsigned long long kOne = 0x3FF0000000000000ull;
     if constexpr (EV == 4) {
       // events e, e + B, e + 2B, e + 3B (B threads), the next four loaded
-      // before the current ones are processed; unit weights
+      // before the current ones are processed
       const long long B = blockDim.x;
       long long e = item.e0 + threadIdx.x;
-      unsigned long long x[4] = {0, 0, 0, 0};
+      unsigned long long x[4] = {0, 0, 0, 0}, w[4] = {kOne, kOne, kOne, kOne};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        if (e + i * B < e1) x[i] = __ldcs(xq + e + i * B);
+        if (e + i * B < e1) {
+          x[i] = __ldcs(xq + e + i * B);
+          if (!UNIT) w[i] = __ldcs(wq + e + i * B);
+        }
       for (; e < e1; e += 4 * B) {
         const long long en = e + 4 * B;
-        unsigned long long nx[4] = {0, 0, 0, 0};
+        unsigned long long nx[4] = {0, 0, 0, 0}, nw[4] = {kOne, kOne, kOne, kOne};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-          if (en + i * B < e1) nx[i] = __ldcs(xq + en + i * B);
+          if (en + i * B < e1) {
+            nx[i] = __ldcs(xq + en + i * B);
+            if (!UNIT) nw[i] = __ldcs(wq + en + i * B);
+          }
         long long k[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) k[i] = key_of(x[i]);
@@ -549,12 +555,15 @@ __global__ void __launch_bounds__(part_fill_block<UNIT>(), EV == 4 ? 2 : (UNIT ?
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           if (e + i * B < e1) {
-            f.add(j[i], kOne);
-            stat_event<UNIT>(p.st, p.stat_col, k[i], x[i], kOne, core1, tail);
+            f.add(j[i], w[i]);
+            stat_event<UNIT>(p.st, p.stat_col, k[i], x[i], w[i], core1, tail);
           }
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) x[i] = nx[i];
+        for (int i = 0; i < 4; ++i) {
+          x[i] = nx[i];
+          w[i] = nw[i];
+        }
       }
     } else {
     const long long step = 2 * (long long)blockDim.x;
@@ -654,21 +663,18 @@ const void* part_fill_row(int row) {
 
 // row: u16 per count row, 8, 16, 24 or 32; f32c: FP32 compensated bins
 // (weighted fills of an FP32C batch; a unit-weight fill counts exactly).
-// A unit-weight fill whose shared tables allow at most two blocks per SM
-// takes the four-events-at-a-time kernel.
+// A fill (unit weights or exact fixed point) whose shared tables allow at
+// most two blocks per SM takes the four-events-at-a-time kernel.
 const void* part_fill_fn(bool unit, bool f32c, int row, size_t fill_smem) {
-  if (unit) {
-    const void* two = part_fill_row<true, false>(row);
-    int per_sm = 0;
-    if (cudaFuncSetAttribute(two, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, two, part_fill_block<true>(), fill_smem) ==
-            cudaSuccess &&
-        per_sm >= 1 && per_sm <= 2)
-      return part_fill_row<true, false, 4>(row);
-    cudaGetLastError();
-    return two;
-  }
-  return f32c ? part_fill_row<false, true>(row) : part_fill_row<false, false>(row);
+  if (f32c && !unit) return part_fill_row<false, true>(row);
+  const void* two = unit ? part_fill_row<true, false>(row) : part_fill_row<false, false>(row);
+  int per_sm = 0;
+  if (cudaFuncSetAttribute(two, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem) == cudaSuccess &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, two, part_fill_block<true>(), fill_smem) == cudaSuccess &&
+      per_sm >= 1 && per_sm <= 2)
+    return unit ? part_fill_row<true, false, 4>(row) : part_fill_row<false, false, 4>(row);
+  cudaGetLastError();
+  return two;
 }
 
 int part_fill_threads(bool unit) { return unit ? part_fill_block<true>() : part_fill_block<false>(); }
