@@ -376,15 +376,19 @@ def test_batch_partitioned_matches_oracle(B, weighted, budget):
             h.close()
 
 
+@pytest.mark.parametrize("budget", [8 << 10, 100 << 10])
 @pytest.mark.parametrize("ncols", [1, 2])
 @pytest.mark.parametrize("weighted", [False, True])
-def test_batch_partitioned_edges_specials_and_accumulate(B, weighted, ncols):
+def test_batch_partitioned_edges_specials_and_accumulate(B, weighted, ncols, budget):
     """Every threshold of every member and its neighbouring doubles (so
     every range boundary and slice boundary), signed zeros, infinities,
     NaN, subnormals; odd weights; two fills accumulate like one of the
     concatenation (graph replay).  With two columns the members alternate
     between the probe points and the same points reversed: each column is
-    partitioned and filled on its own, its statistics in its own slots."""
+    partitioned and filled on its own, its statistics in its own slots.
+    The small budget makes many small ranges (fills of two events per
+    thread at a time); the large one ranges whose tables hold the fill to
+    two blocks per SM (the kernel with four events per thread in flight)."""
     rng = np.random.default_rng(72)
     bw = _one_column_batch(10, 73)
     pts = np.concatenate([edge_probe_values(ax, B.hist_axis_thresholds(ax), rng, nrand=300) for ax in bw.axes])
@@ -401,8 +405,10 @@ def test_batch_partitioned_edges_specials_and_accumulate(B, weighted, ncols):
     batch = None
     try:
         batch = B.Batch(hists, col_of_hist, B.HIST_BATCH_GRAPH)
-        info = batch.configure(2, 8 << 10)
+        info = batch.configure(2, budget)
         assert info["strategy"] == 2
+        if budget > (64 << 10):
+            assert info["blocks_per_sm"] <= 2, info
         cols = [to_device(c) for c in columns]
         wd = to_device(w)
         batch.fill(cols, wd)
