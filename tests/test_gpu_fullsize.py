@@ -168,3 +168,33 @@ def test_cfg5_full_size_locators(B, cfg5_ref, locator):
             batch.close()
         for h in hists:
             h.close()
+
+
+def test_fill_beyond_2_31_events(B):
+    """One plain fill of more than 2^31 events (an odd count): the fill's
+    64-bit event indices, its per-thread pair counts and its odd last event
+    past 2^31.  Unit weights on 100 fixed bins with flows; counts bit-exact
+    against the chunk-parallel oracle, the entry count equal to n."""
+    import torch
+    phys = os.sysconf("SC_PHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    n = (1 << 31) + (1 << 20) + 3
+    if phys < 8 * n * 3:
+        pytest.skip("host memory too small for the oracle's copy of the column")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(17)
+    x = torch.rand(n, dtype=torch.float64, device="cuda", generator=g)
+    x.mul_(1.2).sub_(0.1)
+    ax = W.fixed(100, 0.0, 1.0)
+    h = B.Hist([ax])
+    try:
+        h.fill(x)
+        bins, stats = h.result()
+    finally:
+        h.close()
+    xh = x.cpu().numpy()
+    del x
+    torch.cuda.empty_cache()
+    ref = oracle.fill([ax], xh.reshape(1, -1), threads=_threads())
+    assert stats[0] == n
+    assert np.array_equal(bins, ref.counts.astype(np.float64)), "counts differ beyond 2^31 events"
+    assert_sums_close(stats[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, "stats beyond 2^31 events")

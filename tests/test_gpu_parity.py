@@ -364,3 +364,50 @@ def test_count_and_plain_kernel_variants_agree(B, name, specials):
     ref = oracle.fill(wl.axes, x, w, threads=4)
     check_against_oracle(wl.axes, x, w, *plain, ref, RTOL, RTOL, what=f"no counts cfg{name}")
     check_against_oracle(wl.axes, x, w, *counted, ref, RTOL, RTOL, what=f"counts cfg{name}")
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+@pytest.mark.parametrize("axis", [W.fixed(1000, -5.0, 5.0), W.variable(W.log_edges(500, 0.0, 3.0))],
+                         ids=["fixed1000", "log500"])
+def test_empty_and_tiny_fills(B, axis, weighted):
+    """Fills of 0 events change nothing, through every fill entry point
+    (device bulk, host pipeline, Filter/Define, batch); fills of 1, 2, 3
+    and 5 events (fewer than one thread's pair, an odd last event, flows
+    and NaN among them) then accumulate exactly as the oracle's fill of
+    the same events in the same order."""
+    import torch
+    rng = np.random.default_rng(31)
+    xs = np.array([-7.0, 0.5, 3.0, math.nan, 1200.0, 0.999, 25.0, -0.0, 1.0, 999.9, 12.5])
+    ws = rng.uniform(0.5, 1.5, xs.size) if weighted else None
+    h = B.Hist([axis])
+    hb = B.Hist([axis])
+    batch = None
+    try:
+        empty = torch.empty(0, dtype=torch.float64, device="cuda")
+        h.fill(empty, empty if weighted else None)
+        h.fill_host(torch.empty(0, dtype=torch.float64), torch.empty(0, dtype=torch.float64) if weighted else None)
+        h.fill_columns([empty], [(B.HIST_DEF_COL, 0, 0)], [], empty if weighted else None)
+        batch = B.Batch([hb], [0])
+        batch.fill([empty], empty if weighted else None)
+        torch.cuda.synchronize()
+        for hh in (h, hb):
+            bins, stats = hh.result()
+            assert not np.any(bins) and not np.any(stats), "an empty fill changed the histogram"
+        done = 0
+        for m in (1, 2, 3, 5):
+            xd = to_device(xs[done:done + m].copy())
+            wd = None if ws is None else to_device(ws[done:done + m].copy())
+            h.fill(xd, wd)
+            batch.fill([xd], wd)
+            done += m
+        torch.cuda.synchronize()
+        ref = oracle.fill([axis], xs[:done].reshape(1, -1), None if ws is None else ws[:done])
+        for what, hh in (("bulk", h), ("batch", hb)):
+            bins, stats = hh.result()
+            check_against_oracle([axis], xs[:done], None if ws is None else ws[:done], bins, stats, None, ref,
+                                 what=f"tiny fills ({what})")
+    finally:
+        if batch is not None:
+            batch.close()
+        h.close()
+        hb.close()
