@@ -484,8 +484,14 @@ __device__ __forceinline__ void fill_expr(Filler<NDIM, ACC, SMEM, LOC, SW2>& f) 
   if ((threadIdx.x & 31) == 0 && passed) atomicAdd(ex.g_passed, passed);
 }
 
-template <int NDIM, int ACC, bool SMEM, int LOC, bool SW2, bool EXPR>
+// DIRECT: the block adds its bins to the persistent accumulators itself and
+// the last block sums the statistics partials (small 1D fills: no partial
+// bins and no reduce launch); compiled apart so that the other fills keep
+// none of its code.
+template <int NDIM, int ACC, bool SMEM, int LOC, bool SW2, bool EXPR, bool DIRECT = false>
 __global__ void __launch_bounds__(256, NDIM == 1 ? HGB_MIN_BLOCKS_1D : HGB_MIN_BLOCKS) k_fill(const FillParams p) {
+  static_assert(!DIRECT || (NDIM == 1 && SMEM && (ACC == ACC_UNIT || ACC == ACC_FX) && !SW2 && !EXPR),
+                "direct flush: 1D exact or unit-count shared bins");
   constexpr bool UNIT = (ACC == ACC_UNIT);
   constexpr int NS = NStats<NDIM>::NS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -552,7 +558,26 @@ __global__ void __launch_bounds__(256, NDIM == 1 ? HGB_MIN_BLOCKS_1D : HGB_MIN_B
   for (int k = 2; k < NS; ++k) f.st.d[k] = __dadd_rn(f.st.d[k], slow[k]);
 
   __syncthreads();
-  if (SMEM) {
+  if constexpr (DIRECT) {
+    // the block's exact words straight into the persistent accumulators
+    // (integer sums: the order of the blocks does not matter)
+    if (UNIT) {
+      for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const unsigned c = f.sbins[i];
+        if (c) atomicAdd(&p.g_unit[i], (unsigned long long)c);
+      }
+    } else {
+      for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const unsigned lo = f.sbins[2 * i], hi = f.sbins[2 * i + 1];
+        if (lo) atomicAdd(&p.g_lo[i], (unsigned long long)lo);
+        if (hi) atomicAdd(reinterpret_cast<unsigned long long*>(&p.g_hi[i]), (unsigned long long)hi);
+        if (p.track_counts) {
+          const unsigned c = f.sbins[2 * nb + i];
+          if (c) atomicAdd(&p.g_count[i], (unsigned long long)c);
+        }
+      }
+    }
+  } else if (SMEM) {
     if (UNIT) {
       unsigned* out = reinterpret_cast<unsigned*>(p.part_bins) + (size_t)blockIdx.x * nb;
       for (int i = threadIdx.x; i < nb; i += blockDim.x) out[i] = f.sbins[i];
@@ -582,6 +607,28 @@ __global__ void __launch_bounds__(256, NDIM == 1 ? HGB_MIN_BLOCKS_1D : HGB_MIN_B
       out[i] = __dadd_rn((double)sf[2 * i], (double)sf[2 * i + 1]);
   }
   block_reduce_stats<NS>(f.st.d, p.part_stats + (size_t)blockIdx.x * kMaxStats, sred);
+  if constexpr (DIRECT) {
+    // the last block to finish adds the statistics partials, in block
+    // order with a fixed shuffle tree (k_reduce's order), and resets the
+    // ticket for the next fill
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(p.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (int k = 2 + warp; k < p.nstats; k += blockDim.x >> 5) {
+        double s = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) s = __dadd_rn(s, __ldcg(p.part_stats + (size_t)b * kMaxStats + k));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_down_sync(0xffffffffu, s, o));
+        if (lane == 0) p.g_stats[k] = __dadd_rn(p.g_stats[k], s);
+      }
+      if (threadIdx.x == 0) *p.ticket = 0u;
+    }
+  }
 }
 
 // Reduce: grid (bin tiles) x (slices of partials).  Thread (tile, slice, t)
@@ -675,7 +722,7 @@ __global__ void __launch_bounds__(256) k_locate(const FillParams p, long long* _
 }
 
 template <int NDIM, int ACC, bool SMEM>
-const void* fill_fn(int loc, bool sw2, bool expr) {
+const void* fill_fn(int loc, bool sw2, bool expr, bool direct) {
   if constexpr (NDIM <= 2) {
     // Filter/Define fills (1D and 2D; run-time locate)
     if (expr) return sw2 ? nullptr : reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, -1, false, true>);
@@ -690,6 +737,17 @@ const void* fill_fn(int loc, bool sw2, bool expr) {
   if constexpr (NDIM > 1) {
     return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, -1, false, false>);
   } else {
+    if constexpr (SMEM && (ACC == ACC_UNIT || ACC == ACC_FX)) {
+      if (direct) {
+        if (loc == LOC_AFFINE) return reinterpret_cast<const void*>(&k_fill<1, ACC, true, LOC_AFFINE, false, false, true>);
+        if (loc == LOC_LEARNED)
+          return reinterpret_cast<const void*>(&k_fill<1, ACC, true, LOC_LEARNED, false, false, true>);
+        if (loc == LOC_BUCKET) return reinterpret_cast<const void*>(&k_fill<1, ACC, true, LOC_BUCKET, false, false, true>);
+        if (loc == LOC_BSEARCH)
+          return reinterpret_cast<const void*>(&k_fill<1, ACC, true, LOC_BSEARCH, false, false, true>);
+        return nullptr;
+      }
+    }
     if (loc == LOC_AFFINE) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_AFFINE, false, false>);
     if (loc == LOC_LEARNED) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_LEARNED, false, false>);
     if (loc == LOC_BUCKET) return reinterpret_cast<const void*>(&k_fill<NDIM, ACC, SMEM, LOC_BUCKET, false, false>);
@@ -702,9 +760,10 @@ const void* fill_fn(int loc, bool sw2, bool expr) {
 }
 
 // 1D kernels are specialised per locate mode; ND kernels choose per axis at run time.
-const void* pick_fill(int ndim, int acc, bool smem, int loc, bool sw2, bool expr) {
-#define HGB_PICK(N, A) \
-  if (ndim == N && acc == A) return smem ? fill_fn<N, A, true>(loc, sw2, expr) : fill_fn<N, A, false>(loc, sw2, expr);
+const void* pick_fill(int ndim, int acc, bool smem, int loc, bool sw2, bool expr, bool direct) {
+#define HGB_PICK(N, A)                                                                   \
+  if (ndim == N && acc == A)                                                             \
+    return smem ? fill_fn<N, A, true>(loc, sw2, expr, direct) : fill_fn<N, A, false>(loc, sw2, expr, direct);
   HGB_PICK(1, ACC_UNIT)
   HGB_PICK(1, ACC_FX)
   HGB_PICK(1, ACC_F64)
@@ -742,7 +801,16 @@ int fill_loc(const FillParams& p, int acc_mode) {
 
 // The kernel of a fill.
 const void* fill_kernel(const FillParams& p, int acc_mode) {
-  return pick_fill(p.ndim, acc_mode, p.smem_bins != 0, fill_loc(p, acc_mode), p.sumw2 != 0, p.ex.nsrc > 0);
+  return pick_fill(p.ndim, acc_mode, p.smem_bins != 0, fill_loc(p, acc_mode), p.sumw2 != 0, p.ex.nsrc > 0,
+                   p.direct_flush != 0);
+}
+
+// Whether a fill has a direct-flush kernel: 1D, exact fixed-point or
+// unit-count shared bins, no sum of w^2, no Filter/Define; the specialised
+// bucket-pair kernel keeps the reduce.
+bool fill_direct_ok(const FillParams& p, int acc_mode) {
+  return p.ndim == 1 && p.smem_bins && !p.sumw2 && p.ex.nsrc == 0 && (acc_mode == ACC_UNIT || acc_mode == ACC_FX) &&
+         fill_loc(p, acc_mode) != kLocBucketHiSingle;
 }
 
 int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shape) {

@@ -145,6 +145,14 @@ struct FillParams {
   int32_t aligned;              // columns and weights all 16-byte aligned
   int32_t smem_bins;            // 1 = per-block shared-memory bins, 0 = global atomics
   int32_t sumw2;                // 1 = also the per-bin sum of squared weights (weighted fills)
+  // direct flush (exact fixed-point or unit-count shared bins, no sum of
+  // w^2): each block adds its bins to the persistent accumulators with
+  // integer atomics, and the last block to finish (ticket: a counter that
+  // starts at 0 and that block resets) adds the statistics partials in block
+  // order into g_stats -- no partial bins and no reduce launch
+  int32_t direct_flush;
+  unsigned* ticket;
+  double* g_stats;
   // per-launch partial results (scratch)
   void* part_bins;              // [grid][nbins_total] words per bin depend on the mode
   double* part_stats;           // [grid][kMaxStats]
@@ -379,6 +387,8 @@ struct LaunchShape {
 };
 
 int plan_fill(const FillParams& p, int acc_mode, int sm_count, LaunchShape* shape);
+// Whether a fill has a kernel that flushes its bins itself (p.direct_flush).
+bool fill_direct_ok(const FillParams& p, int acc_mode);
 int launch_fill(const FillParams& p, int acc_mode, const LaunchShape& shape, void* stream);
 int launch_reduce(const ReduceParams& r, void* stream);
 int launch_locate(const FillParams& p, long long* out, void* stream);
