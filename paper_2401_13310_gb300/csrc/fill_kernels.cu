@@ -848,8 +848,10 @@ int launch_reduce(const ReduceParams& r0, void* stream) {
   long long tiles = (r.nbins_total + 255) / 256;
   int slices = 1;
   if (r.part_bins != nullptr) {
-    // about 32 partials per thread, at least ~2 CTAs per SM overall
-    r.slice = 32;
+    // 8 partials per thread: the reduce of a 608-block fill of 1000 bins
+    // then runs 4 x 76 blocks (the summing thread's loads are the latency;
+    // 32 partials per thread took 4 us more per fill call)
+    r.slice = 8;
     slices = (r.nblocks + r.slice - 1) / r.slice;
     if (slices > 65535) slices = 65535;
     r.slice = (r.nblocks + slices - 1) / slices;
