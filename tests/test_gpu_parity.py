@@ -411,3 +411,31 @@ def test_empty_and_tiny_fills(B, axis, weighted):
             batch.close()
         h.close()
         hb.close()
+
+
+@pytest.mark.parametrize("n", [300_007, 6_000_001], ids=["flush_in_fill", "reduce_kernel"])
+def test_statistics_bit_reproducible(B, n):
+    """The plain fill's statistics do not depend on the run: each thread
+    adds its events in a fixed order, blocks combine their threads with a
+    fixed tree, and the block partials are added in block order -- by the
+    fill's last block for small fills, by the reduce kernel for large ones.
+    Two fills of the same events into fresh histograms give the same
+    statistics bit for bit (and the same bins)."""
+    import torch
+    wl = W.cfg2a(n=n)
+    x = to_device(wl.values[0])
+    w = to_device(wl.weights)
+    got = []
+    for _ in range(2):
+        h = B.Hist(wl.axes)
+        try:
+            h.fill(x, w)
+            torch.cuda.synchronize()
+            got.append(h.result())
+        finally:
+            h.close()
+    (b0, s0), (b1, s1) = got
+    assert np.array_equal(b0, b1)
+    assert np.array_equal(s0.view(np.uint64), s1.view(np.uint64)), f"statistics differ: {s0} {s1}"
+    ref = oracle.fill(wl.axes, wl.values, wl.weights)
+    check_against_oracle(wl.axes, wl.values, wl.weights, b0, s0, None, ref, what="reproducible fill")
