@@ -665,14 +665,17 @@ const void* part_fill_row(int row) {
 // (weighted fills of an FP32C batch; a unit-weight fill counts exactly).
 // A fill (unit weights or exact fixed point) whose shared tables allow at
 // most two blocks per SM takes the four-events-at-a-time kernel.
-const void* part_fill_fn(bool unit, bool f32c, int row, size_t fill_smem) {
+const void* part_fill_fn(bool unit, bool f32c, int row, size_t fill_smem, int* events = nullptr) {
+  if (events != nullptr) *events = 2;
   if (f32c && !unit) return part_fill_row<false, true>(row);
   const void* two = unit ? part_fill_row<true, false>(row) : part_fill_row<false, false>(row);
   int per_sm = 0;
   if (cudaFuncSetAttribute(two, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem) == cudaSuccess &&
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, two, part_fill_block<true>(), fill_smem) == cudaSuccess &&
-      per_sm >= 1 && per_sm <= 2)
+      per_sm >= 1 && per_sm <= 2) {
+    if (events != nullptr) *events = 4;
     return unit ? part_fill_row<true, false, 4>(row) : part_fill_row<false, false, 4>(row);
+  }
   cudaGetLastError();
   return two;
 }
@@ -696,6 +699,12 @@ size_t part_scatter_smem(int nranges, int split_nbk, bool weighted) {
 size_t part_fill_smem(int max_keys, int max_bins, int nh, int row_u16, int max_nbk, int slot_bytes) {
   return (((size_t)(max_keys + 1) * row_u16 * 2 + 15) & ~(size_t)15) + (((size_t)(max_nbk + 1) * 2 + 15) & ~(size_t)15) +
          (size_t)max_keys * 8 + sizeof(PartSliceDev) * (size_t)nh + (size_t)max_bins * slot_bytes;
+}
+
+int part_fill_events(bool unit, bool f32c, int row, size_t fill_smem) {
+  int events = 2;
+  part_fill_fn(unit, f32c, row, fill_smem, &events);
+  return events;
 }
 
 int part_grids(int sm_count, int nranges, int split_nbk, size_t fill_smem, int* count_grid, int* fill_per_sm) {

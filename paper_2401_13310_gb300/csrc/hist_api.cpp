@@ -2410,7 +2410,16 @@ void batch_report(const hist_batch* b, hist_batch_tuning_t* r) {
   r->slices = b->strategy == 1 ? (int)b->slices.size() : (b->strategy == 2 ? nranges : 0);
   r->replicas = b->strategy == 1 ? b->slice_replicas : 0;
   r->cost_cap_tenths = b->strategy == 1 ? (int)(10.0 * b->slice_cap + 0.5) : 0;
-  r->events_per_thread = b->strategy == 0 ? b->wide_kev : 4;
+  if (b->strategy == 0) {
+    r->events_per_thread = b->wide_kev;
+  } else if (b->strategy == 1) {
+    r->events_per_thread = 4;
+  } else {
+    // the partitioned fill's kernel for the tuned sample's weights
+    r->events_per_thread = 2;
+    for (const PartPlan& q : b->plans)
+      r->events_per_thread = std::max(r->events_per_thread, part_fill_events(b->placed_unit, b->f32c, q.row, q.smem));
+  }
 }
 }  // namespace
 

@@ -368,6 +368,9 @@ size_t part_count_smem(int nranges, int split_nbk);
 size_t part_scatter_smem(int nranges, int split_nbk, bool weighted);
 size_t part_fill_smem(int max_keys, int max_bins, int nh, int row_u16, int max_nbk, int slot_bytes);
 int part_grids(int sm_count, int nranges, int split_nbk, size_t fill_smem, int* count_grid, int* fill_per_sm);
+// events each thread of the partitioned fill holds at a time (2 or 4) for
+// this precision, count row and shared-memory size
+int part_fill_events(bool unit, bool f32c, int row, size_t fill_smem);
 int launch_part_fill(const PartParams& p, bool unit, bool f32c, int fill_grid, size_t fill_smem, void* stream);
 
 int launch_slice_fill(const SliceParams& p, int block, int grid, size_t smem, void* stream);

@@ -409,6 +409,7 @@ def test_batch_partitioned_edges_specials_and_accumulate(B, weighted, ncols, bud
         assert info["strategy"] == 2
         if budget > (64 << 10):
             assert info["blocks_per_sm"] <= 2, info
+        assert info["events_per_thread"] == (4 if info["blocks_per_sm"] <= 2 else 2), info
         cols = [to_device(c) for c in columns]
         wd = to_device(w)
         batch.fill(cols, wd)
