@@ -408,7 +408,8 @@ int hist_locator_loss_grad(int nseg, float u0, float u_scale, const int32_t *bas
  * No device or host memory is allocated: the scratch is one fixed library
  * array of about 5 MB per device, held until the process exits.  The first
  * call on a device looks up that array's address (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  Calls share the array:
+ * make that first call before any stream capture; later calls may be
+ * captured into a CUDA graph and replayed.  Calls share the array:
  * calls that overlap on the GPU (unordered streams or threads) race and give
  * wrong results.  Errors: HIST_ERR_ARG, HIST_ERR_AXIS, HIST_ERR_TOO_LARGE
  * (nbins + 2 > 1024), HIST_ERR_ALIGN, HIST_ERR_CUDA. */

@@ -14,7 +14,8 @@
 // The array's name means a device address only in device code.  Host code
 // obtains that address per device with cudaGetSymbolAddress, once, with the
 // device current: the first call of the entry point on each device does
-// this set-up, so that first call should come before any stream capture.
+// this set-up, so that first call should come before any stream capture;
+// every later call only enqueues kernels and may be captured into a graph.
 //
 // All calls share the array and it keeps the last call's contents: each
 // call clears the parts that must start at zero.  Calls whose work overlaps

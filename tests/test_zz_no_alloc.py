@@ -132,6 +132,50 @@ def test_noalloc_odd_weights(B):
     assert got_stats[0] == n and math.isnan(got_stats[1]) and math.isnan(reg_stats[1])
 
 
+def test_noalloc_captured_in_a_cuda_graph_and_replayed(B):
+    """After the first call on the device (its one-time set-up), the call is
+    captured into a CUDA graph; every replay, with new events written into
+    the same input buffers, gives the oracle's answer on those events.  The
+    graph holds the whole call -- the thresholds as a kernel argument, the
+    clearing of the scratch, the fill, the reduce and the finish -- and no
+    copy from host memory."""
+    import torch
+    rng = np.random.default_rng(25)
+    cases = ((W.variable(W.log_edges(500, 0.0, 3.0)), True), (W.fixed(1000, -5.0, 5.0), False))
+    for axis, weighted in cases:
+        n = 250_007
+        nb = (axis["nbins"] if axis["kind"] == "fixed" else len(axis["edges"]) - 1) + 2
+        xd = torch.zeros(n, dtype=torch.float64, device="cuda")
+        wd = torch.ones(n, dtype=torch.float64, device="cuda") if weighted else None
+        bins = torch.zeros(nb, dtype=torch.float64, device="cuda")
+        stats = torch.zeros(5, dtype=torch.float64, device="cuda")
+        B.hist_fill_bulk_noalloc(axis, xd, wd, n, 0, bins, stats)  # outside any capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            B.hist_fill_bulk_noalloc(axis, xd, wd, n, 0, bins, stats)
+        for rep in range(3):
+            what = f"{axis['kind']} replay {rep}"
+            x = rng.exponential(30.0, n) if axis["kind"] == "variable" else rng.normal(0, 1.5, n)
+            w = rng.uniform(-0.5, 1.5, n) if weighted else None
+            xd.copy_(torch.from_numpy(x))
+            if weighted:
+                wd.copy_(torch.from_numpy(w))
+            bins.fill_(float("nan"))
+            stats.fill_(float("nan"))
+            g.replay()
+            torch.cuda.synchronize()
+            got_bins, got_stats = bins.cpu().numpy(), stats.cpu().numpy()
+            ref = oracle.fill([axis], x.reshape(1, -1), w)
+            if w is None:
+                assert np.array_equal(got_bins, ref.counts.astype(np.float64)), f"{what}: unit-weight bins"
+            else:
+                assert_sums_close(got_bins, ref.bins_acc, ref.bins_abs, RTOL, f"{what} bins")
+            assert got_stats[0] == n, f"{what}: entries"
+            assert_sums_close(got_stats[1:], ref.stats_acc[1:], ref.stats_abs[1:], RTOL, f"{what} stats")
+        del g
+
+
 def test_noalloc_rejects_oversized_axis(B):
     import torch
     axis = W.fixed(1023, 0.0, 1.0)  # 1025 bins with flows: one above the maximum
