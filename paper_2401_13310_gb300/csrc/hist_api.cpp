@@ -2432,9 +2432,10 @@ extern "C" int hist_batch_tune(hist_batch_t* b, const double* const* cols, int n
   for (hist* h : b->hs)
     if (h->have_done && cudaEventSynchronize(h->done) != cudaSuccess) return HIST_ERR_CUDA;
   b->placed_unit = weights == nullptr;  // unit samples place one word per bin (a weighted fill re-places)
-  // candidates: the wide strategy at five budgets, the sliced one at three
-  // budgets times three work caps (unless the batch was created with a fixed
-  // strategy)
+  // candidates: the wide strategy at five budgets times two occupancies
+  // times two events per thread, the sliced one at two budgets times two
+  // work caps (exact batches: an FP32C batch refuses it), the partitioned
+  // one at three budgets (unless the batch was created with a fixed strategy)
   struct Cand {
     int strategy, budget;
     double cap;
