@@ -307,7 +307,9 @@ typedef struct {
   int32_t slices;          /* sliced: slices of the chosen plan; partitioned: ranges over all columns; 0 wide */
   int32_t replicas;        /* sliced: blocks per slice */
   int32_t cost_cap_tenths; /* sliced: work cap per slice of the chosen plan, tenths of one histogram */
-  int32_t events_per_thread; /* events each thread holds per pass over the histograms */
+  int32_t events_per_thread; /* events each fill thread holds at a time: wide, per pass over the
+                                members (2 or 4); sliced 4; partitioned 2, or 4 in the kernel
+                                compiled for two blocks per SM (tables too large for three) */
 } hist_batch_tuning_t;
 
 /* Autotune the batch (for fills like the sample: a unit-weight sample lets
