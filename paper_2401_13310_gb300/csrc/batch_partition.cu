@@ -457,12 +457,12 @@ struct PartFill {
   }
 };
 
-// Threads per fill block (256), and the blocks per SM its registers are
-// sized for: weighted fills three (80 registers, so that the small ranges of
-// a 48 KB budget run three blocks per SM -- the fill waits mostly on
-// shared-memory latency, so resident warps set its pace), unit-weight fills
-// two (their 64 registers fit three anyway; 512-thread blocks measured 4 %
-// slower on the 8-axis workload).
+// Threads per fill block (256; 512-thread blocks measured 4 % slower on the
+// 8-axis workload).  The two-events kernel's registers are sized for three
+// blocks per SM with weights (80 registers, so that the small ranges of a
+// 48 KB budget run three blocks per SM -- the fill waits mostly on
+// shared-memory latency, so resident warps set its pace) and four with unit
+// weights (64 registers).
 template <bool UNIT>
 __host__ __device__ constexpr int part_fill_block() {
   return 256;
