@@ -200,8 +200,8 @@ def measure_precisions(B, W, hbm: float, n: int) -> dict:
 
 
 def measure_filter_define(B, W, hbm: float, n: int) -> dict:
-    """The paper's RDataFrame example (Filter x != 0, Define r2 = x*x + y*y,
-    Histo1D r2) fused into the fill kernel, beside the same done as separate
+    """The paper's RDataFrame example (rows with x nonzero kept, r2 = x^2 +
+    y^2 defined, r2 histogrammed) fused into the fill kernel, beside the same done as separate
     steps (torch computes r2 and compacts the passing rows, then the fill)."""
     import torch
     g = torch.Generator(device="cuda")

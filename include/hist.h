@@ -162,9 +162,9 @@ int hist_result(hist_t *h, double *bins, double *stats);
 int hist_counts(hist_t *h, uint64_t *counts);
 
 /* ---- fused Filter/Define -------------------------------------------------
- * The paper's RDataFrame example (Sec. 2, Listing 1) filters rows
- * (Filter("x != 0")), defines a column (Define("r2", "x*x + y*y")) and
- * fills a histogram with it.  hist_fill_columns does all three in the fill
+ * The paper's RDataFrame example (Sec. 2, Listing 1) keeps the rows whose
+ * x is nonzero, defines a new column r2 = x^2 + y^2 from two existing ones
+ * and fills a histogram with it.  hist_fill_columns does all three in the fill
  * kernel, without writing the defined column: for each event i of the
  * source columns cols[0..ncols) (device [n] binary64 each, ncols <= 4), if
  * every filter holds (cols[col][i] <op> value, binary64 comparison; NaN

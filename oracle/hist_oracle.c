@@ -16,7 +16,7 @@
  *     Fixed-width bins: bin = 1 + floor(nbins * (x - min) / (max - min)).
  *     Variable-width bins: a binary search over the edges.
  *     A coordinate outside the range goes to the underflow or overflow bin.
- *     Higher dimensions repeat the find-bin step per axis.
+ *     In 2D and 3D every axis is located on its own.
  *   Sec. 3.2 (Native CUDA): in one dimension the statistics are four sums,
  *     the sum of weights, of squared weights, of weight*x and of weight*x^2.
  *

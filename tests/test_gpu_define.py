@@ -1,6 +1,6 @@
 """Fused Filter/Define fill (hist_fill_columns) against the oracle: the
-paper's RDataFrame example -- Filter("x != 0"), Define("r2", "x*x + y*y"),
-Histo1D("r2") -- and 2D and weighted variants, with zeros, signed zeros,
+paper's RDataFrame example (rows with x nonzero kept, r2 = x^2 + y^2 defined
+per row, r2 histogrammed) and 2D and weighted variants, with zeros, signed zeros,
 NaN and infinities in the source columns.  Counts exact; weighted sums and
 statistics within 1e-12 of sum |term|; the entry count is the number of
 rows that pass the filters."""
