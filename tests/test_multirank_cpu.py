@@ -1,4 +1,4 @@
-"""The multi-process side of the benchmark and the replicas-only sharding,
+"""The multi-process side of the benchmark and the sharding of events over ranks,
 as world_size-2 gloo process groups on the CPU (rendezvous on 127.0.0.1):
 the timing reduction takes the max over ranks, and filling each rank's
 share of the events and summing the histograms over ranks gives the
