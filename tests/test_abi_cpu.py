@@ -137,3 +137,30 @@ def test_host_thresholds_random_fixed_axes(lib):
         xmax = xmin + float(rng.choice([1e-6, 0.37, 1.0, 12.5, 1e4]))
         axis = W.fixed(nb, xmin, xmax)
         _check_thresholds(axis, B.hist_axis_thresholds(axis))
+
+
+def test_no_host_fallback_without_a_gpu(lib):
+    """The library has no CPU path: without a GPU, booking a valid
+    histogram fails with HIST_ERR_CUDA instead of succeeding on the host."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(B.HistError) as e:
+        B.hist_book([{"kind": "fixed", "nbins": 10, "xmin": 0.0, "xmax": 1.0}])
+    assert e.value.code == B.HIST_ERR_CUDA
+
+
+def test_binding_fails_loudly_when_the_library_is_missing(tmp_path):
+    """Loading a library that is not there raises; the binding has no
+    fallback to fill with."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("from paper_2401_13310_gb300 import binding as B\n"
+            "try:\n"
+            f"    B.load({str(tmp_path / 'libhist.so')!r})\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "raised:" in r.stdout and "missing" in r.stdout
