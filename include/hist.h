@@ -438,6 +438,20 @@ int hist_ndim(const hist_t *h);
  * out[k] <= key(x).  Errors: HIST_ERR_ARG, HIST_ERR_AXIS. */
 int hist_axis_thresholds(const hist_axis_t *axis, int64_t *out);
 
+/* The FP32 estimate the kernels locate a fixed axis with (host only; needs
+ * no GPU).  For a coordinate x with |x| in [2^-126, 2^128) the device forms
+ * v = fmaf(x24, scale, offset), x24 = x truncated to its leading 24
+ * significant bits, and takes floor(v), clamped to [0, nbins + 1], as the
+ * bin when the fraction of v lies more than eps from an integer; otherwise
+ * (and for every other x) it compares the key of x with the thresholds of
+ * hist_axis_thresholds.  eps bounds |v - (1 + q)|, q the quotient of the
+ * Sec. 3.1 fixed-width formula in binary64, wherever that test can pass.
+ * Returns HIST_OK when the axis takes the estimate, HIST_ERR_UNSUPPORTED
+ * when no useful bound holds (nbins >= 2^21, extreme ranges): the kernels
+ * then locate by the thresholds alone.  Errors: HIST_ERR_ARG, HIST_ERR_AXIS
+ * (an invalid axis, or a variable one). */
+int hist_axis_affine(const hist_axis_t *axis, float *scale, float *offset, float *eps);
+
 /* Static description of a status code. */
 const char *hist_strerror(int code);
 

@@ -125,6 +125,7 @@ def load(path: str | None = None):
             "hist_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "hist_version": (ctypes.c_char_p, []),
             "hist_axis_thresholds": (ctypes.c_int, [_P, _P]),
+            "hist_axis_affine": (ctypes.c_int, [_P, _P, _P, _P]),
             "hist_fill_bulk_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_uint32, _P, _P, _P]),
             "hist_train_locator": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
             "hist_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_uint32, _P]),
@@ -267,6 +268,19 @@ def hist_axis_thresholds(axis) -> np.ndarray:
     del keep
     _check(rc, "hist_axis_thresholds")
     return out
+
+
+def hist_axis_affine(axis):
+    """(scale, offset, eps) of the FP32 estimate a fixed axis is located
+    with, or None when the axis is located by its thresholds alone."""
+    arr, keep = make_axes([axis])
+    s, o, e = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+    rc = load().hist_axis_affine(ctypes.addressof(arr), ctypes.byref(s), ctypes.byref(o), ctypes.byref(e))
+    del keep
+    if rc == HIST_ERR_UNSUPPORTED:
+        return None
+    _check(rc, "hist_axis_affine")
+    return s.value, o.value, e.value
 
 
 def hist_fill_bulk_noalloc(axis, values, weights, n: int, flags: int, bins_out, stats_out,

@@ -753,6 +753,14 @@ int hist_axis_thresholds(const hist_axis_t* axis, int64_t* out) {
   return HIST_OK;
 }
 
+int hist_axis_affine(const hist_axis_t* axis, float* scale, float* offset, float* eps) {
+  if (axis == nullptr || scale == nullptr || offset == nullptr || eps == nullptr) return HIST_ERR_ARG;
+  if (validate_axis(axis->kind, axis->nbins, axis->xmin, axis->xmax, axis->edges) != 0 ||
+      axis->kind != HIST_AXIS_FIXED)
+    return HIST_ERR_AXIS;
+  return affine_estimate(axis->nbins, axis->xmin, axis->xmax, scale, offset, eps) ? HIST_OK : HIST_ERR_UNSUPPORTED;
+}
+
 int64_t hist_nbins_total(const hist_t* h) { return h ? h->nbins_total : -1; }
 int hist_nstats(const hist_t* h) { return h ? h->nstats : -1; }
 int hist_ndim(const hist_t* h) { return h ? h->ndim : -1; }
